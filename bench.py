@@ -1,0 +1,321 @@
+"""Benchmark of the coupled LB-IB time step on GB300.
+
+One step = the whole hot path over the lattice: particle probes / force and
+torque / rigid-body update, MLS marker interpolation and spreading, and the
+fused pull-stream + Zou-He + forced-BGK collide of every cell.
+
+Default workload: sedimentation of a circle (D = 50, density ratio 1.5) in a
+closed 400 x 1200 box, FP32 populations (stored as f - w_i) with FP64
+particle work.  Its 35 MB working set fits in L2, so L2 is flushed between
+timed steps.  Also reported: the same step on a 16384 x 4096 Couette lattice
+with 64 particles (4.8 GB of populations, beyond L2) for the HBM roofline.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "MLUPS incl. IBM coupling, % of HBM roofline; batched & adjoint vs plain"
+FALLBACK_HBM_GBS = 6800.0
+BYTES_PER_CELL = {0: 144, 1: 72, 2: 36}  # read + write 9 populations (FP64 / FP32 / FP16)
+PREC_NAMES = {0: "f64", 1: "f32", 2: "f16-storage/f32"}
+
+# dram__bytes_read.sum + dram__bytes_write.sum per fluid-kernel launch from one
+# ncu capture, keyed by the hash of the kernel sources it was taken on
+NCU_TRAFFIC = {}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for name in ("fluid.cu", "lbib_device.cuh", "lbib_internal.h"):
+        h.update((ROOT / "paper_1606_01805_gb300" / "csrc" / name).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        try:
+            d = json.loads(p.read_text())
+            for k in ("hbm_gbs", "hbm_GBps", "hbm_copy_gbs"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=5)
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(name, steps):
+    from paper_1606_01805_gb300 import workloads as W
+
+    if name == "sedimentation":
+        return W.sedimentation("circle", steps=steps)
+    if name == "sedimentation_ellipse":
+        return W.sedimentation("ellipse", steps=steps)
+    if name == "couette":
+        return W.couette_circle(steps=steps)
+    if name == "large":
+        return W.large_couette(steps=steps)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def gpu_sim(wl, prec):
+    from paper_1606_01805_gb300 import lbib
+
+    sim = lbib.Simulation(wl.nx, wl.ny, wl.tau, precision=prec, max_particles=max(16, len(wl.particles)),
+                          **wl.lattice_kwargs())
+    for p in wl.particles:
+        sim.add_particle(**p.kwargs())
+    return sim
+
+
+def time_device(wl, prec, steps, warmup, flush):
+    """Device time of `steps` steps (CUDA events inside the library on the
+    context's stream), optionally flushing L2 before each step."""
+    import torch
+
+    sim = gpu_sim(wl, prec)
+    big = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if flush else None
+    big2 = torch.ones(64 << 20, dtype=torch.float32, device="cuda") if flush else None
+
+    def do_flush():
+        if flush:
+            big.fill_(1)          # write 256 MB (> 129 MB L2)
+            big2.sum()            # then read 256 MB so L2 holds clean lines
+
+    for _ in range(warmup):
+        do_flush()
+        sim.step_timed(1)
+    sim.sync()
+    ms_step = ms_fluid = 0.0
+    for _ in range(steps):
+        do_flush()
+        a, b = sim.step_timed(1)
+        ms_step += a
+        ms_fluid += b
+    sim.sync()
+    launches = steps * (3 if wl.particles else 1)
+    markers = sum(p.n_markers for p in wl.particles)
+    sim.close()
+    return ms_step, ms_fluid, launches
+
+
+def time_e2e(wl, prec, steps):
+    """The user's job through the public API with host buffers: upload the
+    initial populations, advance `steps`, read back fields and particles."""
+    import numpy as np
+    import torch
+
+    from paper_1606_01805_gb300 import lbib
+
+    sim = gpu_sim(wl, prec)
+    f0 = sim.populations()  # host copy of the initial state (job input)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.set_populations(f0)
+    sim.step(steps)
+    rho, ux, uy = sim.fields()
+    parts = sim.particles()
+    t1 = time.perf_counter()
+    h2d = f0.nbytes
+    d2h = rho.nbytes + ux.nbytes + uy.nbytes + len(parts) * 9 * 8
+    sim.close()
+    return t1 - t0, h2d, d2h
+
+
+def cpu_oracle_rate(wl, budget_s=10.0, min_steps=5):
+    """The FP64 oracle as it stands, single-threaded, on the first steps of
+    the same workload (bounded by `budget_s` of CPU time)."""
+    from oracle import oracle as o
+    from paper_1606_01805_gb300 import workloads as W
+
+    sim = W.run_with(lambda nx, ny, tau, **kw: o.Sim(nx, ny, tau, **kw), wl, steps=0)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        sim.step(1)
+        n += 1
+        dt = time.perf_counter() - t0
+        if (dt >= budget_s and n >= min_steps) or n >= wl.steps:
+            break
+    return wl.cells * n / dt / 1e6, n, dt
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sedimentation")
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16s"])
+    ap.add_argument("--no-large", action="store_true", help="skip the 16384 x 4096 roofline run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    prec = {"fp64": 0, "fp32": 1, "fp16s": 2}[args.precision]
+    ws, rank, local = dist_env()
+    wl = make_workload(args.workload, steps=20000)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = max(1, args.steps)
+        from oracle import oracle as o
+        from paper_1606_01805_gb300 import workloads as W
+
+        sim = W.run_with(lambda nx, ny, tau, **kw: o.Sim(nx, ny, tau, **kw), wl, steps=0)
+        for _ in range(args.warmup):
+            sim.step(1)
+        t0 = time.perf_counter()
+        sim.step(steps)
+        dt = time.perf_counter() - t0
+        v = wl.cells * steps / dt / 1e6
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": 1,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": dt / steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "nx": wl.nx, "ny": wl.ny,
+                                            "particles": len(wl.particles)},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{steps} full-lattice steps after {args.warmup} warm-up"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+
+    import torch
+
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1606_01805_gb300 import build
+
+    build.build()
+    flush = True  # this workload's working set is smaller than L2
+    with ClockSampler(local) as clk:
+        ms_step, ms_fluid, launches = time_device(wl, prec, args.steps, args.warmup, flush)
+    T = torch.tensor([ms_step, ms_fluid], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.barrier()
+        dist.all_reduce(T, op=dist.ReduceOp.MAX)
+    ms_step, ms_fluid = T.tolist()
+    cells = wl.cells
+    value = ws * cells * args.steps / (ms_step * 1e-3) / 1e6  # MLUPS over all replicas
+    peak, peak_kind = hbm_peak()
+    algo_bytes = BYTES_PER_CELL[prec] * cells
+    achieved = algo_bytes / (ms_fluid * 1e-3 / args.steps) / 1e9
+    traffic = NCU_TRAFFIC.get(kernel_hash())
+    out = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAMES[prec], "data": "synthetic",
+        "config": {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "tau": wl.tau,
+                   "particles": len(wl.particles), "precision": args.precision +
+                   " populations, fp64 particle work", "l2": "flushed before every timed step",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_fluid (fused pull-stream / Zou-He / forced BGK)",
+                     "peak_source": f"{peak_kind} (burst copy)",
+                     "algorithmic_bytes_per_launch": algo_bytes},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "ms_fluid_per_step": ms_fluid / args.steps,
+    }
+    if rank == 0:
+        e2e_s, h2d, d2h = time_e2e(wl, prec, args.steps)
+        out["e2e"] = {"value": cells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+                      "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                      "job": f"upload f0, {args.steps} steps, read fields + particles"}
+        if not args.no_large:
+            big = make_workload("large", steps=0)
+            s2, f2, _ = time_device(big, prec, 10, 3, flush=False)
+            a2 = BYTES_PER_CELL[prec] * big.cells / (f2 * 1e-3 / 10) / 1e9
+            out["large_lattice"] = {"workload": big.name, "particles": len(big.particles),
+                                    "value": big.cells * 10 / (s2 * 1e-3) / 1e6, "unit": "MLUPS",
+                                    "fluid_GBps": a2, "frac_of_peak": a2 / peak,
+                                    "frac_of_roofline_mlups": big.cells * 10 / (s2 * 1e-3) /
+                                    (peak * 1e9 / BYTES_PER_CELL[prec])}
+        if not args.no_cpu:
+            v, n, dt = cpu_oracle_rate(wl)
+            out["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                                   "sample": f"first {n} steps of {wl.name} ({dt:.1f} s, FP64, 1 thread)"}
+        print(json.dumps(out))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

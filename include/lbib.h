@@ -1,0 +1,193 @@
+/*
+ * lbib.h -- C ABI of the GB300 (sm_103a) library for the coupled
+ * lattice-Boltzmann / immersed-boundary (LB-IB) method of Coclite,
+ * de Tullio, Pascazio and Decuzzi, "A combined Lattice Boltzmann and
+ * Immersed Boundary approach for predicting the vascular transport of
+ * differently shaped particles" (arXiv:1606.01805).
+ *
+ * One context holds one D2Q9 lattice and its rigid particles on one GPU.
+ * A step (lbm_step) is, in this order (Section 2, weak coupling):
+ *   1. pull-streaming (Eq. 4) with Zou-He known-velocity walls (Section 2.1);
+ *   2. density and velocity moments (Eqs. 6-7);
+ *   3. per particle: probe-based surface stress, force and torque (Eqs.
+ *      13-14, Section 2.3) and the two-level rigid-body update (Eqs. 15-16);
+ *   4. MLS interpolation of lattice velocity to the Lagrangian markers
+ *      (Eqs. 8-10), direct-forcing marker force (Eq. 11), spreading of the
+ *      marker forces to the lattice (Eq. 12);
+ *   5. BGK collision with the Guo forcing term (Eqs. 2, 4, 5).
+ *
+ * Conventions shared by every call:
+ *  - Lattice units: dx = dt = 1.  Nodes (x, y), 0 <= x < nx, 0 <= y < ny.
+ *    Wall nodes are the first/last row (column) of nodes, so a channel
+ *    between y walls has height H = ny - 1.
+ *  - Host arrays of fields are y-major: element (x, y) at index y * nx + x.
+ *    Populations are [9][ny][nx] in the velocity order e_0 = (0,0),
+ *    e_1..e_4 = (1,0), (0,1), (-1,0), (0,-1), e_5..e_8 = (1,1), (-1,1),
+ *    (-1,-1), (1,-1) (Eq. 3).
+ *  - Every call returns an lbm_status; nothing throws across the ABI.  On
+ *    an error, lbm_last_error() gives a one-line reason.
+ *  - A context is used by one host thread at a time.
+ *  - Device work is enqueued on cfg.cuda_stream (NULL: the legacy default
+ *    stream).  lbm_step does not synchronise; every lbm_get_* call does.
+ */
+#ifndef LBIB_H
+#define LBIB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,     /* bad argument or configuration */
+    LBM_ENOMEM = 2,     /* workspace too small or allocation failed */
+    LBM_ECUDA = 3,      /* a CUDA runtime call failed */
+    LBM_ETIMEOUT = 4,   /* a bounded device wait expired */
+    LBM_ENONFINITE = 5, /* NaN/Inf or non-positive density detected */
+    LBM_EINTERNAL = 6,
+    LBM_EDOMAIN = 7     /* a marker or probe support crossed a wall */
+} lbm_status;
+
+/* side kinds, for sides ordered x-, x+, y-, y+ */
+typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_VELOCITY = 1 } lbm_bc;
+
+/* storage / arithmetic of the populations.  Particle work (probes, force
+   and torque reduction, MLS 3x3 solves, rigid-body update) is always FP64. */
+typedef enum {
+    LBM_FP64 = 0,        /* FP64 populations, FP64 collision */
+    LBM_FP32 = 1,        /* FP32 populations stored as f - w_i, FP32 collision */
+    LBM_FP16_SHIFTED = 2 /* FP16 storage of f - w_i, FP32 collision */
+} lbm_precision;
+
+typedef enum { LBM_INIT_REST = 0, LBM_INIT_COUETTE = 1, LBM_INIT_TAYLOR_GREEN = 2 } lbm_init_kind;
+
+/* particle shapes of Sections 3 and 4 */
+typedef enum {
+    LBM_SHAPE_CIRCLE = 0,   /* dim[0] = diameter */
+    LBM_SHAPE_ELLIPSE = 1,  /* dim[0] = major axis, dim[1] = minor axis (full) */
+    LBM_SHAPE_RECT = 2,     /* dim[0] = width (body x), dim[1] = height */
+    LBM_SHAPE_SQUARE = 3,   /* dim[0] = side */
+    LBM_SHAPE_TRIANGLE = 4  /* equilateral, dim[0] = side */
+} lbm_shape;
+
+/* MLS weight functions: Eq. 10 (default) and Eqs. 17-20 */
+typedef enum {
+    LBM_W_EXP = 0, LBM_W_CUBIC = 1, LBM_W_QUARTIC = 2, LBM_W_COSINE = 3, LBM_W_POLY = 4
+} lbm_weight;
+
+typedef struct {
+    int32_t nx, ny;         /* lattice nodes, each >= 3 */
+    double tau;             /* BGK relaxation time, > 0.5; nu = (tau - 1/2)/3 */
+    int32_t bc[4];          /* lbm_bc per side x-, x+, y-, y+; opposite sides equal */
+    double wall_u[4][2];    /* velocity of each wall side (ignored if periodic) */
+    double body_force[2];   /* constant fluid body-force density g_f */
+    double gravity[2];      /* gravity on the particles (buoyancy-corrected) */
+    int32_t precision;      /* lbm_precision */
+    int32_t init;           /* lbm_init_kind; Couette uses wall_u of y- and y+ */
+    double init_u;          /* Taylor-Green amplitude */
+    int32_t weight;         /* lbm_weight */
+    double marker_spacing;  /* target marker spacing; <= 0 means 0.3 */
+    int32_t max_particles;  /* capacity; <= 0 means 16 */
+    int32_t max_markers;    /* total marker capacity; <= 0 means 16384 */
+    void* cuda_stream;      /* cudaStream_t, or NULL */
+    void* d_workspace;      /* caller-owned device memory, or NULL to allocate */
+    size_t workspace_bytes; /* size of d_workspace */
+} lbm_config;
+
+typedef struct {
+    int32_t shape;          /* lbm_shape */
+    double dim[2];          /* see lbm_shape */
+    double xc, yc, theta;   /* centroid and orientation of the body x axis */
+    double rho_s;           /* solid density (fluid reference density is 1) */
+    double u0[2], omega0;   /* initial velocity and angular velocity */
+    int32_t n_markers;      /* 0: perimeter / marker_spacing */
+} lbm_particle_desc;
+
+typedef struct {
+    double xc, yc, theta;   /* centroid (unwrapped in periodic x) and angle */
+    double u[2], omega;     /* velocity and angular velocity */
+    double F[2], M;         /* hydrodynamic force and torque of the last step */
+} lbm_particle_state;
+
+/*
+ * Device bytes the context needs for cfg (sizes, precision and capacities).
+ * A caller that owns device memory (e.g. a PyTorch tensor) passes a block of
+ * at least this size in cfg.d_workspace; the library then allocates nothing
+ * on the device.  Returns LBM_EINVAL for an invalid configuration.
+ */
+lbm_status lbm_workspace_bytes(const lbm_config* cfg, size_t* bytes);
+
+/*
+ * Create a context and its initial field f* = f^eq(rho, u0) (Eq. 2): rest,
+ * the planar Couette profile between the y walls (Section 4.1) or a
+ * Taylor-Green vortex.  Errors: LBM_EINVAL (tau <= 0.5, nx or ny < 3,
+ * opposite sides of different kinds, bad capacities), LBM_ENOMEM (workspace
+ * too small, or cudaMalloc failed when d_workspace is NULL), LBM_ECUDA.
+ * On success *out owns host state only; device memory is the caller's
+ * workspace or library-allocated and freed by lbm_destroy.
+ */
+lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out);
+
+/*
+ * Add a rigid particle before the first step (Sections 3-4).  Markers are
+ * placed at the midpoints of equal arc-length pieces of the perimeter
+ * (polygons: per face), with S_l the piece length and the outward normal.
+ * Errors: LBM_EINVAL (after the first step, bad shape or size, capacity
+ * exceeded, or a marker/probe support crossing a wall).  *out_id receives
+ * the particle index.  Copies the markers host -> device and synchronises.
+ */
+lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* desc, int32_t* out_id);
+
+/*
+ * Advance nsteps >= 0 time steps (the five stages above per step),
+ * asynchronously on the context's stream.  Errors detected on the device
+ * (a support crossing a wall: LBM_EDOMAIN) are reported by the next
+ * lbm_sync / lbm_get_* call.
+ */
+lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps);
+
+/*
+ * As lbm_step, with CUDA events around each step and around its fused
+ * stream-collide launch.  Synchronises; adds the summed device time of
+ * the steps (ms) to *ms_step and of the stream-collide launches to
+ * *ms_fluid (either may be NULL).
+ */
+lbm_status lbm_step_timed(lbm_ctx* ctx, int32_t nsteps, double* ms_step, double* ms_fluid);
+
+/* Wait for the stream; report a device-side error flagged since init. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/*
+ * Density and velocity (host, nx*ny doubles each, y-major) of the
+ * populations after streaming of the stored state, i.e. the moments of
+ * Eqs. 6-7 at the start of the next step (constant body force with its
+ * half step, no immersed-boundary force).  Any pointer may be NULL.
+ */
+lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* ux, double* uy);
+
+/* Stored post-collision populations f* (host, [9][ny][nx] doubles). */
+lbm_status lbm_get_populations(lbm_ctx* ctx, double* f);
+/* Replace the stored post-collision populations (host, [9][ny][nx]). */
+lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f);
+
+/* Particle states (host); *n receives the particle count. */
+lbm_status lbm_get_particles(lbm_ctx* ctx, lbm_particle_state* out, int32_t cap, int32_t* n);
+
+/* Steps done since lbm_init. */
+int64_t lbm_steps_done(const lbm_ctx* ctx);
+
+/* One-line reason for the last error on ctx (never NULL). */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Free the context (and the device memory it allocated itself). */
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

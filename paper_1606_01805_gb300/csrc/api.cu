@@ -1,0 +1,453 @@
+// api.cu -- host side of the C ABI declared in include/lbib.h: configuration
+// checks, the device workspace layout, particle set-up and the per-step
+// launch sequence (particles -> spreading -> fused fluid step).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_fp16.h>
+
+#include "lbib_internal.h"
+
+using namespace lbib;
+
+struct lbm_ctx {
+    lbm_config cfg;
+    Geo G;
+    int prec;
+    size_t sb, cb;            // bytes per stored / computed element
+    cudaStream_t stream;
+    void* ws = nullptr;
+    bool owns_ws = false;
+    void* f[2];
+    int cur = 0;
+    void* flb;
+    uint8_t* flags;
+    DParticle* parts;
+    double2* rb;
+    double2* nb;
+    double* S;
+    void* recs;
+    int4* boxes;
+    unsigned* err;
+    double* scratch;
+    int scratch_rows;
+    int np = 0, nmark = 0;
+    double rc_max = 0;
+    int64_t steps = 0;
+    std::vector<DParticle> hparts;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    std::string msg;
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+size_t up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+    size_t f0, f1, flb, flags, parts, rb, nb, S, recs, boxes, err, scratch, total;
+    int pitch, nseg, scratch_rows;
+};
+
+int cap_particles(const lbm_config& c) { return c.max_particles > 0 ? c.max_particles : 16; }
+int cap_markers(const lbm_config& c) { return c.max_markers > 0 ? c.max_markers : 16384; }
+
+const char* check_config(const lbm_config* c) {
+    if (!c) return "null configuration";
+    if (c->nx < 3 || c->ny < 3) return "nx and ny must be >= 3";
+    if (!(c->tau > 0.5)) return "tau must exceed 1/2";
+    for (int i = 0; i < 4; ++i)
+        if (c->bc[i] != LBM_BC_PERIODIC && c->bc[i] != LBM_BC_VELOCITY) return "unknown side kind";
+    if ((c->bc[0] == LBM_BC_PERIODIC) != (c->bc[1] == LBM_BC_PERIODIC)) return "x sides differ";
+    if ((c->bc[2] == LBM_BC_PERIODIC) != (c->bc[3] == LBM_BC_PERIODIC)) return "y sides differ";
+    if (c->precision < LBM_FP64 || c->precision > LBM_FP16_SHIFTED) return "unknown precision";
+    if (c->init < LBM_INIT_REST || c->init > LBM_INIT_TAYLOR_GREEN) return "unknown init";
+    if (c->weight < LBM_W_EXP || c->weight > LBM_W_POLY) return "unknown weight";
+    if (c->init == LBM_INIT_COUETTE && c->bc[2] != LBM_BC_VELOCITY) return "Couette needs y walls";
+    if ((long long)c->nx * c->ny > (1LL << 40)) return "lattice too large";
+    return nullptr;
+}
+
+Layout layout(const lbm_config& c) {
+    Layout L;
+    const int prec = c.precision;
+    L.pitch = (c.nx + 31) / 32 * 32;
+    L.nseg = L.pitch / 32;
+    const size_t plane = (size_t)L.pitch * c.ny;
+    const size_t P = cap_particles(c), M = cap_markers(c);
+    // rows of FP64 field output staged per lbm_get_fields chunk (<= 24 MB)
+    L.scratch_rows = (int)std::max<size_t>(1, std::min<size_t>(c.ny, (size_t)(1u << 20) / c.nx));
+    size_t o = 0;
+    L.f0 = o; o = up(o + 9 * plane * storage_bytes(prec));
+    L.f1 = o; o = up(o + 9 * plane * storage_bytes(prec));
+    L.flb = o; o = up(o + 2 * plane * compute_bytes(prec));
+    L.flags = o; o = up(o + (size_t)c.ny * L.nseg);
+    L.parts = o; o = up(o + P * sizeof(DParticle));
+    L.rb = o; o = up(o + M * sizeof(double2));
+    L.nb = o; o = up(o + M * sizeof(double2));
+    L.S = o; o = up(o + M * sizeof(double));
+    L.recs = o; o = up(o + M * rec_bytes(prec));
+    L.boxes = o; o = up(o + P * sizeof(int4));
+    L.err = o; o = up(o + 16);
+    L.scratch = o; o = up(o + 3 * (size_t)L.scratch_rows * c.nx * sizeof(double));
+    L.total = o;
+    return L;
+}
+
+lbm_status fail(lbm_ctx* ctx, lbm_status s, const std::string& m) {
+    if (ctx) ctx->msg = m;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx* ctx, cudaError_t e, const char* where) {
+    return fail(ctx, LBM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                             \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+lbm_status device_error(lbm_ctx* ctx) {
+    unsigned e = 0;
+    CK(cudaMemcpyAsync(&e, ctx->err, sizeof e, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (e & ERR_DOMAIN) return fail(ctx, LBM_EDOMAIN, "a marker or probe support crossed a wall");
+    if (e & ERR_NONFINITE) return fail(ctx, LBM_ENONFINITE, "non-finite particle state");
+    if (e & ERR_TIMEOUT) return fail(ctx, LBM_ETIMEOUT, "a device wait expired");
+    return LBM_OK;
+}
+
+// one time step: particles (probes, rigid update, markers) -> spreading -> fluid
+lbm_status enqueue_step(lbm_ctx* ctx, cudaEvent_t mid) {
+    const void* fcur = ctx->f[ctx->cur];
+    if (ctx->np > 0) {
+        ParticleArgs pa;
+        pa.f = fcur;
+        pa.G = ctx->G;
+        pa.parts = ctx->parts;
+        pa.rb = ctx->rb;
+        pa.nb = ctx->nb;
+        pa.S = ctx->S;
+        pa.recs = ctx->recs;
+        pa.boxes = ctx->boxes;
+        pa.err = ctx->err;
+        pa.gravity[0] = ctx->cfg.gravity[0];
+        pa.gravity[1] = ctx->cfg.gravity[1];
+        pa.weight = ctx->cfg.weight;
+        CK(launch_particles(ctx->prec, pa, ctx->np, ctx->stream));
+        SpreadArgs sa;
+        sa.G = ctx->G;
+        sa.parts = ctx->parts;
+        sa.recs = ctx->recs;
+        sa.boxes = ctx->boxes;
+        sa.flb = ctx->flb;
+        sa.flags = ctx->flags;
+        sa.err = ctx->err;
+        const int t = (int)std::ceil((2.0 * ctx->rc_max + 4.0) / 16.0) + 1;
+        CK(launch_spread(ctx->prec, sa, ctx->np, t * t, ctx->stream));
+    }
+    if (mid) CK(cudaEventRecord(mid, ctx->stream));
+    FluidArgs fa;
+    fa.fin = fcur;
+    fa.fout = ctx->f[ctx->cur ^ 1];
+    fa.flb = ctx->flb;
+    fa.flags = ctx->flags;
+    fa.G = ctx->G;
+    CK(launch_fluid(ctx->prec, fa, ctx->stream));
+    ctx->cur ^= 1;
+    ctx->steps += 1;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_workspace_bytes(const lbm_config* cfg, size_t* bytes) {
+    if (const char* why = check_config(cfg)) {
+        (void)why;
+        return LBM_EINVAL;
+    }
+    if (!bytes) return LBM_EINVAL;
+    *bytes = layout(*cfg).total;
+    return LBM_OK;
+}
+
+lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    if (check_config(cfg)) return LBM_EINVAL;
+    const Layout L = layout(*cfg);
+    lbm_ctx* ctx = new lbm_ctx();
+    ctx->cfg = *cfg;
+    ctx->prec = cfg->precision;
+    ctx->sb = storage_bytes(ctx->prec);
+    ctx->cb = compute_bytes(ctx->prec);
+    ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    if (cfg->d_workspace) {
+        if (cfg->workspace_bytes < L.total) {
+            delete ctx;
+            return LBM_ENOMEM;
+        }
+        ctx->ws = cfg->d_workspace;
+    } else {
+        if (cudaMalloc(&ctx->ws, L.total) != cudaSuccess) {
+            delete ctx;
+            return LBM_ENOMEM;
+        }
+        ctx->owns_ws = true;
+    }
+    char* b = static_cast<char*>(ctx->ws);
+    ctx->f[0] = b + L.f0;
+    ctx->f[1] = b + L.f1;
+    ctx->flb = b + L.flb;
+    ctx->flags = reinterpret_cast<uint8_t*>(b + L.flags);
+    ctx->parts = reinterpret_cast<DParticle*>(b + L.parts);
+    ctx->rb = reinterpret_cast<double2*>(b + L.rb);
+    ctx->nb = reinterpret_cast<double2*>(b + L.nb);
+    ctx->S = reinterpret_cast<double*>(b + L.S);
+    ctx->recs = b + L.recs;
+    ctx->boxes = reinterpret_cast<int4*>(b + L.boxes);
+    ctx->err = reinterpret_cast<unsigned*>(b + L.err);
+    ctx->scratch = reinterpret_cast<double*>(b + L.scratch);
+    ctx->scratch_rows = L.scratch_rows;
+    Geo& G = ctx->G;
+    G.nx = cfg->nx;
+    G.ny = cfg->ny;
+    G.pitch = L.pitch;
+    G.nseg = L.nseg;
+    G.plane = (long long)L.pitch * cfg->ny;
+    G.px = cfg->bc[0] == LBM_BC_PERIODIC;
+    G.py = cfg->bc[2] == LBM_BC_PERIODIC;
+    for (int i = 0; i < 4; ++i) {
+        G.uw[i][0] = cfg->wall_u[i][0];
+        G.uw[i][1] = cfg->wall_u[i][1];
+    }
+    G.g[0] = cfg->body_force[0];
+    G.g[1] = cfg->body_force[1];
+    G.tau = cfg->tau;
+    // zero everything (padding columns, force field, flags, error word)
+    cudaError_t e = cudaMemsetAsync(ctx->ws, 0, L.total, ctx->stream);
+    if (e == cudaSuccess) e = launch_init(ctx->prec, ctx->f[0], G, cfg->init, cfg->init_u, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        if (ctx->owns_ws) cudaFree(ctx->ws);
+        delete ctx;
+        return LBM_ECUDA;
+    }
+    *out = ctx;
+    return LBM_OK;
+}
+
+lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* d, int32_t* out_id) {
+    if (!ctx || !d) return LBM_EINVAL;
+    if (ctx->steps > 0) return fail(ctx, LBM_EINVAL, "particles must be added before the first step");
+    if (ctx->np >= cap_particles(ctx->cfg)) return fail(ctx, LBM_EINVAL, "particle capacity exceeded");
+    if (d->shape < LBM_SHAPE_CIRCLE || d->shape > LBM_SHAPE_TRIANGLE || !(d->dim[0] > 0) ||
+        !(d->rho_s > 0))
+        return fail(ctx, LBM_EINVAL, "bad particle shape, size or density");
+    if ((d->shape == LBM_SHAPE_ELLIPSE || d->shape == LBM_SHAPE_RECT) && !(d->dim[1] > 0))
+        return fail(ctx, LBM_EINVAL, "shape needs two dimensions");
+    const int room = cap_markers(ctx->cfg) - ctx->nmark;
+    std::vector<double> rb(2 * (size_t)room + 2), nb(2 * (size_t)room + 2), S((size_t)room + 1);
+    ShapeOut so;
+    if (make_shape(*d, ctx->cfg.marker_spacing, rb.data(), nb.data(), S.data(), room, &so) < 0)
+        return fail(ctx, LBM_EINVAL, "marker capacity exceeded");
+    const int n = so.n;
+    // every marker and probe support must stay inside the walls
+    const double c = std::cos(d->theta), s = std::sin(d->theta);
+    for (int l = 0; l < n; ++l) {
+        const double x = d->xc + c * rb[2 * l] - s * rb[2 * l + 1];
+        const double y = d->yc + s * rb[2 * l] + c * rb[2 * l + 1];
+        const double nx = c * nb[2 * l] - s * nb[2 * l + 1], ny = s * nb[2 * l] + c * nb[2 * l + 1];
+        for (int pass = 0; pass < 2; ++pass) {
+            const double px = x + pass * 1.2 * nx, py = y + pass * 1.2 * ny;
+            const int i0 = (int)std::floor(px + 0.5), j0 = (int)std::floor(py + 0.5);
+            if (!ctx->G.px && (i0 - 1 < 0 || i0 + 1 > ctx->G.nx - 1))
+                return fail(ctx, LBM_EINVAL, "particle support crosses an x wall");
+            if (!ctx->G.py && (j0 - 1 < 0 || j0 + 1 > ctx->G.ny - 1))
+                return fail(ctx, LBM_EINVAL, "particle support crosses a y wall");
+        }
+    }
+    DParticle P;
+    std::memset(&P, 0, sizeof P);
+    for (int h = 0; h < 2; ++h) {
+        P.X[h][0] = d->xc;
+        P.X[h][1] = d->yc;
+        P.th[h] = d->theta;
+        P.U[h][0] = d->u0[0];
+        P.U[h][1] = d->u0[1];
+        P.W[h] = d->omega0;
+    }
+    P.area = so.area;
+    P.rho_s = d->rho_s;
+    P.mass = d->rho_s * so.area;
+    P.inertia = P.mass * so.inertia_per_mass;
+    P.m0 = ctx->nmark;
+    P.nm = n;
+    std::vector<double2> r2(n), n2(n);
+    for (int l = 0; l < n; ++l) {
+        r2[l] = make_double2(rb[2 * l], rb[2 * l + 1]);
+        n2[l] = make_double2(nb[2 * l], nb[2 * l + 1]);
+    }
+    CK(cudaMemcpyAsync(ctx->rb + P.m0, r2.data(), n * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->nb + P.m0, n2.data(), n * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->S + P.m0, S.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->parts + ctx->np, &P, sizeof P, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->hparts.push_back(P);
+    ctx->rc_max = std::max(ctx->rc_max, so.rcirc);
+    ctx->nmark += n;
+    if (out_id) *out_id = ctx->np;
+    ctx->np += 1;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps) {
+    if (!ctx || nsteps < 0) return LBM_EINVAL;
+    for (int32_t k = 0; k < nsteps; ++k) {
+        lbm_status s = enqueue_step(ctx, nullptr);
+        if (s != LBM_OK) return s;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_step_timed(lbm_ctx* ctx, int32_t nsteps, double* ms_step, double* ms_fluid) {
+    if (!ctx || nsteps < 0) return LBM_EINVAL;
+    for (auto& e : ctx->ev)
+        if (!e) CK(cudaEventCreate(&e));
+    double tot = 0, flu = 0;
+    for (int32_t k = 0; k < nsteps; ++k) {
+        CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+        lbm_status s = enqueue_step(ctx, ctx->ev[1]);
+        if (s != LBM_OK) return s;
+        CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+        CK(cudaEventSynchronize(ctx->ev[2]));
+        float a = 0, b = 0;
+        CK(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[2]));
+        CK(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]));
+        tot += a;
+        flu += b;
+    }
+    if (ms_step) *ms_step += tot;
+    if (ms_fluid) *ms_fluid += flu;
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx* ctx) {
+    if (!ctx) return LBM_EINVAL;
+    return device_error(ctx);
+}
+
+lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* ux, double* uy) {
+    if (!ctx) return LBM_EINVAL;
+    lbm_status s = device_error(ctx);
+    if (s != LBM_OK) return s;
+    const int nx = ctx->G.nx, ny = ctx->G.ny;
+    const size_t chunk = (size_t)ctx->scratch_rows * nx;
+    for (int y0 = 0; y0 < ny; y0 += ctx->scratch_rows) {
+        const int rows = std::min(ctx->scratch_rows, ny - y0);
+        FieldArgs fa;
+        fa.f = ctx->f[ctx->cur];
+        fa.G = ctx->G;
+        fa.y0 = y0;
+        fa.rows = rows;
+        fa.rho = ctx->scratch;
+        fa.ux = ctx->scratch + chunk;
+        fa.uy = ctx->scratch + 2 * chunk;
+        CK(launch_fields(ctx->prec, fa, ctx->stream));
+        const size_t n = (size_t)rows * nx, off = (size_t)y0 * nx;
+        if (rho) CK(cudaMemcpyAsync(rho + off, fa.rho, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        if (ux) CK(cudaMemcpyAsync(ux + off, fa.ux, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        if (uy) CK(cudaMemcpyAsync(uy + off, fa.uy, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx* ctx, double* f) {
+    if (!ctx || !f) return LBM_EINVAL;
+    const int nx = ctx->G.nx, ny = ctx->G.ny, pitch = ctx->G.pitch;
+    const size_t n = 9 * (size_t)ctx->G.plane;
+    std::vector<unsigned char> h(n * ctx->sb);
+    CK(cudaMemcpyAsync(h.data(), ctx->f[ctx->cur], h.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < 9; ++i) {
+        const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const size_t k = (size_t)i * ctx->G.plane + (size_t)y * pitch + x;
+                double v;
+                if (ctx->prec == LBM_FP64) v = reinterpret_cast<double*>(h.data())[k];
+                else if (ctx->prec == LBM_FP32) v = reinterpret_cast<float*>(h.data())[k];
+                else v = __half2float(reinterpret_cast<__half*>(h.data())[k]);
+                f[((size_t)i * ny + y) * nx + x] = v + w;
+            }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f) {
+    if (!ctx || !f) return LBM_EINVAL;
+    const int nx = ctx->G.nx, ny = ctx->G.ny, pitch = ctx->G.pitch;
+    const size_t n = 9 * (size_t)ctx->G.plane;
+    std::vector<unsigned char> h(n * ctx->sb, 0);
+    for (int i = 0; i < 9; ++i) {
+        const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const size_t k = (size_t)i * ctx->G.plane + (size_t)y * pitch + x;
+                const double v = f[((size_t)i * ny + y) * nx + x] - w;
+                if (ctx->prec == LBM_FP64) reinterpret_cast<double*>(h.data())[k] = v;
+                else if (ctx->prec == LBM_FP32) reinterpret_cast<float*>(h.data())[k] = (float)v;
+                else reinterpret_cast<__half*>(h.data())[k] = __float2half_rn((float)v);
+            }
+    }
+    CK(cudaMemcpyAsync(ctx->f[ctx->cur], h.data(), h.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_particles(lbm_ctx* ctx, lbm_particle_state* out, int32_t cap, int32_t* n) {
+    if (!ctx) return LBM_EINVAL;
+    lbm_status s = device_error(ctx);
+    if (s != LBM_OK && s != LBM_EDOMAIN) return s;
+    if (n) *n = ctx->np;
+    if (ctx->np == 0 || !out || cap <= 0) return s;
+    std::vector<DParticle> h(ctx->np);
+    CK(cudaMemcpyAsync(h.data(), ctx->parts, ctx->np * sizeof(DParticle), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < std::min<int>(cap, ctx->np); ++i) {
+        out[i].xc = h[i].X[0][0];
+        out[i].yc = h[i].X[0][1];
+        out[i].theta = h[i].th[0];
+        out[i].u[0] = h[i].U[0][0];
+        out[i].u[1] = h[i].U[0][1];
+        out[i].omega = h[i].W[0];
+        out[i].F[0] = h[i].F[0];
+        out[i].F[1] = h[i].F[1];
+        out[i].M = h[i].M;
+    }
+    return s;
+}
+
+int64_t lbm_steps_done(const lbm_ctx* ctx) { return ctx ? ctx->steps : 0; }
+
+const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->msg.c_str() : "null context"; }
+
+void lbm_destroy(lbm_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->owns_ws) cudaFree(ctx->ws);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,221 @@
+"""ctypes binding of the C ABI in ``include/lbib.h`` (liblbib.so).
+
+Argument marshalling only: every stage of the LB-IB step runs in the CUDA
+kernels of the library.  PyTorch supplies the device workspace (through its
+caching allocator) and the CUDA stream.  Importing this module does not need
+a GPU; creating a :class:`Simulation` does, and fails loudly if the library
+has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from pathlib import Path
+
+import numpy as np
+
+PKG = Path(__file__).resolve().parent
+LIB_PATH = PKG / "liblbib.so"
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_ENONFINITE, LBM_EINTERNAL, LBM_EDOMAIN = range(8)
+STATUS_NAMES = ["LBM_OK", "LBM_EINVAL", "LBM_ENOMEM", "LBM_ECUDA", "LBM_ETIMEOUT",
+                "LBM_ENONFINITE", "LBM_EINTERNAL", "LBM_EDOMAIN"]
+LBM_BC_PERIODIC, LBM_BC_VELOCITY = 0, 1
+LBM_FP64, LBM_FP32, LBM_FP16_SHIFTED = 0, 1, 2
+LBM_INIT_REST, LBM_INIT_COUETTE, LBM_INIT_TAYLOR_GREEN = 0, 1, 2
+LBM_SHAPE_CIRCLE, LBM_SHAPE_ELLIPSE, LBM_SHAPE_RECT, LBM_SHAPE_SQUARE, LBM_SHAPE_TRIANGLE = range(5)
+LBM_W_EXP, LBM_W_CUBIC, LBM_W_QUARTIC, LBM_W_COSINE, LBM_W_POLY = range(5)
+
+# every symbol include/lbib.h declares
+EXPORTS = ["lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "lbm_step_timed",
+           "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
+           "lbm_get_particles", "lbm_steps_done", "lbm_last_error", "lbm_destroy"]
+
+
+class lbm_config(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("tau", C.c_double),
+        ("bc", C.c_int32 * 4), ("wall_u", (C.c_double * 2) * 4),
+        ("body_force", C.c_double * 2), ("gravity", C.c_double * 2),
+        ("precision", C.c_int32), ("init", C.c_int32), ("init_u", C.c_double),
+        ("weight", C.c_int32), ("marker_spacing", C.c_double),
+        ("max_particles", C.c_int32), ("max_markers", C.c_int32),
+        ("cuda_stream", C.c_void_p), ("d_workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
+    ]
+
+
+class lbm_particle_desc(C.Structure):
+    _fields_ = [
+        ("shape", C.c_int32), ("dim", C.c_double * 2), ("xc", C.c_double), ("yc", C.c_double),
+        ("theta", C.c_double), ("rho_s", C.c_double), ("u0", C.c_double * 2),
+        ("omega0", C.c_double), ("n_markers", C.c_int32),
+    ]
+
+
+class lbm_particle_state(C.Structure):
+    _fields_ = [
+        ("xc", C.c_double), ("yc", C.c_double), ("theta", C.c_double), ("u", C.c_double * 2),
+        ("omega", C.c_double), ("F", C.c_double * 2), ("M", C.c_double),
+    ]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {what}")
+        self.status = status
+
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+
+
+def load(path: os.PathLike | str | None = None):
+    """Load liblbib.so (built by ``paper_1606_01805_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        raise RuntimeError(f"{p} is missing: build it with `python -m paper_1606_01805_gb300.build`")
+    L = C.CDLL(str(p))
+    L.lbm_workspace_bytes.argtypes = [C.POINTER(lbm_config), C.POINTER(C.c_size_t)]
+    L.lbm_init.argtypes = [C.POINTER(lbm_config), C.POINTER(C.c_void_p)]
+    L.lbm_add_particle.argtypes = [C.c_void_p, C.POINTER(lbm_particle_desc), C.POINTER(C.c_int32)]
+    L.lbm_step.argtypes = [C.c_void_p, C.c_int32]
+    L.lbm_step_timed.argtypes = [C.c_void_p, C.c_int32, _dp, _dp]
+    L.lbm_sync.argtypes = [C.c_void_p]
+    L.lbm_get_fields.argtypes = [C.c_void_p, _dp, _dp, _dp]
+    L.lbm_get_populations.argtypes = [C.c_void_p, _dp]
+    L.lbm_set_populations.argtypes = [C.c_void_p, _dp]
+    L.lbm_get_particles.argtypes = [C.c_void_p, C.POINTER(lbm_particle_state), C.c_int32,
+                                    C.POINTER(C.c_int32)]
+    L.lbm_steps_done.restype = C.c_int64
+    L.lbm_steps_done.argtypes = [C.c_void_p]
+    L.lbm_last_error.restype = C.c_char_p
+    L.lbm_last_error.argtypes = [C.c_void_p]
+    L.lbm_destroy.argtypes = [C.c_void_p]
+    L.lbm_destroy.restype = None
+    for fn in ("lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "lbm_step_timed",
+               "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
+               "lbm_get_particles"):
+        getattr(L, fn).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def make_config(nx, ny, tau, bc=(0, 0, 1, 1), wall_u=((0, 0),) * 4, body_force=(0, 0),
+                gravity=(0, 0), precision=LBM_FP32, init=LBM_INIT_REST, init_u=0.0,
+                weight=LBM_W_EXP, marker_spacing=0.3, max_particles=16, max_markers=16384):
+    c = lbm_config()
+    c.nx, c.ny, c.tau = nx, ny, tau
+    for i in range(4):
+        c.bc[i] = bc[i]
+        c.wall_u[i][0], c.wall_u[i][1] = wall_u[i]
+    c.body_force[0], c.body_force[1] = body_force
+    c.gravity[0], c.gravity[1] = gravity
+    c.precision, c.init, c.init_u = precision, init, init_u
+    c.weight, c.marker_spacing = weight, marker_spacing
+    c.max_particles, c.max_markers = max_particles, max_markers
+    return c
+
+
+class Simulation:
+    """One LB-IB lattice on the current CUDA device.
+
+    The device workspace is a torch uint8 tensor; the stream is torch's
+    current stream (or the one given)."""
+
+    def __init__(self, nx, ny, tau, stream=None, **kw):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        L = load()
+        self.cfg = make_config(nx, ny, tau, **kw)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.cfg.cuda_stream = C.c_void_p(self.stream.cuda_stream)
+        nbytes = C.c_size_t()
+        self._check(L.lbm_workspace_bytes(C.byref(self.cfg), C.byref(nbytes)), "workspace size")
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+        self.cfg.d_workspace = C.c_void_p(self.workspace.data_ptr())
+        self.cfg.workspace_bytes = nbytes.value
+        h = C.c_void_p()
+        self._check(L.lbm_init(C.byref(self.cfg), C.byref(h)), "lbm_init")
+        self._h = h
+        self.nx, self.ny = nx, ny
+        self.np = 0
+
+    def _check(self, rc, what):
+        if rc != LBM_OK:
+            msg = load().lbm_last_error(self._h).decode() if getattr(self, "_h", None) else what
+            raise LbmError(rc, msg or what)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_particle(self, shape, dim, xc, yc, theta=0.0, rho_s=1.0, u0=(0.0, 0.0), omega0=0.0,
+                     n_markers=0):
+        d = lbm_particle_desc()
+        d.shape = shape
+        d.dim[0] = dim[0]
+        d.dim[1] = dim[1] if len(dim) > 1 else 0.0
+        d.xc, d.yc, d.theta, d.rho_s = xc, yc, theta, rho_s
+        d.u0[0], d.u0[1] = u0
+        d.omega0, d.n_markers = omega0, n_markers
+        pid = C.c_int32()
+        self._check(load().lbm_add_particle(self._h, C.byref(d), C.byref(pid)), "lbm_add_particle")
+        self.np += 1
+        return pid.value
+
+    def step(self, n=1):
+        self._check(load().lbm_step(self._h, n), "lbm_step")
+
+    def step_timed(self, n=1):
+        ms_step, ms_fluid = C.c_double(0), C.c_double(0)
+        self._check(load().lbm_step_timed(self._h, n, C.byref(ms_step), C.byref(ms_fluid)),
+                    "lbm_step_timed")
+        return ms_step.value, ms_fluid.value
+
+    def sync(self):
+        self._check(load().lbm_sync(self._h), "lbm_sync")
+
+    @property
+    def steps_done(self):
+        return load().lbm_steps_done(self._h)
+
+    def fields(self):
+        r = np.empty((self.ny, self.nx))
+        ux = np.empty_like(r)
+        uy = np.empty_like(r)
+        self._check(load().lbm_get_fields(self._h, _ptr(r), _ptr(ux), _ptr(uy)), "lbm_get_fields")
+        return r, ux, uy
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        self._check(load().lbm_get_populations(self._h, _ptr(f)), "lbm_get_populations")
+        return f
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, np.float64)
+        assert f.shape == (9, self.ny, self.nx)
+        self._check(load().lbm_set_populations(self._h, _ptr(f)), "lbm_set_populations")
+
+    def particles(self):
+        n = max(self.np, 1)
+        arr = (lbm_particle_state * n)()
+        cnt = C.c_int32()
+        self._check(load().lbm_get_particles(self._h, arr, n, C.byref(cnt)), "lbm_get_particles")
+        return [dict(xc=p.xc, yc=p.yc, theta=p.theta, u=(p.u[0], p.u[1]), omega=p.omega,
+                     F=(p.F[0], p.F[1]), M=p.M) for p in arr[: cnt.value]]

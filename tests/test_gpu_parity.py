@@ -1,0 +1,224 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs (element by element on small ragged lattices, on the
+velocity field and particle state for the paper-shaped workloads)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as o
+from paper_1606_01805_gb300 import lbib
+from paper_1606_01805_gb300 import workloads as W
+
+from ._parity import FP32, FP64, gpu_factory, oracle_factory, particle_errs, rest_populations, \
+    run_pair, vel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # collected only with -m gpu on a GPU machine
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1606_01805_gb300 import build
+
+    build.build()
+    lbib.load()
+
+
+LATTICES = {
+    # 67 x 45: ragged against the 32 x 8 blocks of the fluid kernel
+    "channel": dict(bc=(0, 0, 1, 1), wall_u=((0, 0), (0, 0), (-0.01, 0.002), (0.012, -0.001)),
+                    body_force=(2e-6, -1e-6)),
+    "box": dict(bc=(1, 1, 1, 1), wall_u=((0, 0.003), (0, -0.004), (0.005, 0), (-0.008, 0)),
+                body_force=(1e-6, 2e-6)),
+    "periodic": dict(bc=(0, 0, 0, 0), body_force=(3e-6, 0.0)),
+    "ychannel": dict(bc=(1, 1, 0, 0), wall_u=((0, 0.01), (0, -0.01), (0, 0), (0, 0))),
+}
+
+
+@pytest.mark.parametrize("prec,atol", [(FP64, 1e-14), (FP32, 1e-7)])
+@pytest.mark.parametrize("kind", sorted(LATTICES))
+@pytest.mark.parametrize("size", [(67, 45), (3, 3), (32, 8)])
+def test_fluid_populations_elementwise(kind, prec, atol, size):
+    nx, ny = size
+    wl = W.Workload(f"fluid_{kind}", nx, ny, 0.63, steps=12, **LATTICES[kind])
+    f0 = W.random_populations(nx, ny, seed=11, base=rest_populations())
+    ref, gpu = run_pair(wl, prec, populations=f0)
+    np.testing.assert_allclose(gpu.populations(), ref.populations(), rtol=0, atol=atol)
+    for a, b in zip(gpu.fields(), ref.fields()):
+        np.testing.assert_allclose(a, b, rtol=0, atol=10 * atol)
+
+
+def _coupled(kind, shape, dim, xc, yc, theta=0.3, rho_s=1.2, u0=(0.002, -0.001), omega0=0.0004,
+             n=0):
+    wl = W.Workload(f"coupled_{kind}", 67, 45, 0.7, steps=25, gravity=(1e-6, -2e-6),
+                    **LATTICES[kind])
+    wl.particles = [W.Particle(shape, dim, xc, yc, theta=theta, rho_s=rho_s, u0=u0, omega0=omega0,
+                               n_markers=n)]
+    return wl
+
+
+COUPLED = [
+    ("channel", W.CIRCLE, (12.0,), 30.3, 22.1, 48),
+    ("channel", W.ELLIPSE, (14.0, 7.0), 40.2, 20.7, 0),
+    ("box", W.RECT, (12.0, 5.0), 33.0, 21.5, 0),
+    ("periodic", W.TRIANGLE, (11.0,), 2.5, 43.6, 0),   # straddles both periodic edges
+    ("box", W.SQUARE, (9.0,), 50.1, 14.9, 0),
+]
+
+
+@pytest.mark.parametrize("case", COUPLED, ids=[f"{c[0]}-{c[1]}" for c in COUPLED])
+def test_coupled_step_fp64_elementwise(case):
+    kind, shape, dim, xc, yc, n = case
+    wl = _coupled(kind, shape, dim, xc, yc, n=n)
+    f0 = W.random_populations(67, 45, seed=5, base=rest_populations(), amp=0.005, smooth=0.01)
+    ref, gpu = run_pair(wl, FP64, populations=f0)
+    np.testing.assert_allclose(gpu.populations(), ref.populations(), rtol=0, atol=1e-13)
+    rp, gp = ref.particles()[0], gpu.particles()[0]
+    for key in ("xc", "yc", "theta", "omega", "M"):
+        assert gp[key] == pytest.approx(rp[key], rel=1e-9, abs=1e-13), key
+    for key in ("u", "F"):
+        np.testing.assert_allclose(gp[key], rp[key], rtol=1e-9, atol=1e-13)
+
+
+@pytest.mark.parametrize("case", COUPLED, ids=[f"{c[0]}-{c[1]}" for c in COUPLED])
+def test_coupled_step_fp32(case):
+    kind, shape, dim, xc, yc, n = case
+    wl = _coupled(kind, shape, dim, xc, yc, n=n)
+    f0 = W.random_populations(67, 45, seed=5, base=rest_populations(), amp=0.005, smooth=0.01)
+    ref, gpu = run_pair(wl, FP32, populations=f0)
+    assert vel_err(ref.fields(), gpu.fields()) < 1e-4
+    rp, gp = ref.particles()[0], gpu.particles()[0]
+    dpos, dom = particle_errs(rp, gp, omega_floor=1e-5)
+    assert dpos < 1e-3 and dom < 1e-3
+
+
+@pytest.fixture(scope="module")
+def couette_ref():
+    wl = W.couette_circle(steps=2000)
+    ref = W.run_with(oracle_factory, wl)
+    return wl, ref.fields(), ref.particles()[0]
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_couette_circle_2000_steps(couette_ref, prec):
+    """The plain-method workload (400 x 100 Couette, circle D = 20, 63
+    markers) after 2000 steps: velocity field max-relative error <= 1e-4,
+    centroid within 1e-3 lu, angular velocity within 1e-3 relative."""
+    wl, rf, rp = couette_ref
+    gpu = W.run_with(gpu_factory(prec), wl)
+    err = vel_err(rf, gpu.fields())
+    gp = gpu.particles()[0]
+    U = wl.wall_u[3][0]
+    dpos, dom = particle_errs(rp, gp, omega_floor=1e-3 * U / (wl.ny - 1))
+    if prec == FP64:
+        assert err < 1e-10 and dpos < 1e-9 and dom < 1e-9
+    assert err < 1e-4 and dpos < 1e-3 and dom < 1e-3
+
+
+@pytest.mark.parametrize("shape", ["circle", "ellipse"])
+def test_sedimentation_full_size_fp32(shape):
+    """The sedimentation lattice at full size (400 x 1200 closed box, walls
+    and corners, gravity and buoyancy, density ratio 1.5), FP32 path, first
+    120 steps against the oracle."""
+    wl = W.sedimentation(shape, steps=120)
+    ref, gpu = run_pair(wl, FP32)
+    assert vel_err(ref.fields(), gpu.fields()) < 1e-4
+    dpos, dom = particle_errs(ref.particles()[0], gpu.particles()[0], omega_floor=1e-6)
+    assert dpos < 1e-3 and dom < 1e-3
+    assert gpu.particles()[0]["u"][1] < 0  # it falls
+
+
+@pytest.mark.parametrize("idx", range(5), ids=[W.SHAPE_NAMES[s] for s, _ in W.SHAPE_SET])
+def test_couette_shape_set_fp32(idx):
+    """Each particle of the shape set in the 1024 x 256 Couette channel."""
+    wl = W.couette_shapes(steps=60)[idx]
+    ref, gpu = run_pair(wl, FP32)
+    assert vel_err(ref.fields(), gpu.fields()) < 1e-4
+    U = wl.wall_u[3][0]
+    dpos, dom = particle_errs(ref.particles()[0], gpu.particles()[0],
+                              omega_floor=1e-3 * U / (wl.ny - 1))
+    assert dpos < 1e-3 and dom < 1e-3
+
+
+@pytest.mark.parametrize("weight", [o.W_EXP, o.W_CUBIC, o.W_QUARTIC, o.W_COSINE, o.W_POLY])
+def test_weight_functions_fp64(weight):
+    wl = _coupled("channel", W.ELLIPSE, (14.0, 7.0), 33.4, 22.6).with_(weight=weight, steps=15)
+    ref, gpu = run_pair(wl, FP64)
+    np.testing.assert_allclose(gpu.populations(), ref.populations(), rtol=0, atol=1e-13)
+    assert gpu.particles()[0]["M"] == pytest.approx(ref.particles()[0]["M"], rel=1e-9, abs=1e-14)
+
+
+def test_zero_steps_and_initial_fields():
+    """Before any step both sides hold f^eq of the Couette profile."""
+    wl = W.couette_circle(steps=0)
+    ref, gpu = run_pair(wl, FP64, steps=0)
+    np.testing.assert_allclose(gpu.populations(), ref.populations(), rtol=0, atol=1e-16)
+    gpu.step(0)
+    assert gpu.steps_done == 0
+
+
+def test_taylor_green_fp32():
+    wl = W.Workload("tg", 64, 64, 0.8, bc=(0, 0, 0, 0), init=W.TAYLOR_GREEN, init_u=0.01,
+                    steps=500)
+    ref, gpu = run_pair(wl, FP32)
+    assert vel_err(ref.fields(), gpu.fields()) < 1e-4
+
+
+def test_support_crossing_a_wall_is_reported():
+    """A particle driven into the bottom wall: the oracle stops with a domain
+    error, and the CUDA path reports LBM_EDOMAIN at the next sync (its
+    kernels skip the out-of-domain nodes instead of touching them)."""
+    wl = W.Workload("crash", 64, 40, 0.8, steps=0)
+    wl.particles = [W.Particle(W.CIRCLE, (10.0,), 32.0, 9.0, u0=(0.0, -0.5), n_markers=40)]
+    ref = W.run_with(oracle_factory, wl)
+    with pytest.raises(RuntimeError):
+        ref.step(10)
+    gpu = W.run_with(gpu_factory(FP32), wl)
+    gpu.step(10)
+    with pytest.raises(lbib.LbmError) as ei:
+        gpu.sync()
+    assert ei.value.status == lbib.LBM_EDOMAIN
+
+
+def test_add_particle_validation():
+    sim = lbib.Simulation(64, 40, 0.8, precision=FP32)
+    with pytest.raises(lbib.LbmError):
+        sim.add_particle(W.CIRCLE, (20.0,), 32.0, 11.0)  # support would cross y = 0
+    with pytest.raises(lbib.LbmError):
+        sim.add_particle(W.ELLIPSE, (10.0, 0.0), 32.0, 20.0)
+    sim.add_particle(W.CIRCLE, (10.0,), 32.0, 20.0)
+    sim.step(1)
+    with pytest.raises(lbib.LbmError):
+        sim.add_particle(W.CIRCLE, (10.0,), 20.0, 20.0)  # after the first step
+
+
+def test_large_lattice_couette_stays_linear():
+    """16384 x 4096 FP32 Couette (the bandwidth workload, 4.8 GB of
+    populations): the linear profile is a steady state at any size."""
+    wl = W.large_couette(n_particles=0, steps=30)
+    gpu = W.run_with(gpu_factory(FP32), wl)
+    _, ux, uy = gpu.fields()
+    U = wl.wall_u[3][0]
+    y = np.arange(wl.ny)
+    want = -U + 2 * U * y / (wl.ny - 1)
+    assert np.abs(ux - want[:, None]).max() < 1e-6 * U * 100
+    assert np.abs(uy).max() < 1e-6 * U * 100
+
+
+def test_large_lattice_with_particles_runs_clean():
+    wl = W.large_couette(steps=20)
+    gpu = W.run_with(gpu_factory(FP32), wl)
+    gpu.sync()
+    ps = gpu.particles()
+    assert len(ps) == 64
+    H = wl.ny - 1
+    U = wl.wall_u[3][0]
+    for p, q in zip(ps, wl.particles):
+        assert math.isfinite(p["xc"]) and abs(p["yc"] - q.yc) < 0.1
+        # accelerating toward the local undisturbed velocity
+        ul = -U + 2 * U * q.yc / H
+        assert p["u"][0] * ul >= 0
