@@ -27,6 +27,9 @@ struct lbm_ctx {
     void* flb;
     uint8_t* flags;
     DParticle* parts;
+    int4* blk;
+    double* partial;
+    unsigned* count;
     double2* rb;
     double2* nb;
     double* S;
@@ -35,11 +38,13 @@ struct lbm_ctx {
     unsigned* err;
     double* scratch;
     int scratch_rows;
-    int np = 0, nmark = 0;
+    int np = 0, nmark = 0, nblk = 0;
     double rc_max = 0;
     int64_t steps = 0;
     std::vector<DParticle> hparts;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // GRAPH_STEPS steps from buffer 0 / 1
+    bool graphs_ok = true;
     std::string msg;
 };
 
@@ -49,12 +54,14 @@ constexpr size_t ALIGN = 256;
 size_t up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t f0, f1, flb, flags, parts, rb, nb, S, recs, boxes, err, scratch, total;
+    size_t f0, f1, flb, flags, parts, blk, partial, count, rb, nb, S, recs, boxes, err, scratch, total;
     int pitch, nseg, scratch_rows;
 };
 
 int cap_particles(const lbm_config& c) { return c.max_particles > 0 ? c.max_particles : 16; }
 int cap_markers(const lbm_config& c) { return c.max_markers > 0 ? c.max_markers : 16384; }
+// marker blocks: every particle starts a new block of MB markers
+int cap_blocks(const lbm_config& c) { return cap_markers(c) / MB + cap_particles(c) + 1; }
 
 const char* check_config(const lbm_config* c) {
     if (!c) return "null configuration";
@@ -87,6 +94,10 @@ Layout layout(const lbm_config& c) {
     L.flb = o; o = up(o + 2 * plane * compute_bytes(prec));
     L.flags = o; o = up(o + (size_t)c.ny * L.nseg);
     L.parts = o; o = up(o + P * sizeof(DParticle));
+    const size_t NB = cap_blocks(c);
+    L.blk = o; o = up(o + NB * sizeof(int4));
+    L.partial = o; o = up(o + 3 * NB * sizeof(double));
+    L.count = o; o = up(o + P * sizeof(unsigned));
     L.rb = o; o = up(o + M * sizeof(double2));
     L.nb = o; o = up(o + M * sizeof(double2));
     L.S = o; o = up(o + M * sizeof(double));
@@ -123,14 +134,20 @@ lbm_status device_error(lbm_ctx* ctx) {
     return LBM_OK;
 }
 
-// one time step: particles (probes, rigid update, markers) -> spreading -> fluid
-lbm_status enqueue_step(lbm_ctx* ctx, cudaEvent_t mid) {
-    const void* fcur = ctx->f[ctx->cur];
+constexpr int GRAPH_STEPS = 32;  // even, so a replay returns to the same buffer
+
+// one time step from buffer `cur` on stream `st`: particles (probes, rigid
+// update, markers) -> spreading -> fluid.  Bookkeeping is the caller's.
+lbm_status enqueue_step(lbm_ctx* ctx, cudaStream_t st, int cur, cudaEvent_t mid) {
+    const void* fcur = ctx->f[cur];
     if (ctx->np > 0) {
         ParticleArgs pa;
         pa.f = fcur;
         pa.G = ctx->G;
         pa.parts = ctx->parts;
+        pa.blk = ctx->blk;
+        pa.partial = ctx->partial;
+        pa.count = ctx->count;
         pa.rb = ctx->rb;
         pa.nb = ctx->nb;
         pa.S = ctx->S;
@@ -140,7 +157,8 @@ lbm_status enqueue_step(lbm_ctx* ctx, cudaEvent_t mid) {
         pa.gravity[0] = ctx->cfg.gravity[0];
         pa.gravity[1] = ctx->cfg.gravity[1];
         pa.weight = ctx->cfg.weight;
-        CK(launch_particles(ctx->prec, pa, ctx->np, ctx->stream));
+        CK(launch_probes(ctx->prec, pa, ctx->nblk, st));
+        CK(launch_markers(ctx->prec, pa, ctx->nblk, st));
         SpreadArgs sa;
         sa.G = ctx->G;
         sa.parts = ctx->parts;
@@ -149,20 +167,41 @@ lbm_status enqueue_step(lbm_ctx* ctx, cudaEvent_t mid) {
         sa.flb = ctx->flb;
         sa.flags = ctx->flags;
         sa.err = ctx->err;
-        const int t = (int)std::ceil((2.0 * ctx->rc_max + 4.0) / 16.0) + 1;
-        CK(launch_spread(ctx->prec, sa, ctx->np, t * t, ctx->stream));
+        // tiles of 32 x 16 cells covering the largest support box
+        const double ext = 2.0 * ctx->rc_max + 4.0;
+        const int tiles = ((int)std::ceil(ext / 32.0) + 1) * ((int)std::ceil(ext / 16.0) + 1);
+        CK(launch_spread(ctx->prec, sa, ctx->np, tiles, st));
     }
-    if (mid) CK(cudaEventRecord(mid, ctx->stream));
+    if (mid) CK(cudaEventRecord(mid, st));
     FluidArgs fa;
     fa.fin = fcur;
-    fa.fout = ctx->f[ctx->cur ^ 1];
+    fa.fout = ctx->f[cur ^ 1];
     fa.flb = ctx->flb;
     fa.flags = ctx->flags;
     fa.G = ctx->G;
-    CK(launch_fluid(ctx->prec, fa, ctx->stream));
-    ctx->cur ^= 1;
-    ctx->steps += 1;
+    CK(launch_fluid(ctx->prec, fa, st));
     return LBM_OK;
+}
+
+// Capture GRAPH_STEPS steps starting from buffer `cur` on a private stream
+// (the caller's stream may be the legacy default stream, which cannot be
+// captured).  Returns false if capture is not possible here.
+bool capture_graph(lbm_ctx* ctx, int cur) {
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return false;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        int c = cur;
+        for (int k = 0; k < GRAPH_STEPS && ok; ++k, c ^= 1) ok = enqueue_step(ctx, cs, c, nullptr) == LBM_OK;
+        cudaGraph_t g = nullptr;
+        const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
+        ok = ok && ended && g && cudaGraphInstantiate(&ctx->graph[cur], g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+    }
+    cudaStreamDestroy(cs);
+    cudaGetLastError();  // a failed capture leaves no sticky error
+    if (!ok) ctx->graph[cur] = nullptr;
+    return ok;
 }
 
 }  // namespace
@@ -209,6 +248,9 @@ lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
     ctx->flb = b + L.flb;
     ctx->flags = reinterpret_cast<uint8_t*>(b + L.flags);
     ctx->parts = reinterpret_cast<DParticle*>(b + L.parts);
+    ctx->blk = reinterpret_cast<int4*>(b + L.blk);
+    ctx->partial = reinterpret_cast<double*>(b + L.partial);
+    ctx->count = reinterpret_cast<unsigned*>(b + L.count);
     ctx->rb = reinterpret_cast<double2*>(b + L.rb);
     ctx->nb = reinterpret_cast<double2*>(b + L.nb);
     ctx->S = reinterpret_cast<double*>(b + L.S);
@@ -232,6 +274,14 @@ lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
     G.g[0] = cfg->body_force[0];
     G.g[1] = cfg->body_force[1];
     G.tau = cfg->tau;
+    G.omega = 1.0 / cfg->tau;
+    for (int i = 0; i < 4; ++i) {
+        G.uwf[i][0] = (float)G.uw[i][0];
+        G.uwf[i][1] = (float)G.uw[i][1];
+    }
+    G.gf[0] = (float)G.g[0];
+    G.gf[1] = (float)G.g[1];
+    G.omegaf = (float)G.omega;
     // zero everything (padding columns, force field, flags, error word)
     cudaError_t e = cudaMemsetAsync(ctx->ws, 0, L.total, ctx->stream);
     if (e == cudaSuccess) e = launch_init(ctx->prec, ctx->f[0], G, cfg->init, cfg->init_u, ctx->stream);
@@ -281,6 +331,8 @@ lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* d, int32_t* o
         P.X[h][0] = d->xc;
         P.X[h][1] = d->yc;
         P.th[h] = d->theta;
+        P.cs[h][0] = std::cos(d->theta);
+        P.cs[h][1] = std::sin(d->theta);
         P.U[h][0] = d->u0[0];
         P.U[h][1] = d->u0[1];
         P.W[h] = d->omega0;
@@ -291,6 +343,12 @@ lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* d, int32_t* o
     P.inertia = P.mass * so.inertia_per_mass;
     P.m0 = ctx->nmark;
     P.nm = n;
+    P.b0 = ctx->nblk;
+    P.nblk = (n + MB - 1) / MB;
+    if (P.b0 + P.nblk > cap_blocks(ctx->cfg)) return fail(ctx, LBM_EINVAL, "marker capacity exceeded");
+    std::vector<int4> blocks(P.nblk);
+    for (int k = 0; k < P.nblk; ++k)
+        blocks[k] = make_int4(ctx->np, P.m0 + k * MB, std::min(MB, n - k * MB), 0);
     std::vector<double2> r2(n), n2(n);
     for (int l = 0; l < n; ++l) {
         r2[l] = make_double2(rb[2 * l], rb[2 * l + 1]);
@@ -300,10 +358,13 @@ lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* d, int32_t* o
     CK(cudaMemcpyAsync(ctx->nb + P.m0, n2.data(), n * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->S + P.m0, S.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->parts + ctx->np, &P, sizeof P, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->blk + P.b0, blocks.data(), P.nblk * sizeof(int4), cudaMemcpyHostToDevice,
+                       ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->hparts.push_back(P);
     ctx->rc_max = std::max(ctx->rc_max, so.rcirc);
     ctx->nmark += n;
+    ctx->nblk += P.nblk;
     if (out_id) *out_id = ctx->np;
     ctx->np += 1;
     return LBM_OK;
@@ -311,9 +372,22 @@ lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* d, int32_t* o
 
 lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps) {
     if (!ctx || nsteps < 0) return LBM_EINVAL;
+    // long runs replay a captured graph of GRAPH_STEPS steps (launch-bound
+    // small lattices), the remainder is launched directly
+    while (nsteps >= GRAPH_STEPS && ctx->graphs_ok) {
+        if (!ctx->graph[ctx->cur] && !capture_graph(ctx, ctx->cur)) {
+            ctx->graphs_ok = false;
+            break;
+        }
+        CK(cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream));
+        ctx->steps += GRAPH_STEPS;
+        nsteps -= GRAPH_STEPS;
+    }
     for (int32_t k = 0; k < nsteps; ++k) {
-        lbm_status s = enqueue_step(ctx, nullptr);
+        lbm_status s = enqueue_step(ctx, ctx->stream, ctx->cur, nullptr);
         if (s != LBM_OK) return s;
+        ctx->cur ^= 1;
+        ctx->steps += 1;
     }
     return LBM_OK;
 }
@@ -325,8 +399,10 @@ lbm_status lbm_step_timed(lbm_ctx* ctx, int32_t nsteps, double* ms_step, double*
     double tot = 0, flu = 0;
     for (int32_t k = 0; k < nsteps; ++k) {
         CK(cudaEventRecord(ctx->ev[0], ctx->stream));
-        lbm_status s = enqueue_step(ctx, ctx->ev[1]);
+        lbm_status s = enqueue_step(ctx, ctx->stream, ctx->cur, ctx->ev[1]);
         if (s != LBM_OK) return s;
+        ctx->cur ^= 1;
+        ctx->steps += 1;
         CK(cudaEventRecord(ctx->ev[2], ctx->stream));
         CK(cudaEventSynchronize(ctx->ev[2]));
         float a = 0, b = 0;
@@ -446,6 +522,8 @@ void lbm_destroy(lbm_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    for (auto& g : ctx->graph)
+        if (g) cudaGraphExecDestroy(g);
     if (ctx->owns_ws) cudaFree(ctx->ws);
     delete ctx;
 }

@@ -27,45 +27,145 @@ __device__ __forceinline__ void collide(C v[9], C drho, C ux, C uy, C Fx, C Fy, 
     }
 }
 
+// four consecutive storage elements starting at a 4-aligned index
+template <class S, class C> struct Vec4;
+template <> struct Vec4<float, float> {
+    static __device__ __forceinline__ void load(const float* p, float v[4]) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+    static __device__ __forceinline__ void store(float* p, const float v[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <> struct Vec4<double, double> {
+    static __device__ __forceinline__ void load(const double* p, double v[4]) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void store(double* p, const double v[4]) {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    }
+};
+template <> struct Vec4<__half, float> {
+    static __device__ __forceinline__ void load(const __half* p, float v[4]) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void store(__half* p, const float v[4]) {
+        const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+        uint2 q;
+        q.x = *reinterpret_cast<const unsigned*>(&a);
+        q.y = *reinterpret_cast<const unsigned*>(&b);
+        *reinterpret_cast<uint2*>(p) = q;
+    }
+};
+
+// one cell: moments, IB force, forced BGK collision (Eqs. 2, 4-7)
+template <class C>
+__device__ __forceinline__ void cell_update(C v[9], const Geo& G, C fx_ib, C fy_ib) {
+    C drho, jx, jy;
+    moments<C>(v, drho, jx, jy);
+    const C Fx = geo_g<C>(G, 0) + fx_ib, Fy = geo_g<C>(G, 1) + fy_ib;
+    const C inv = C(1) / (C(1) + drho);
+    const C ux = (jx + C(0.5) * Fx) * inv, uy = (jy + C(0.5) * Fy) * inv;
+    collide<C>(v, drho, ux, uy, Fx, Fy, geo_omega<C>(G));
+}
+
+// Fused step, four consecutive cells (x0 .. x0+3, x0 = 4 * lane index) of
+// one row per thread; a warp covers 128 cells of a row.  Populations move
+// as 16-byte vectors: a pull along +-x is a one-lane shuffle of the
+// neighbouring vector, with one extra element load at the warp's two ends.
+// Cells on a wall or periodic edge take the per-cell general path.
 template <class S, class C>
 __global__ void __launch_bounds__(32 * BY) k_fluid(FluidArgs a) {
     const Geo& G = a.G;
     const S* __restrict__ fin = static_cast<const S*>(a.fin);
     S* __restrict__ fout = static_cast<S*>(a.fout);
     C* __restrict__ flb = static_cast<C*>(a.flb);
-    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int lane = threadIdx.x;
+    const int x0 = (blockIdx.x * 32 + lane) * 4;
     const int y = blockIdx.y * BY + threadIdx.y;
-    if (y >= G.ny) return;  // whole warp
-    const int seg = y * G.nseg + blockIdx.x;
-    const bool forced = a.flags[seg] != 0;  // same address for the warp
-    if (x < G.nx) {
-        C v[9];
-        const long long c = (long long)y * G.pitch + x;
-        if (x > 0 && x < G.nx - 1 && y > 0 && y < G.ny - 1) {
+    if (y >= G.ny) return;  // whole warp (one row)
+    const long long row = (long long)y * G.pitch;
+    // the vector values of cell x0 + k are its pulled populations whenever
+    // the cell is interior (all 9 sources inside, none of them clamped)
+    const bool rows_in = y >= 1 && y <= G.ny - 2;
+    const bool any = x0 < G.nx;
+    // force flags of the 32-cell segment of this thread (8 threads share one)
+    const int seg = y * G.nseg + (x0 >> 5);
+    const bool forced = any && a.flags[seg] != 0;
+
+    C v[9][4];
+    // vector loads for every lane (addresses clamped in-bounds), shuffles by all
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ys = min(max(y - cy(i), 0), G.ny - 1);
+        const S* rp = fin + (long long)i * G.plane + (long long)ys * G.pitch;
+        const int xa = min(x0, G.pitch - 4);
+        C q[4];
+        Vec4<S, C>::load(rp + xa, q);
+        if (cx(i) == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[i][k] = q[k];
+        } else if (cx(i) > 0) {  // source x - 1
+            C left = __shfl_up_sync(0xffffffffu, q[3], 1);
+            if (lane == 0) left = ld<S, C>(rp + max(xa - 1, 0));
+            v[i][0] = left; v[i][1] = q[0]; v[i][2] = q[1]; v[i][3] = q[2];
+        } else {  // source x + 1
+            C right = __shfl_down_sync(0xffffffffu, q[0], 1);
+            if (lane == 31) right = ld<S, C>(rp + min(xa + 4, G.pitch - 1));
+            v[i][0] = q[1]; v[i][1] = q[2]; v[i][2] = q[3]; v[i][3] = right;
+        }
+    }
+    if (any) {
+        C fxi[4] = {C(0), C(0), C(0), C(0)}, fyi[4] = {C(0), C(0), C(0), C(0)};
+        if (forced) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (x0 + k < G.nx) {
+                    fxi[k] = flb[row + x0 + k];
+                    fyi[k] = flb[G.plane + row + x0 + k];
+                    flb[row + x0 + k] = C(0);
+                    flb[G.plane + row + x0 + k] = C(0);
+                }
+        }
+        C out[9][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            C c[9];
+            const int xk = x0 + k;
+            if (rows_in && xk >= 1 && xk <= G.nx - 2) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) c[i] = v[i][k];
+            } else if (xk < G.nx) {
+                pull_general<S, C>(fin, G, xk, y, c);
+                complete_walls<S, C>(fin, G, xk, y, c);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) c[i] = C(0);
+            }
+            cell_update<C>(c, G, fxi[k], fyi[k]);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) out[i][k] = c[i];
+        }
+        if (x0 + 3 < G.nx) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Vec4<S, C>::store(fout + (long long)i * G.plane + row + x0, out[i]);
+        } else {
 #pragma unroll
             for (int i = 0; i < 9; ++i)
-                v[i] = ld<S, C>(fin + (long long)i * G.plane + c - (long long)cy(i) * G.pitch - cx(i));
-        } else {
-            pull_general<S, C>(fin, G, x, y, v);
-            complete_walls<S, C>(fin, G, x, y, v);
-        }
-        C drho, jx, jy;
-        moments<C>(v, drho, jx, jy);
-        C Fx = C(G.g[0]), Fy = C(G.g[1]);
-        if (forced) {
-            Fx += flb[c];
-            Fy += flb[G.plane + c];
-            flb[c] = C(0);
-            flb[G.plane + c] = C(0);
-        }
-        const C rho = C(1) + drho;
-        const C ux = (jx + C(0.5) * Fx) / rho, uy = (jy + C(0.5) * Fy) / rho;
-        collide<C>(v, drho, ux, uy, Fx, Fy, C(1.0 / G.tau));
 #pragma unroll
-        for (int i = 0; i < 9; ++i) st<S, C>(fout + (long long)i * G.plane + c, v[i]);
+                for (int k = 0; k < 4; ++k)
+                    if (x0 + k < G.nx) st<S, C>(fout + (long long)i * G.plane + row + x0 + k, out[i][k]);
+        }
     }
     __syncwarp();
-    if (forced && threadIdx.x == 0) a.flags[seg] = 0;
+    if (forced && (lane & 7) == 0) a.flags[seg] = 0;
 }
 
 // initial post-collision field f* = f^eq(rho, u) (Eq. 2), shifted
@@ -97,12 +197,12 @@ template <class S, class C>
 __global__ void k_fields(FieldArgs a) {
     const int x = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * BY + threadIdx.y;
     if (x >= a.G.nx || r >= a.rows) return;
-    double rho, ux, uy;
+    C rho, ux, uy;
     node_fields<S, C>(static_cast<const S*>(a.f), a.G, x, a.y0 + r, rho, ux, uy);
     const long long k = (long long)r * a.G.nx + x;
-    a.rho[k] = rho;
-    a.ux[k] = ux;
-    a.uy[k] = uy;
+    a.rho[k] = (double)rho;
+    a.ux[k] = (double)ux;
+    a.uy[k] = (double)uy;
 }
 
 dim3 grid_for(int nx, int rows) { return dim3((nx + 31) / 32, (rows + BY - 1) / BY); }
@@ -123,7 +223,7 @@ cudaError_t launch_init(int prec, void* f, const Geo& G, int kind, double init_u
 }
 
 cudaError_t launch_fluid(int prec, const FluidArgs& a, cudaStream_t s) {
-    const dim3 b(32, BY), g = grid_for(a.G.nx, a.G.ny);
+    const dim3 b(32, BY), g((a.G.nx + 127) / 128, (a.G.ny + BY - 1) / BY);
     if (prec == LBM_FP64) k_fluid<double, double><<<g, b, 0, s>>>(a);
     else if (prec == LBM_FP32) k_fluid<float, float><<<g, b, 0, s>>>(a);
     else k_fluid<__half, float><<<g, b, 0, s>>>(a);

@@ -41,6 +41,17 @@ template <> __device__ __forceinline__ void st<__half, float>(__half* p, float v
     *p = __float2half_rn(v);
 }
 
+// ------------------------------------------- constants in precision C ----
+template <class C> __device__ __forceinline__ C geo_g(const Geo& G, int k);
+template <> __device__ __forceinline__ double geo_g<double>(const Geo& G, int k) { return G.g[k]; }
+template <> __device__ __forceinline__ float geo_g<float>(const Geo& G, int k) { return G.gf[k]; }
+template <class C> __device__ __forceinline__ C geo_uw(const Geo& G, int s, int k);
+template <> __device__ __forceinline__ double geo_uw<double>(const Geo& G, int s, int k) { return G.uw[s][k]; }
+template <> __device__ __forceinline__ float geo_uw<float>(const Geo& G, int s, int k) { return G.uwf[s][k]; }
+template <class C> __device__ __forceinline__ C geo_omega(const Geo& G);
+template <> __device__ __forceinline__ double geo_omega<double>(const Geo& G) { return G.omega; }
+template <> __device__ __forceinline__ float geo_omega<float>(const Geo& G) { return G.omegaf; }
+
 // ------------------------------------------------- streaming + walls ----
 // Pull the populations arriving at (x, y) (Eq. 4 in pull form).  Sources
 // across a wall side are unknown and left at 0; periodic sides wrap.
@@ -118,7 +129,7 @@ __device__ __forceinline__ void complete_walls(const S* __restrict__ f, const Ge
                                                C v[9]) {
     const bool bot = !G.py && y == 0, top = !G.py && y == G.ny - 1;
     const bool lef = !G.px && x == 0, rig = !G.px && x == G.nx - 1;
-    const C gx = C(G.g[0]), gy = C(G.g[1]);
+    const C gx = geo_g<C>(G, 0), gy = geo_g<C>(G, 1);
     if ((bot || top) && (lef || rig)) {
         const int sx = lef ? 1 : -1, sy = bot ? 1 : -1;
         C nbv[9];
@@ -127,19 +138,19 @@ __device__ __forceinline__ void complete_walls(const S* __restrict__ f, const Ge
 #pragma unroll
         for (int i = 0; i < 9; ++i) d += nbv[i];
         const int side = bot ? 2 : 3;  // corners move with the wall along y
-        const C ux = C(G.uw[side][0]), uy = C(G.uw[side][1]);
+        const C ux = geo_uw<C>(G, side, 0), uy = geo_uw<C>(G, side, 1);
         if (bot && lef) zou_he_corner<1, 1, C>(v, d, ux, uy, gx, gy);
         else if (bot) zou_he_corner<-1, 1, C>(v, d, ux, uy, gx, gy);
         else if (lef) zou_he_corner<1, -1, C>(v, d, ux, uy, gx, gy);
         else zou_he_corner<-1, -1, C>(v, d, ux, uy, gx, gy);
     } else if (bot) {
-        zou_he_edge<0, 1, C>(v, C(G.uw[2][0]), C(G.uw[2][1]), gx, gy);
+        zou_he_edge<0, 1, C>(v, geo_uw<C>(G, 2, 0), geo_uw<C>(G, 2, 1), gx, gy);
     } else if (top) {
-        zou_he_edge<0, -1, C>(v, C(G.uw[3][0]), C(G.uw[3][1]), gx, gy);
+        zou_he_edge<0, -1, C>(v, geo_uw<C>(G, 3, 0), geo_uw<C>(G, 3, 1), gx, gy);
     } else if (lef) {
-        zou_he_edge<1, 0, C>(v, C(G.uw[0][0]), C(G.uw[0][1]), gx, gy);
+        zou_he_edge<1, 0, C>(v, geo_uw<C>(G, 0, 0), geo_uw<C>(G, 0, 1), gx, gy);
     } else if (rig) {
-        zou_he_edge<-1, 0, C>(v, C(G.uw[1][0]), C(G.uw[1][1]), gx, gy);
+        zou_he_edge<-1, 0, C>(v, geo_uw<C>(G, 1, 0), geo_uw<C>(G, 1, 1), gx, gy);
     }
 }
 
@@ -152,10 +163,22 @@ __device__ __forceinline__ void moments(const C v[9], C& drho, C& jx, C& jy) {
 }
 
 // Density and velocity u* (constant force with its half step, no IB force)
-// at the unwrapped node (ix, iy); false if the node lies across a wall.
+// in the compute precision C, from shifted populations v.
+template <class C>
+__device__ __forceinline__ void fields_of(const C v[9], const Geo& G, C& rho, C& ux, C& uy) {
+    C d, jx, jy;
+    moments<C>(v, d, jx, jy);
+    rho = C(1) + d;
+    const C inv = C(1) / rho;
+    ux = (jx + C(0.5) * geo_g<C>(G, 0)) * inv;
+    uy = (jy + C(0.5) * geo_g<C>(G, 1)) * inv;
+}
+
+// wrap / wall path of node_fields, kept out of line so the unrolled gathers
+// of the marker kernels stay small
 template <class S, class C>
-__device__ __forceinline__ bool node_fields(const S* __restrict__ f, const Geo& G, int ix, int iy,
-                                            double& rho, double& ux, double& uy) {
+__device__ __noinline__ bool node_fields_general(const S* __restrict__ f, const Geo& G, int ix,
+                                                 int iy, C& rho, C& ux, C& uy) {
     if (ix < 0 || ix >= G.nx) {
         if (!G.px) return false;
         ix = ((ix % G.nx) + G.nx) % G.nx;
@@ -167,12 +190,24 @@ __device__ __forceinline__ bool node_fields(const S* __restrict__ f, const Geo& 
     C v[9];
     pull_general<S, C>(f, G, ix, iy, v);
     complete_walls<S, C>(f, G, ix, iy, v);
-    C d, jx, jy;
-    moments<C>(v, d, jx, jy);
-    rho = 1.0 + (double)d;
-    ux = ((double)jx + 0.5 * G.g[0]) / rho;
-    uy = ((double)jy + 0.5 * G.g[1]) / rho;
+    fields_of<C>(v, G, rho, ux, uy);
     return true;
+}
+
+// rho, u* at the unwrapped node (ix, iy); false if it lies across a wall
+template <class S, class C>
+__device__ __forceinline__ bool node_fields(const S* __restrict__ f, const Geo& G, int ix, int iy,
+                                            C& rho, C& ux, C& uy) {
+    if (ix > 0 && ix < G.nx - 1 && iy > 0 && iy < G.ny - 1) {
+        C v[9];
+        const long long c = (long long)iy * G.pitch + ix;
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            v[i] = ld<S, C>(f + (long long)i * G.plane + c - (long long)cy(i) * G.pitch - cx(i));
+        fields_of<C>(v, G, rho, ux, uy);
+        return true;
+    }
+    return node_fields_general<S, C>(f, G, ix, iy, rho, ux, uy);
 }
 
 // --------------------------------------------------------------- MLS ----
@@ -180,19 +215,20 @@ __device__ __forceinline__ bool node_fields(const S* __restrict__ f, const Geo& 
 // argument r = |x - x_k| / r_w with r_w = 2.6.  The polynomial weight is
 // read as the 4-point kernel in q = 2 r (as printed its second branch takes
 // the root of a negative number).
-__device__ __forceinline__ double mls_weight(int kind, double r) {
-    if (r > 1.0) return 0.0;
+template <class W>
+__device__ __forceinline__ W mls_weight(int kind, W r) {
+    if (r > W(1)) return W(0);
     switch (kind) {
-        case LBM_W_CUBIC: return 2.0 / 3.0 - 4.0 * r * r + 4.0 * r * r * r;
-        case LBM_W_QUARTIC: return 1.0 + r * r * (-6.0 + r * (8.0 - 3.0 * r));
-        case LBM_W_COSINE: return 0.25 * (1.0 + cospi(0.5 * r));
+        case LBM_W_CUBIC: return W(2.0 / 3.0) - W(4) * r * r + W(4) * r * r * r;
+        case LBM_W_QUARTIC: return W(1) + r * r * (W(-6) + r * (W(8) - W(3) * r));
+        case LBM_W_COSINE: return W(0.25) * (W(1) + cospi(W(0.5) * r));
         case LBM_W_POLY: {
-            const double q = 2.0 * r;
-            return q <= 1.0 ? 0.125 * (3.0 - 2.0 * q + sqrt(1.0 + 4.0 * q - 4.0 * q * q))
-                            : 0.125 * (5.0 - 2.0 * q - sqrt(-7.0 + 12.0 * q - 4.0 * q * q));
+            const W q = W(2) * r;
+            return q <= W(1) ? W(0.125) * (W(3) - W(2) * q + sqrt(W(1) + W(4) * q - W(4) * q * q))
+                             : W(0.125) * (W(5) - W(2) * q - sqrt(W(-7) + W(12) * q - W(4) * q * q));
         }
         default: {
-            const double s = r * (1.0 / 0.3);
+            const W s = r * W(1.0 / 0.3);
             return exp(-s * s);
         }
     }
@@ -201,23 +237,26 @@ __device__ __forceinline__ double mls_weight(int kind, double r) {
 // MLS operator at (px, py) over the 3x3 nodes around the nearest node:
 // phi (Eq. 8 weights) and, if D, the weights of the two linear
 // coefficients (the x and y derivatives of the fit).  Linear basis in
-// coordinates relative to the point; the 3x3 moment matrix A = sum W p p^T
-// is inverted in FP64 by its adjugate.  (i0, j0) = lower-left node.
-template <bool D>
-__device__ __forceinline__ void mls(int kind, double px, double py, int& i0, int& j0, double phi[9],
-                                    double dphx[9], double dphy[9]) {
+// coordinates relative to the point; the weights are evaluated in precision
+// W, the 3x3 moment matrix A = sum W p p^T is accumulated and inverted (by
+// its adjugate) in FP64.  (i0, j0) = lower-left node.
+template <bool D, class Wt>
+__device__ __forceinline__ void mls(int kind, double px, double py, int& i0, int& j0, Wt phi[9],
+                                    Wt dphx[9], Wt dphy[9]) {
     const int ic = (int)floor(px + 0.5), jc = (int)floor(py + 0.5);
     i0 = ic - 1;
     j0 = jc - 1;
-    double W[9], DX[9], DY[9];
+    Wt W[9], DX[9], DY[9];
     double a00 = 0, a01 = 0, a02 = 0, a11 = 0, a12 = 0, a22 = 0;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const double dx = (double)(i0 + k % 3) - px, dy = (double)(j0 + k / 3) - py;
-        const double w = mls_weight(kind, sqrt(dx * dx + dy * dy) * (1.0 / 2.6));
-        W[k] = w;
-        DX[k] = dx;
-        DY[k] = dy;
+        const Wt dxw = (Wt)dx, dyw = (Wt)dy;
+        const Wt ww = mls_weight<Wt>(kind, sqrt(dxw * dxw + dyw * dyw) * Wt(1.0 / 2.6));
+        const double w = (double)ww;
+        W[k] = ww;
+        DX[k] = dxw;
+        DY[k] = dyw;
         a00 += w;
         a01 += w * dx;
         a02 += w * dy;
@@ -225,16 +264,16 @@ __device__ __forceinline__ void mls(int kind, double px, double py, int& i0, int
         a12 += w * dx * dy;
         a22 += w * dy * dy;
     }
-    // adjugate of the symmetric matrix
+    // adjugate of the symmetric matrix (FP64)
     const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
     const double det = a00 * c00 + a01 * c01 + a02 * c02;
     const double id = 1.0 / det;
-    const double i00 = c00 * id, i01 = c01 * id, i02 = c02 * id;
+    const Wt i00 = (Wt)(c00 * id), i01 = (Wt)(c01 * id), i02 = (Wt)(c02 * id);
 #pragma unroll
     for (int k = 0; k < 9; ++k) phi[k] = W[k] * (i00 + i01 * DX[k] + i02 * DY[k]);
     if (D) {
-        const double i11 = (a00 * a22 - a02 * a02) * id, i12 = (a01 * a02 - a00 * a12) * id;
-        const double i22 = (a00 * a11 - a01 * a01) * id;
+        const Wt i11 = (Wt)((a00 * a22 - a02 * a02) * id), i12 = (Wt)((a01 * a02 - a00 * a12) * id);
+        const Wt i22 = (Wt)((a00 * a11 - a01 * a01) * id);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             dphx[k] = W[k] * (i01 + i11 * DX[k] + i12 * DY[k]);

@@ -20,18 +20,25 @@ struct Geo {
     int px, py;               // periodic in x / y
     double uw[4][2];          // wall velocities, sides x-, x+, y-, y+
     double g[2];              // constant fluid body force
-    double tau;
+    double tau, omega;        // relaxation time and its inverse
+    // the same constants in FP32, precomputed on the host: the FP32 kernels
+    // must not touch FP64 (a small fraction of the FP32 rate on this part)
+    float uwf[4][2], gf[2], omegaf;
 };
 
 // Rigid particle on the device (all FP64).  Index 0 of the history arrays
 // is the latest level, index 1 the level before it.
 struct DParticle {
     double X[2][2], th[2], U[2][2], W[2];
+    double cs[2][2];          // (cos, sin) of th[0] and th[1]
     double F[2], M;
     double mass, inertia, area, rho_s;
     int m0, nm;               // first marker, marker count
+    int b0, nblk;             // first marker block, marker blocks (MB markers each)
     long long nupd;           // rigid-body updates done
 };
+
+constexpr int MB = 8;         // markers per block of the marker kernels (one warp, 4 lanes each)
 
 // Spreading record of one marker: the unwrapped lower-left node (i0, j0) of
 // its 3x3 support and the 9 contributions S_l phi_k F_l (Eq. 12).
@@ -48,6 +55,9 @@ struct ParticleArgs {
     const void* f;            // post-collision populations (storage type)
     Geo G;
     DParticle* parts;
+    const int4* blk;          // per marker block: (particle, first marker, markers, 0)
+    double* partial;          // per marker block: F_x, F_y, M partial sums
+    unsigned* count;          // per particle: marker blocks done (reset by the last)
     const double2* rb;        // body-frame marker positions
     const double2* nb;        // body-frame normals
     const double* S;          // marker arc lengths
@@ -87,7 +97,8 @@ struct FieldArgs {
 cudaError_t launch_init(int prec, void* f, const Geo& G, int kind, double init_u, cudaStream_t s);
 cudaError_t launch_fluid(int prec, const FluidArgs& a, cudaStream_t s);
 cudaError_t launch_fields(int prec, const FieldArgs& a, cudaStream_t s);
-cudaError_t launch_particles(int prec, const ParticleArgs& a, int np, cudaStream_t s);
+cudaError_t launch_probes(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s);
+cudaError_t launch_markers(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s);
 cudaError_t launch_spread(int prec, const SpreadArgs& a, int np, int tiles, cudaStream_t s);
 size_t storage_bytes(int prec);
 size_t compute_bytes(int prec);

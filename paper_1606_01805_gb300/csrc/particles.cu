@@ -1,13 +1,18 @@
 // particles.cu -- immersed-boundary kernels of the LB-IB step.
 //
-// k_particles (one CTA per particle, FP64):
-//   probes 1.2 dx along the outward normals of the body at its latest level,
-//   MLS fit of density and velocity there, surface traction, block reduction
-//   of force and torque (Eqs. 13-14), two-level rigid-body update (Eqs.
-//   15-16), then the markers at the new level: MLS interpolation (Eq. 8),
-//   direct-forcing force (Eq. 11) and the per-marker spreading record
-//   S_l phi_k F_l of Eq. 12, plus the particle's support box.
-// k_spread (one CTA per 16x16 tile of a particle's box): gathers, cell by
+// The markers of all particles are cut into blocks of MB = 8 (one warp per
+// block, four lanes per marker), so the FP64 work spreads over many SMs and
+// each lane's dependency chain covers only 2-3 of the 9 support nodes.
+// k_probes: probe 1.2 dx along the outward normal of each marker of the body
+//   at its latest level, MLS fit of density and velocity there, surface
+//   traction; warp sums of force and torque per block (Eqs. 13-14).  The
+//   last block of a particle to finish (atomic counter, no waiting) adds the
+//   block sums in block order and applies the two-level rigid-body update
+//   (Eqs. 15-16), all in FP64.
+// k_markers: markers at the new level: MLS interpolation (Eq. 8),
+//   direct-forcing force (Eq. 11), the per-marker spreading record
+//   S_l phi_k F_l of Eq. 12 and the particle's support box.
+// k_spread (one CTA per 32x16 tile of a particle's box): gathers, cell by
 //   cell and in marker order, the records whose support covers the cell,
 //   then adds the particle's sum into f_lb (the only atomic: one add per
 //   cell and particle, contended only where particles overlap) and flags the
@@ -20,8 +25,7 @@ namespace lbib {
 
 namespace {
 
-constexpr int PT = 256;    // threads per particle CTA
-constexpr int TILE = 16;   // spreading tile edge
+constexpr int TX = 32, TY = 16;  // spreading tile (cells); one thread per cell
 constexpr double CS2 = 1.0 / 3.0;
 constexpr double PROBE = 1.2;
 
@@ -41,210 +45,310 @@ __device__ __forceinline__ int warp_max(int v) {
     return v;
 }
 
+constexpr int LPM = 4;  // lanes per marker: lane q gathers support nodes q, q + 4, q + 8
+
+template <class T>
+__device__ __forceinline__ T quad_sum(T v) {  // sum over the 4 lanes of a marker
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    return v;
+}
+
+// The MLS operator of Eqs. 8-10 split over the 4 lanes of a marker: lane q
+// holds support nodes k = q, q + 4, q + 8 (k < 9) of the 3x3 block around
+// the nearest node of (px, py).  Weights in precision C; the moment matrix
+// A = sum W p p^T is reduced across the lanes and inverted (adjugate) in
+// FP64.  On return the lane has, for its nodes, W (in w[]), the offsets,
+// and the first (phi) and, if D, second/third rows of A^-1 [W p].
+template <bool D, class C>
+struct QuadMLS {
+    int i0, j0;      // lower-left node of the support
+    int nk;          // nodes held by this lane (3 or 2)
+    int kk[3];
+    C phi[3], dpx[3], dpy[3];
+
+    __device__ __forceinline__ void build(int kind, double px, double py, int q, bool active) {
+        const int ic = (int)floor(px + 0.5), jc = (int)floor(py + 0.5);
+        i0 = ic - 1;
+        j0 = jc - 1;
+        nk = q == 0 ? 3 : 2;
+        C W[3], DX[3], DY[3];
+        double a00 = 0, a01 = 0, a02 = 0, a11 = 0, a12 = 0, a22 = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int k = q + 4 * j;
+            kk[j] = k;
+            W[j] = C(0);
+            DX[j] = C(0);
+            DY[j] = C(0);
+            if (j < nk && active) {
+                const double dx = (double)(i0 + k % 3) - px, dy = (double)(j0 + k / 3) - py;
+                const C dxw = (C)dx, dyw = (C)dy;
+                W[j] = mls_weight<C>(kind, sqrt(dxw * dxw + dyw * dyw) * C(1.0 / 2.6));
+                DX[j] = dxw;
+                DY[j] = dyw;
+                const double w = (double)W[j], ddx = (double)dxw, ddy = (double)dyw;
+                a00 += w;
+                a01 += w * ddx;
+                a02 += w * ddy;
+                a11 += w * ddx * ddx;
+                a12 += w * ddx * ddy;
+                a22 += w * ddy * ddy;
+            }
+        }
+        a00 = quad_sum(a00); a01 = quad_sum(a01); a02 = quad_sum(a02);
+        a11 = quad_sum(a11); a12 = quad_sum(a12); a22 = quad_sum(a22);
+        if (!active) a00 = a11 = a22 = 1.0;  // keep idle lanes finite
+        const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+        const double id = 1.0 / (a00 * c00 + a01 * c01 + a02 * c02);
+        const C i00 = (C)(c00 * id), i01 = (C)(c01 * id), i02 = (C)(c02 * id);
+        C i11 = C(0), i12 = C(0), i22 = C(0);
+        if (D) {
+            i11 = (C)((a00 * a22 - a02 * a02) * id);
+            i12 = (C)((a01 * a02 - a00 * a12) * id);
+            i22 = (C)((a00 * a11 - a01 * a01) * id);
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            phi[j] = W[j] * (i00 + i01 * DX[j] + i02 * DY[j]);
+            if (D) {
+                dpx[j] = W[j] * (i01 + i11 * DX[j] + i12 * DY[j]);
+                dpy[j] = W[j] * (i02 + i12 * DX[j] + i22 * DY[j]);
+            }
+        }
+    }
+};
+
 template <class S, class C>
-__global__ void __launch_bounds__(PT) k_particles(ParticleArgs a) {
+__global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     const S* __restrict__ f = static_cast<const S*>(a.f);
     const Geo& G = a.G;
-    DParticle* P = a.parts + blockIdx.x;
-    Rec<C>* recs = static_cast<Rec<C>*>(a.recs);
-    __shared__ double red[3][PT / 32];
-    __shared__ int ired[4][PT / 32];
-    __shared__ double st_new[6];  // X, Y, theta, U, V, W at the new level
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int m0 = P->m0, nm = P->nm;
-    const double X0 = P->X[0][0], Y0 = P->X[0][1], th0 = P->th[0];
-    const double U0 = P->U[0][0], V0 = P->U[0][1], W0 = P->W[0];
-    const double th1 = P->th[1], U1 = P->U[1][0], V1 = P->U[1][1], W1 = P->W[1];
-    const double nu = CS2 * (G.tau - 0.5);
-    double c0, s0, c1, s1;
-    sincos(th0, &s0, &c0);
-    sincos(th1, &s1, &c1);
+    const int4 bk = a.blk[blockIdx.x];
+    DParticle* P = a.parts + bk.x;
+    const int lane = threadIdx.x, q = lane & (LPM - 1);
+    const int ml = lane / LPM, m = bk.y + ml;  // marker (absolute index)
+    const bool active = ml < bk.z;
     unsigned err = 0;
-
-    // ---- probes on the body at the latest level -> F, M (Eqs. 13-14)
-    double Fx = 0, Fy = 0, Mz = 0;
-    for (int l = threadIdx.x; l < nm; l += PT) {
-        const double2 rb = a.rb[m0 + l], nb = a.nb[m0 + l];
-        const double Sl = a.S[m0 + l];
-        const double rx = c0 * rb.x - s0 * rb.y, ry = s0 * rb.x + c0 * rb.y;  // x_l - X_c
-        const double nx = c0 * nb.x - s0 * nb.y, ny = s0 * nb.x + c0 * nb.y;
-        const double px = X0 + rx + PROBE * nx, py = Y0 + ry + PROBE * ny;
-        int i0, j0;
-        double phi[9], dpx[9], dpy[9];
-        mls<true>(a.weight, px, py, i0, j0, phi, dpx, dpy);
-        double r = 0, uxx = 0, uxy = 0, uyx = 0, uyy = 0;
+    // body at its latest level
+    const double c0 = P->cs[0][0], s0 = P->cs[0][1];
+    double2 rb = make_double2(0, 0), nb = make_double2(1, 0);
+    if (active) {
+        rb = a.rb[m];
+        nb = a.nb[m];
+    }
+    const double rx = c0 * rb.x - s0 * rb.y, ry = s0 * rb.x + c0 * rb.y;  // x_l - X_c
+    const double nx = c0 * nb.x - s0 * nb.y, ny = s0 * nb.x + c0 * nb.y;
+    const double px = P->X[0][0] + rx + PROBE * nx, py = P->X[0][1] + ry + PROBE * ny;
+    QuadMLS<true, C> M;
+    M.build(a.weight, px, py, q, active);
+    // MLS fit of rho and grad u at the probe (Section 2.3)
+    C r = C(0), uxx = C(0), uxy = C(0), uyx = C(0), uyy = C(0);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            double rk, uk, vk;
-            if (!node_fields<S, C>(f, G, i0 + k % 3, j0 + k / 3, rk, uk, vk)) {
+    for (int j = 0; j < 3; ++j) {
+        if (j < M.nk && active) {
+            const int k = M.kk[j];
+            C rk, uk, vk;
+            if (!node_fields<S, C>(f, G, M.i0 + k % 3, M.j0 + k / 3, rk, uk, vk)) {
                 err |= ERR_DOMAIN;
-                rk = 1.0; uk = 0.0; vk = 0.0;
+                rk = C(1); uk = C(0); vk = C(0);
             }
-            r += phi[k] * rk;
-            uxx += dpx[k] * uk;
-            uxy += dpy[k] * uk;
-            uyx += dpx[k] * vk;
-            uyy += dpy[k] * vk;
+            r += M.phi[j] * rk;
+            uxx += M.dpx[j] * uk;
+            uxy += M.dpy[j] * uk;
+            uyx += M.dpx[j] * vk;
+            uyy += M.dpy[j] * vk;
         }
-        // rigid velocity of the marker at the two stored levels
+    }
+    r = quad_sum(r); uxx = quad_sum(uxx); uxy = quad_sum(uxy); uyx = quad_sum(uyx); uyy = quad_sum(uyy);
+    double Fx = 0, Fy = 0, Mz = 0;
+    if (active && q == 0) {
+        // change of the marker's rigid velocity between the two stored levels
+        const double c1 = P->cs[1][0], s1 = P->cs[1][1];
         const double r1x = c1 * rb.x - s1 * rb.y, r1y = s1 * rb.x + c1 * rb.y;
-        const double dvx = (U0 - W0 * ry) - (U1 - W1 * r1y);
-        const double dvy = (V0 + W0 * rx) - (V1 + W1 * r1x);
-        const double p = CS2 * (r - 1.0) + r * PROBE * (dvx * nx + dvy * ny);
-        const double mu = r * nu;
-        const double txx = 2.0 * mu * uxx, tyy = 2.0 * mu * uyy, txy = mu * (uxy + uyx);
-        const double tx = txx * nx + txy * ny - p * nx;
-        const double ty = txy * nx + tyy * ny - p * ny;
-        Fx += tx * Sl;
-        Fy += ty * Sl;
-        Mz += (rx * ty - ry * tx) * Sl;
+        const C dvx = (C)((P->U[0][0] - P->W[0] * ry) - (P->U[1][0] - P->W[1] * r1y));
+        const C dvy = (C)((P->U[0][1] + P->W[0] * rx) - (P->U[1][1] + P->W[1] * r1x));
+        const C cnx = (C)nx, cny = (C)ny;
+        const C p = C(CS2) * (r - C(1)) + r * C(PROBE) * (dvx * cnx + dvy * cny);
+        const C mu = r * (C)(CS2 * (G.tau - 0.5));
+        const C txx = C(2) * mu * uxx, tyy = C(2) * mu * uyy, txy = mu * (uxy + uyx);
+        const double tx = (double)(txx * cnx + txy * cny - p * cnx);
+        const double ty = (double)(txy * cnx + tyy * cny - p * cny);
+        const double Sl = a.S[m];
+        Fx = tx * Sl;
+        Fy = ty * Sl;
+        Mz = (rx * ty - ry * tx) * Sl;
     }
     Fx = warp_sum(Fx);
     Fy = warp_sum(Fy);
     Mz = warp_sum(Mz);
+    if (err) atomicOr(a.err, err);
+    unsigned done = 0;
     if (lane == 0) {
-        red[0][wid] = Fx;
-        red[1][wid] = Fy;
-        red[2][wid] = Mz;
+        double* part = a.partial + 3 * (long long)blockIdx.x;
+        part[0] = Fx;
+        part[1] = Fy;
+        part[2] = Mz;
+        __threadfence();
+        done = atomicAdd(a.count + bk.x, 1u);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double F0 = 0, F1 = 0, M = 0;
-        for (int w = 0; w < PT / 32; ++w) {
-            F0 += red[0][w];
-            F1 += red[1][w];
-            M += red[2][w];
-        }
-        // ---- rigid-body update (Eqs. 15-16): one-level start, then BDF2
-        const double buoy = (P->rho_s - 1.0) * P->area;
-        const double ax = (F0 + buoy * a.gravity[0]) / P->mass;
-        const double ay = (F1 + buoy * a.gravity[1]) / P->mass;
-        const double al = M / P->inertia;
-        double U, V, W, X, Y, T;
-        if (P->nupd == 0) {
-            U = U0 + ax;
-            V = V0 + ay;
-            W = W0 + al;
-            X = X0 + U;
-            Y = Y0 + V;
-            T = th0 + W;
-        } else {
-            const double k = 2.0 / 3.0;
-            U = k * (2.0 * U0 - 0.5 * U1 + ax);
-            V = k * (2.0 * V0 - 0.5 * V1 + ay);
-            W = k * (2.0 * W0 - 0.5 * W1 + al);
-            X = k * (2.0 * X0 - 0.5 * P->X[1][0] + U);
-            Y = k * (2.0 * Y0 - 0.5 * P->X[1][1] + V);
-            T = k * (2.0 * th0 - 0.5 * th1 + W);
-        }
-        P->X[1][0] = X0; P->X[1][1] = Y0; P->th[1] = th0;
-        P->U[1][0] = U0; P->U[1][1] = V0; P->W[1] = W0;
-        P->X[0][0] = X; P->X[0][1] = Y; P->th[0] = T;
-        P->U[0][0] = U; P->U[0][1] = V; P->W[0] = W;
-        P->F[0] = F0; P->F[1] = F1; P->M = M;
-        P->nupd += 1;
-        if (!isfinite(X) || !isfinite(Y) || !isfinite(T)) err |= ERR_NONFINITE;
-        st_new[0] = X; st_new[1] = Y; st_new[2] = T;
-        st_new[3] = U; st_new[4] = V; st_new[5] = W;
+    done = __shfl_sync(0xffffffffu, done, 0);
+    if (done != (unsigned)P->nblk - 1) return;  // whole warp
+    // ---- last block of this particle: all lanes load the block sums (fixed
+    // lane assignment and shuffle tree, so the sum is deterministic)
+    __threadfence();
+    double F0 = 0, F1 = 0, Mt = 0;
+    for (int b = P->b0 + lane; b < P->b0 + P->nblk; b += 32) {
+        F0 += __ldcg(a.partial + 3 * (long long)b);
+        F1 += __ldcg(a.partial + 3 * (long long)b + 1);
+        Mt += __ldcg(a.partial + 3 * (long long)b + 2);
     }
-    __syncthreads();
+    F0 = warp_sum(F0);
+    F1 = warp_sum(F1);
+    Mt = warp_sum(Mt);
+    if (lane != 0) return;
+    const double X0 = P->X[0][0], Y0 = P->X[0][1], th0 = P->th[0];
+    const double U0 = P->U[0][0], V0 = P->U[0][1], W0 = P->W[0];
+    const double buoy = (P->rho_s - 1.0) * P->area;
+    const double ax = (F0 + buoy * a.gravity[0]) / P->mass;
+    const double ay = (F1 + buoy * a.gravity[1]) / P->mass;
+    const double al = Mt / P->inertia;
+    double U, V, W, X, Y, T;
+    if (P->nupd == 0) {  // one stored level: u1 = u0 + a, x1 = x0 + u1
+        U = U0 + ax;
+        V = V0 + ay;
+        W = W0 + al;
+        X = X0 + U;
+        Y = Y0 + V;
+        T = th0 + W;
+    } else {  // Eqs. 15-16 and the same two-level form for position and angle
+        const double k = 2.0 / 3.0;
+        U = k * (2.0 * U0 - 0.5 * P->U[1][0] + ax);
+        V = k * (2.0 * V0 - 0.5 * P->U[1][1] + ay);
+        W = k * (2.0 * W0 - 0.5 * P->W[1] + al);
+        X = k * (2.0 * X0 - 0.5 * P->X[1][0] + U);
+        Y = k * (2.0 * Y0 - 0.5 * P->X[1][1] + V);
+        T = k * (2.0 * th0 - 0.5 * P->th[1] + W);
+    }
+    P->X[1][0] = X0; P->X[1][1] = Y0; P->th[1] = th0;
+    P->U[1][0] = U0; P->U[1][1] = V0; P->W[1] = W0;
+    P->X[0][0] = X; P->X[0][1] = Y; P->th[0] = T;
+    P->U[0][0] = U; P->U[0][1] = V; P->W[0] = W;
+    P->F[0] = F0; P->F[1] = F1; P->M = Mt;
+    P->cs[1][0] = P->cs[0][0]; P->cs[1][1] = P->cs[0][1];
+    double sT, cT;
+    sincos(T, &sT, &cT);
+    P->cs[0][0] = cT; P->cs[0][1] = sT;
+    P->nupd += 1;
+    if (!isfinite(X) || !isfinite(Y) || !isfinite(T) || !isfinite(U) || !isfinite(W))
+        atomicOr(a.err, ERR_NONFINITE);
+    a.count[bk.x] = 0;
+    a.boxes[bk.x] = make_int4(INT_MAX, INT_MAX, INT_MIN, INT_MIN);
+}
 
-    // ---- markers at the new level: interpolation, direct forcing, records
-    const double X = st_new[0], Y = st_new[1];
-    double cn, sn;
-    sincos(st_new[2], &sn, &cn);
-    const double U = st_new[3], V = st_new[4], W = st_new[5];
-    int bx0 = INT_MAX, by0 = INT_MAX, bx1 = INT_MIN, by1 = INT_MIN;
-    for (int l = threadIdx.x; l < nm; l += PT) {
-        const double2 rb = a.rb[m0 + l];
-        const double Sl = a.S[m0 + l];
-        const double rx = cn * rb.x - sn * rb.y, ry = sn * rb.x + cn * rb.y;
-        int i0, j0;
-        double phi[9];
-        mls<false>(a.weight, X + rx, Y + ry, i0, j0, phi, nullptr, nullptr);
-        double ux = 0, uy = 0;
+template <class S, class C>
+__global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
+    const S* __restrict__ f = static_cast<const S*>(a.f);
+    const Geo& G = a.G;
+    const int4 bk = a.blk[blockIdx.x];
+    const DParticle* P = a.parts + bk.x;
+    Rec<C>* recs = static_cast<Rec<C>*>(a.recs);
+    const int lane = threadIdx.x, q = lane & (LPM - 1);
+    const int ml = lane / LPM, m = bk.y + ml;  // marker (absolute index)
+    const bool active = ml < bk.z;
+    unsigned err = 0;
+    const double X = P->X[0][0], Y = P->X[0][1];
+    const double cn = P->cs[0][0], sn = P->cs[0][1];
+    const double2 rb = active ? a.rb[m] : make_double2(0, 0);
+    const double rx = cn * rb.x - sn * rb.y, ry = sn * rb.x + cn * rb.y;
+    QuadMLS<false, C> M;
+    M.build(a.weight, X + rx, Y + ry, q, active);
+    C ux = C(0), uy = C(0);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            double rk, uk, vk;
-            if (!node_fields<S, C>(f, G, i0 + k % 3, j0 + k / 3, rk, uk, vk)) {
+    for (int j = 0; j < 3; ++j) {
+        if (j < M.nk && active) {
+            const int k = M.kk[j];
+            C rk, uk, vk;
+            if (!node_fields<S, C>(f, G, M.i0 + k % 3, M.j0 + k / 3, rk, uk, vk)) {
                 err |= ERR_DOMAIN;
-                uk = 0.0; vk = 0.0;
+                uk = C(0); vk = C(0);
             }
-            ux += phi[k] * uk;
-            uy += phi[k] * vk;
+            ux += M.phi[j] * uk;
+            uy += M.phi[j] * vk;
         }
-        const double Flx = (U - W * ry) - ux, Fly = (V + W * rx) - uy;  // Eq. 11, dt = 1
-        Rec<C> rc;
-        rc.i0 = i0;
-        rc.j0 = j0;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            rc.cx[k] = (C)(Sl * phi[k] * Flx);
-            rc.cy[k] = (C)(Sl * phi[k] * Fly);
-        }
-        recs[m0 + l] = rc;
-        bx0 = min(bx0, i0);
-        by0 = min(by0, j0);
-        bx1 = max(bx1, i0 + 2);
-        by1 = max(by1, j0 + 2);
     }
+    ux = quad_sum(ux);  // Eq. 8: U(x_l)
+    uy = quad_sum(uy);
+    int bx0 = INT_MAX, by0 = INT_MAX, bx1 = INT_MIN, by1 = INT_MIN;
+    if (active) {
+        // Eq. 11 with dt = 1, times the arc length c_l = S_l of Eq. 12
+        const double Sl = a.S[m];
+        const C sx = (C)(Sl * ((P->U[0][0] - P->W[0] * ry) - (double)ux));
+        const C sy = (C)(Sl * ((P->U[0][1] + P->W[0] * rx) - (double)uy));
+        Rec<C>* rc = recs + m;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            if (j < M.nk) {
+                rc->cx[M.kk[j]] = M.phi[j] * sx;
+                rc->cy[M.kk[j]] = M.phi[j] * sy;
+            }
+        if (q == 0) {
+            rc->i0 = M.i0;
+            rc->j0 = M.j0;
+            bx0 = M.i0;
+            by0 = M.j0;
+            bx1 = M.i0 + 2;
+            by1 = M.j0 + 2;
+        }
+    }
+    if (err) atomicOr(a.err, err);
     bx0 = warp_min(bx0);
     by0 = warp_min(by0);
     bx1 = warp_max(bx1);
     by1 = warp_max(by1);
     if (lane == 0) {
-        ired[0][wid] = bx0;
-        ired[1][wid] = by0;
-        ired[2][wid] = bx1;
-        ired[3][wid] = by1;
+        int4* b = a.boxes + bk.x;
+        atomicMin(&b->x, bx0);
+        atomicMin(&b->y, by0);
+        atomicMax(&b->z, bx1);
+        atomicMax(&b->w, by1);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int4 b = make_int4(INT_MAX, INT_MAX, INT_MIN, INT_MIN);
-        for (int w = 0; w < PT / 32; ++w) {
-            b.x = min(b.x, ired[0][w]);
-            b.y = min(b.y, ired[1][w]);
-            b.z = max(b.z, ired[2][w]);
-            b.w = max(b.w, ired[3][w]);
-        }
-        a.boxes[blockIdx.x] = b;
-    }
-    if (err) atomicOr(a.err, err);
 }
 
 template <class C>
-__global__ void __launch_bounds__(TILE * TILE) k_spread(SpreadArgs a) {
+__global__ void __launch_bounds__(TX * TY) k_spread(SpreadArgs a) {
+    // records examined per round: as many as fit the static shared list
+    constexpr int CAP = sizeof(Rec<C>) * TX * TY <= 48 * 1024 ? TX * TY : TX * TY / 2;
     const Geo& G = a.G;
     const DParticle* P = a.parts + blockIdx.y;
     const Rec<C>* recs = static_cast<const Rec<C>*>(a.recs);
     C* flb = static_cast<C*>(a.flb);
-    __shared__ Rec<C> list[TILE * TILE];
-    __shared__ int wcount[TILE * TILE / 32];
+    __shared__ Rec<C> list[CAP];
+    __shared__ int wcount[TX * TY / 32];
     const int4 box = a.boxes[blockIdx.y];
     if (box.x > box.z) return;
-    const int tx = (box.z - box.x + TILE) / TILE, ty = (box.w - box.y + TILE) / TILE;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && tx * ty > (int)gridDim.x) atomicOr(a.err, ERR_DOMAIN);
-    if ((int)blockIdx.x >= tx * ty) return;  // whole CTA
-    const int x0 = box.x + (blockIdx.x % tx) * TILE, y0 = box.y + (blockIdx.x / tx) * TILE;
+    const int ntx = (box.z - box.x + TX) / TX, nty = (box.w - box.y + TY) / TY;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ntx * nty > (int)gridDim.x) atomicOr(a.err, ERR_DOMAIN);
+    if ((int)blockIdx.x >= ntx * nty) return;  // whole CTA
+    const int x0 = box.x + (blockIdx.x % ntx) * TX, y0 = box.y + (blockIdx.x / ntx) * TY;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int cxl = x0 + t % TILE, cyl = y0 + t / TILE;  // this thread's (unwrapped) cell
+    const int cxl = x0 + t % TX, cyl = y0 + t / TX;  // this thread's (unwrapped) cell
     const int m0 = P->m0, nm = P->nm;
     C ax = C(0), ay = C(0);
     bool touched = false;
-    for (int base = 0; base < nm; base += TILE * TILE) {
+    for (int base = 0; base < nm; base += CAP) {
         const int l = base + t;
         bool rel = false;
         Rec<C> r;
-        if (l < nm) {
+        if (t < CAP && l < nm) {
             r = recs[m0 + l];
-            rel = r.i0 <= x0 + TILE - 1 && r.i0 + 2 >= x0 && r.j0 <= y0 + TILE - 1 && r.j0 + 2 >= y0;
+            rel = r.i0 <= x0 + TX - 1 && r.i0 + 2 >= x0 && r.j0 <= y0 + TY - 1 && r.j0 + 2 >= y0;
         }
         // order-preserving compaction of the relevant records
         const unsigned bal = __ballot_sync(0xffffffffu, rel);
         if (lane == 0) wcount[wid] = __popc(bal);
         __syncthreads();
         int off = 0, total = 0;
-        for (int w = 0; w < TILE * TILE / 32; ++w) {
+        for (int w = 0; w < TX * TY / 32; ++w) {
             off += (w < wid) ? wcount[w] : 0;
             total += wcount[w];
         }
@@ -280,19 +384,27 @@ __global__ void __launch_bounds__(TILE * TILE) k_spread(SpreadArgs a) {
 
 size_t rec_bytes(int prec) { return prec == LBM_FP64 ? sizeof(Rec<double>) : sizeof(Rec<float>); }
 
-cudaError_t launch_particles(int prec, const ParticleArgs& a, int np, cudaStream_t s) {
-    if (np <= 0) return cudaSuccess;
-    if (prec == LBM_FP64) k_particles<double, double><<<np, PT, 0, s>>>(a);
-    else if (prec == LBM_FP32) k_particles<float, float><<<np, PT, 0, s>>>(a);
-    else k_particles<__half, float><<<np, PT, 0, s>>>(a);
+cudaError_t launch_probes(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (prec == LBM_FP64) k_probes<double, double><<<nblocks, 32, 0, s>>>(a);
+    else if (prec == LBM_FP32) k_probes<float, float><<<nblocks, 32, 0, s>>>(a);
+    else k_probes<__half, float><<<nblocks, 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_markers(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (prec == LBM_FP64) k_markers<double, double><<<nblocks, 32, 0, s>>>(a);
+    else if (prec == LBM_FP32) k_markers<float, float><<<nblocks, 32, 0, s>>>(a);
+    else k_markers<__half, float><<<nblocks, 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_spread(int prec, const SpreadArgs& a, int np, int tiles, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     const dim3 g(tiles, np);
-    if (prec == LBM_FP64) k_spread<double><<<g, TILE * TILE, 0, s>>>(a);
-    else k_spread<float><<<g, TILE * TILE, 0, s>>>(a);
+    if (prec == LBM_FP64) k_spread<double><<<g, TX * TY, 0, s>>>(a);
+    else k_spread<float><<<g, TX * TY, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ def oracle_factory(nx, ny, tau, **kw):
 
 def gpu_factory(prec):
     def make(nx, ny, tau, **kw):
-        return lbib.Simulation(nx, ny, tau, precision=prec, **kw)
+        return lbib.Simulation(nx, ny, tau, precision=prec, max_particles=256, **kw)
     return make
 
 

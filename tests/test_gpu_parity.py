@@ -222,3 +222,17 @@ def test_large_lattice_with_particles_runs_clean():
         # accelerating toward the local undisturbed velocity
         ul = -U + 2 * U * q.yc / H
         assert p["u"][0] * ul >= 0
+
+
+def test_graph_replay_matches_direct_launches():
+    """lbm_step replays a captured 32-step graph for long runs: the result is
+    bitwise that of launching the steps one call at a time."""
+    wl = _coupled("box", W.ELLIPSE, (14.0, 7.0), 33.4, 22.6).with_(steps=0)
+    a = W.run_with(gpu_factory(FP32), wl)
+    b = W.run_with(gpu_factory(FP32), wl)
+    a.step(70)          # two graph replays + 6 direct steps
+    for _ in range(70):
+        b.step(1)
+    assert a.steps_done == b.steps_done == 70
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    assert a.particles() == b.particles()
