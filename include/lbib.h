@@ -178,6 +178,39 @@ lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f);
 /* Particle states (host); *n receives the particle count. */
 lbm_status lbm_get_particles(lbm_ctx* ctx, lbm_particle_state* out, int32_t cap, int32_t* n);
 
+/*
+ * lbm_step_static -- the paper has no counterpart: this is a deployment
+ * variant of lbm_step for callers that cannot allocate device memory while
+ * they run, e.g. a host program whose device memory all comes from a
+ * fixed pool set up at start-up, or one that must never let an allocation
+ * stall or synchronise the device mid-run.  It advances nsteps steps
+ * exactly as lbm_step does (same kernels, same order, same results) but
+ * keeps the immersed-boundary scratch -- per marker block force/torque
+ * sums, per-particle completion counters and support boxes, per-marker
+ * spreading records -- in one static device array of
+ * LBM_STATIC_SCRATCH_BYTES compiled into the library, instead of in the
+ * context's workspace.  It allocates nothing: no cudaMalloc, no cudaFree,
+ * no allocating library routine; the populations and particle state it
+ * reads and writes are the context's, as for lbm_step.
+ *  - Limits: at most LBM_STATIC_MAX_PARTICLES particles and
+ *    LBM_STATIC_MAX_MARKERS markers in the context, else LBM_EINVAL with
+ *    the reason in lbm_last_error.
+ *  - The static array is held by every GPU that loads the library until
+ *    the process exits.  The first call on a device looks up its device
+ *    address (once per device, with that device current); make that first
+ *    call before any stream capture.
+ *  - All calls share the one array, which keeps the last call's contents;
+ *    each call clears the counters that must start at zero.  Calls that
+ *    overlap on the GPU (other streams, other contexts, other threads)
+ *    race on the array: serialise them.
+ *  - Launches directly on the context's stream, asynchronously; errors as
+ *    for lbm_step.
+ */
+#define LBM_STATIC_SCRATCH_BYTES (3u << 20)
+#define LBM_STATIC_MAX_PARTICLES 1024
+#define LBM_STATIC_MAX_MARKERS 16384
+lbm_status lbm_step_static(lbm_ctx* ctx, int32_t nsteps);
+
 /* Steps done since lbm_init. */
 int64_t lbm_steps_done(const lbm_ctx* ctx);
 

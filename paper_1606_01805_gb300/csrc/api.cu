@@ -529,3 +529,106 @@ void lbm_destroy(lbm_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// lbm_step_static: the step with the immersed-boundary scratch in a static
+// device array instead of the context's workspace (see include/lbib.h).
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+// Scratch shared by every lbm_step_static call in the process, on every
+// device that loads this library, until the process exits.
+static __device__ __align__(256) unsigned char g_ib_scratch[LBM_STATIC_SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[MAX_DEVICES] = {};
+
+// Device address of g_ib_scratch on the current device (host code only sees
+// a host-side stand-in under that name).  Looked up once per device.
+cudaError_t static_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_ib_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_step_static(lbm_ctx* ctx, int32_t nsteps) {
+    if (!ctx || nsteps < 0) return LBM_EINVAL;
+    if (ctx->np > LBM_STATIC_MAX_PARTICLES || ctx->nmark > LBM_STATIC_MAX_MARKERS)
+        return fail(ctx, LBM_EINVAL,
+                    "lbm_step_static: more than " + std::to_string(LBM_STATIC_MAX_PARTICLES) +
+                        " particles or " + std::to_string(LBM_STATIC_MAX_MARKERS) +
+                        " markers do not fit its static scratch");
+    // layout of this context's scratch inside the static array
+    size_t o = 0;
+    const size_t o_partial = o; o = up(o + 3 * (size_t)ctx->nblk * sizeof(double));
+    const size_t o_count = o;   o = up(o + (size_t)ctx->np * sizeof(unsigned));
+    const size_t o_boxes = o;   o = up(o + (size_t)ctx->np * sizeof(int4));
+    const size_t o_recs = o;    o = up(o + (size_t)ctx->nmark * rec_bytes(ctx->prec));
+    if (o > LBM_STATIC_SCRATCH_BYTES)
+        return fail(ctx, LBM_EINVAL, "lbm_step_static: scratch needs exceed LBM_STATIC_SCRATCH_BYTES");
+    void* base = nullptr;
+    CK(static_scratch(&base));
+    char* sb = static_cast<char*>(base);
+    // the per-particle completion counters must start at zero; everything
+    // else is written before it is read within each step
+    if (ctx->np > 0) CK(cudaMemsetAsync(sb + o_count, 0, (size_t)ctx->np * sizeof(unsigned), ctx->stream));
+    for (int32_t k = 0; k < nsteps; ++k) {
+        const void* fcur = ctx->f[ctx->cur];
+        if (ctx->np > 0) {
+            ParticleArgs pa;
+            pa.f = fcur;
+            pa.G = ctx->G;
+            pa.parts = ctx->parts;
+            pa.blk = ctx->blk;
+            pa.partial = reinterpret_cast<double*>(sb + o_partial);
+            pa.count = reinterpret_cast<unsigned*>(sb + o_count);
+            pa.rb = ctx->rb;
+            pa.nb = ctx->nb;
+            pa.S = ctx->S;
+            pa.recs = sb + o_recs;
+            pa.boxes = reinterpret_cast<int4*>(sb + o_boxes);
+            pa.err = ctx->err;
+            pa.gravity[0] = ctx->cfg.gravity[0];
+            pa.gravity[1] = ctx->cfg.gravity[1];
+            pa.weight = ctx->cfg.weight;
+            CK(launch_probes(ctx->prec, pa, ctx->nblk, ctx->stream));
+            CK(launch_markers(ctx->prec, pa, ctx->nblk, ctx->stream));
+            SpreadArgs sa;
+            sa.G = ctx->G;
+            sa.parts = ctx->parts;
+            sa.recs = pa.recs;
+            sa.boxes = pa.boxes;
+            sa.flb = ctx->flb;
+            sa.flags = ctx->flags;
+            sa.err = ctx->err;
+            const double ext = 2.0 * ctx->rc_max + 4.0;
+            const int tiles = ((int)std::ceil(ext / 32.0) + 1) * ((int)std::ceil(ext / 16.0) + 1);
+            CK(launch_spread(ctx->prec, sa, ctx->np, tiles, ctx->stream));
+        }
+        FluidArgs fa;
+        fa.fin = fcur;
+        fa.fout = ctx->f[ctx->cur ^ 1];
+        fa.flb = ctx->flb;
+        fa.flags = ctx->flags;
+        fa.G = ctx->G;
+        CK(launch_fluid(ctx->prec, fa, ctx->stream));
+        ctx->cur ^= 1;
+        ctx->steps += 1;
+    }
+    return LBM_OK;
+}

@@ -29,7 +29,9 @@ LBM_W_EXP, LBM_W_CUBIC, LBM_W_QUARTIC, LBM_W_COSINE, LBM_W_POLY = range(5)
 # every symbol include/lbib.h declares
 EXPORTS = ["lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "lbm_step_timed",
            "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
-           "lbm_get_particles", "lbm_steps_done", "lbm_last_error", "lbm_destroy"]
+           "lbm_get_particles", "lbm_steps_done", "lbm_last_error", "lbm_destroy",
+           "lbm_step_static"]
+LBM_STATIC_MAX_PARTICLES, LBM_STATIC_MAX_MARKERS = 1024, 16384
 
 
 class lbm_config(C.Structure):
@@ -95,9 +97,10 @@ def load(path: os.PathLike | str | None = None):
     L.lbm_last_error.argtypes = [C.c_void_p]
     L.lbm_destroy.argtypes = [C.c_void_p]
     L.lbm_destroy.restype = None
+    L.lbm_step_static.argtypes = [C.c_void_p, C.c_int32]
     for fn in ("lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "lbm_step_timed",
                "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
-               "lbm_get_particles"):
+               "lbm_get_particles", "lbm_step_static"):
         getattr(L, fn).restype = C.c_int
     _lib = L
     return L
