@@ -186,8 +186,8 @@ lbm_status lbm_get_particles(lbm_ctx* ctx, lbm_particle_state* out, int32_t cap,
  * stall or synchronise the device mid-run.  It advances nsteps steps
  * exactly as lbm_step does (same kernels, same order, same results) but
  * keeps the immersed-boundary scratch -- per marker block force/torque
- * sums, per-particle completion counters and support boxes, per-marker
- * spreading records -- in one static device array of
+ * sums, per-particle support boxes, per-marker spreading records -- in one
+ * static device array of
  * LBM_STATIC_SCRATCH_BYTES compiled into the library, instead of in the
  * context's workspace.  It allocates nothing: no cudaMalloc, no cudaFree,
  * no allocating library routine; the populations and particle state it
@@ -200,9 +200,10 @@ lbm_status lbm_get_particles(lbm_ctx* ctx, lbm_particle_state* out, int32_t cap,
  *    address (once per device, with that device current); make that first
  *    call before any stream capture.
  *  - All calls share the one array, which keeps the last call's contents;
- *    each call clears the counters that must start at zero.  Calls that
- *    overlap on the GPU (other streams, other contexts, other threads)
- *    race on the array: serialise them.
+ *    nothing in it has to start at zero (every entry is reset or written
+ *    before it is read within a step).  Calls that overlap on the GPU
+ *    (other streams, other contexts, other threads) race on the array:
+ *    serialise them.
  *  - Launches directly on the context's stream, asynchronously; errors as
  *    for lbm_step.
  */

@@ -26,10 +26,9 @@ struct lbm_ctx {
     int cur = 0;
     void* flb;
     uint8_t* flags;
-    DParticle* parts;
+    DParticle* parts;         // two state buffers of cap_particles each
     int4* blk;
     double* partial;
-    unsigned* count;
     double2* rb;
     double2* nb;
     double* S;
@@ -45,6 +44,8 @@ struct lbm_ctx {
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // GRAPH_STEPS steps from buffer 0 / 1
     bool graphs_ok = true;
+    cudaGraphExec_t timed[2] = {nullptr, nullptr};  // one step with its timing events
+    bool timed_ok = true;
     std::string msg;
 };
 
@@ -54,7 +55,7 @@ constexpr size_t ALIGN = 256;
 size_t up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t f0, f1, flb, flags, parts, blk, partial, count, rb, nb, S, recs, boxes, err, scratch, total;
+    size_t f0, f1, flb, flags, parts, blk, partial, rb, nb, S, recs, boxes, err, scratch, total;
     int pitch, nseg, scratch_rows;
 };
 
@@ -93,11 +94,10 @@ Layout layout(const lbm_config& c) {
     L.f1 = o; o = up(o + 9 * plane * storage_bytes(prec));
     L.flb = o; o = up(o + 2 * plane * compute_bytes(prec));
     L.flags = o; o = up(o + (size_t)c.ny * L.nseg);
-    L.parts = o; o = up(o + P * sizeof(DParticle));
+    L.parts = o; o = up(o + 2 * P * sizeof(DParticle));
     const size_t NB = cap_blocks(c);
     L.blk = o; o = up(o + NB * sizeof(int4));
     L.partial = o; o = up(o + 3 * NB * sizeof(double));
-    L.count = o; o = up(o + P * sizeof(unsigned));
     L.rb = o; o = up(o + M * sizeof(double2));
     L.nb = o; o = up(o + M * sizeof(double2));
     L.S = o; o = up(o + M * sizeof(double));
@@ -136,18 +136,20 @@ lbm_status device_error(lbm_ctx* ctx) {
 
 constexpr int GRAPH_STEPS = 32;  // even, so a replay returns to the same buffer
 
-// one time step from buffer `cur` on stream `st`: particles (probes, rigid
-// update, markers) -> spreading -> fluid.  Bookkeeping is the caller's.
-lbm_status enqueue_step(lbm_ctx* ctx, cudaStream_t st, int cur, cudaEvent_t mid) {
+// Part of one time step from buffer `cur` on stream `st`: the immersed-
+// boundary kernels (ib = true: probes / rigid update / markers, spreading)
+// or the fused fluid kernel (ib = false).  Bookkeeping is the caller's.
+lbm_status enqueue_step_part(lbm_ctx* ctx, cudaStream_t st, int cur, bool ib) {
     const void* fcur = ctx->f[cur];
-    if (ctx->np > 0) {
+    if (ib) {
+        if (ctx->np == 0) return LBM_OK;
         ParticleArgs pa;
         pa.f = fcur;
         pa.G = ctx->G;
-        pa.parts = ctx->parts;
+        pa.pin = ctx->parts + (size_t)cur * cap_particles(ctx->cfg);
+        pa.pout = ctx->parts + (size_t)(cur ^ 1) * cap_particles(ctx->cfg);
         pa.blk = ctx->blk;
         pa.partial = ctx->partial;
-        pa.count = ctx->count;
         pa.rb = ctx->rb;
         pa.nb = ctx->nb;
         pa.S = ctx->S;
@@ -171,8 +173,8 @@ lbm_status enqueue_step(lbm_ctx* ctx, cudaStream_t st, int cur, cudaEvent_t mid)
         const double ext = 2.0 * ctx->rc_max + 4.0;
         const int tiles = ((int)std::ceil(ext / 32.0) + 1) * ((int)std::ceil(ext / 16.0) + 1);
         CK(launch_spread(ctx->prec, sa, ctx->np, tiles, st));
+        return LBM_OK;
     }
-    if (mid) CK(cudaEventRecord(mid, st));
     FluidArgs fa;
     fa.fin = fcur;
     fa.fout = ctx->f[cur ^ 1];
@@ -181,6 +183,15 @@ lbm_status enqueue_step(lbm_ctx* ctx, cudaStream_t st, int cur, cudaEvent_t mid)
     fa.G = ctx->G;
     CK(launch_fluid(ctx->prec, fa, st));
     return LBM_OK;
+}
+
+// one time step from buffer `cur` on stream `st` (mid: optional event
+// between the IB kernels and the fluid kernel).  Bookkeeping is the caller's.
+lbm_status enqueue_step(lbm_ctx* ctx, cudaStream_t st, int cur, cudaEvent_t mid) {
+    lbm_status s = enqueue_step_part(ctx, st, cur, true);
+    if (s != LBM_OK) return s;
+    if (mid) CK(cudaEventRecord(mid, st));
+    return enqueue_step_part(ctx, st, cur, false);
 }
 
 // Capture GRAPH_STEPS steps starting from buffer `cur` on a private stream
@@ -204,6 +215,38 @@ bool capture_graph(lbm_ctx* ctx, int cur) {
     return ok;
 }
 
+// enqueue_step for capture: the event between the IB kernels and the fluid
+// kernel is an external record, i.e. a real event-record node
+lbm_status enqueue_timed_step(lbm_ctx* ctx, cudaStream_t st, int cur) {
+    lbm_status s = enqueue_step_part(ctx, st, cur, true);
+    if (s != LBM_OK) return s;
+    CK(cudaEventRecordWithFlags(ctx->ev[1], st, cudaEventRecordExternal));
+    return enqueue_step_part(ctx, st, cur, false);
+}
+
+// One step from buffer `cur` with the three timing events recorded inside
+// the graph (same launches as enqueue_step, replayed like lbm_step replays).
+bool capture_timed(lbm_ctx* ctx, int cur) {
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return false;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        // external records: real event-record nodes, not capture-internal
+        // dependencies
+        ok = cudaEventRecordWithFlags(ctx->ev[0], cs, cudaEventRecordExternal) == cudaSuccess &&
+             enqueue_timed_step(ctx, cs, cur) == LBM_OK &&
+             cudaEventRecordWithFlags(ctx->ev[2], cs, cudaEventRecordExternal) == cudaSuccess;
+        cudaGraph_t g = nullptr;
+        const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
+        ok = ok && ended && g && cudaGraphInstantiate(&ctx->timed[cur], g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+    }
+    cudaStreamDestroy(cs);
+    cudaGetLastError();
+    if (!ok) ctx->timed[cur] = nullptr;
+    return ok;
+}
+
 }  // namespace
 
 extern "C" {
@@ -220,6 +263,7 @@ lbm_status lbm_workspace_bytes(const lbm_config* cfg, size_t* bytes) {
 
 lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
     if (!out) return LBM_EINVAL;
+    cudaGetLastError();  // a stale error of earlier work must not fail this context
     *out = nullptr;
     if (check_config(cfg)) return LBM_EINVAL;
     const Layout L = layout(*cfg);
@@ -250,7 +294,6 @@ lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
     ctx->parts = reinterpret_cast<DParticle*>(b + L.parts);
     ctx->blk = reinterpret_cast<int4*>(b + L.blk);
     ctx->partial = reinterpret_cast<double*>(b + L.partial);
-    ctx->count = reinterpret_cast<unsigned*>(b + L.count);
     ctx->rb = reinterpret_cast<double2*>(b + L.rb);
     ctx->nb = reinterpret_cast<double2*>(b + L.nb);
     ctx->S = reinterpret_cast<double*>(b + L.S);
@@ -341,6 +384,8 @@ lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* d, int32_t* o
     P.rho_s = d->rho_s;
     P.mass = d->rho_s * so.area;
     P.inertia = P.mass * so.inertia_per_mass;
+    P.inv_mass = 1.0 / P.mass;
+    P.inv_inertia = 1.0 / P.inertia;
     P.m0 = ctx->nmark;
     P.nm = n;
     P.b0 = ctx->nblk;
@@ -357,7 +402,9 @@ lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* d, int32_t* o
     CK(cudaMemcpyAsync(ctx->rb + P.m0, r2.data(), n * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->nb + P.m0, n2.data(), n * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->S + P.m0, S.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->parts + ctx->np, &P, sizeof P, cudaMemcpyHostToDevice, ctx->stream));
+    for (int buf = 0; buf < 2; ++buf)
+        CK(cudaMemcpyAsync(ctx->parts + (size_t)buf * cap_particles(ctx->cfg) + ctx->np, &P, sizeof P,
+                           cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->blk + P.b0, blocks.data(), P.nblk * sizeof(int4), cudaMemcpyHostToDevice,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -398,12 +445,19 @@ lbm_status lbm_step_timed(lbm_ctx* ctx, int32_t nsteps, double* ms_step, double*
         if (!e) CK(cudaEventCreate(&e));
     double tot = 0, flu = 0;
     for (int32_t k = 0; k < nsteps; ++k) {
-        CK(cudaEventRecord(ctx->ev[0], ctx->stream));
-        lbm_status s = enqueue_step(ctx, ctx->stream, ctx->cur, ctx->ev[1]);
-        if (s != LBM_OK) return s;
+        // each step is a replay of its captured one-step graph (as lbm_step
+        // replays steps), with the timing events inside it
+        if (ctx->timed_ok && !ctx->timed[ctx->cur] && !capture_timed(ctx, ctx->cur)) ctx->timed_ok = false;
+        if (ctx->timed_ok) {
+            CK(cudaGraphLaunch(ctx->timed[ctx->cur], ctx->stream));
+        } else {
+            CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+            lbm_status s = enqueue_step(ctx, ctx->stream, ctx->cur, ctx->ev[1]);
+            if (s != LBM_OK) return s;
+            CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+        }
         ctx->cur ^= 1;
         ctx->steps += 1;
-        CK(cudaEventRecord(ctx->ev[2], ctx->stream));
         CK(cudaEventSynchronize(ctx->ev[2]));
         float a = 0, b = 0;
         CK(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[2]));
@@ -497,7 +551,9 @@ lbm_status lbm_get_particles(lbm_ctx* ctx, lbm_particle_state* out, int32_t cap,
     if (n) *n = ctx->np;
     if (ctx->np == 0 || !out || cap <= 0) return s;
     std::vector<DParticle> h(ctx->np);
-    CK(cudaMemcpyAsync(h.data(), ctx->parts, ctx->np * sizeof(DParticle), cudaMemcpyDeviceToHost, ctx->stream));
+    const DParticle* cur_state = ctx->parts + (size_t)ctx->cur * cap_particles(ctx->cfg);
+    CK(cudaMemcpyAsync(h.data(), cur_state, ctx->np * sizeof(DParticle), cudaMemcpyDeviceToHost,
+                       ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     for (int i = 0; i < std::min<int>(cap, ctx->np); ++i) {
         out[i].xc = h[i].X[0][0];
@@ -523,6 +579,8 @@ void lbm_destroy(lbm_ctx* ctx) {
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
     for (auto& g : ctx->graph)
+        if (g) cudaGraphExecDestroy(g);
+    for (auto& g : ctx->timed)
         if (g) cudaGraphExecDestroy(g);
     if (ctx->owns_ws) cudaFree(ctx->ws);
     delete ctx;
@@ -576,7 +634,6 @@ extern "C" lbm_status lbm_step_static(lbm_ctx* ctx, int32_t nsteps) {
     // layout of this context's scratch inside the static array
     size_t o = 0;
     const size_t o_partial = o; o = up(o + 3 * (size_t)ctx->nblk * sizeof(double));
-    const size_t o_count = o;   o = up(o + (size_t)ctx->np * sizeof(unsigned));
     const size_t o_boxes = o;   o = up(o + (size_t)ctx->np * sizeof(int4));
     const size_t o_recs = o;    o = up(o + (size_t)ctx->nmark * rec_bytes(ctx->prec));
     if (o > LBM_STATIC_SCRATCH_BYTES)
@@ -584,19 +641,19 @@ extern "C" lbm_status lbm_step_static(lbm_ctx* ctx, int32_t nsteps) {
     void* base = nullptr;
     CK(static_scratch(&base));
     char* sb = static_cast<char*>(base);
-    // the per-particle completion counters must start at zero; everything
-    // else is written before it is read within each step
-    if (ctx->np > 0) CK(cudaMemsetAsync(sb + o_count, 0, (size_t)ctx->np * sizeof(unsigned), ctx->stream));
+    // nothing in the scratch has to start at zero: within each step the
+    // probe kernel resets the boxes and every other entry is written before
+    // it is read
     for (int32_t k = 0; k < nsteps; ++k) {
         const void* fcur = ctx->f[ctx->cur];
         if (ctx->np > 0) {
             ParticleArgs pa;
             pa.f = fcur;
             pa.G = ctx->G;
-            pa.parts = ctx->parts;
+            pa.pin = ctx->parts + (size_t)ctx->cur * cap_particles(ctx->cfg);
+            pa.pout = ctx->parts + (size_t)(ctx->cur ^ 1) * cap_particles(ctx->cfg);
             pa.blk = ctx->blk;
             pa.partial = reinterpret_cast<double*>(sb + o_partial);
-            pa.count = reinterpret_cast<unsigned*>(sb + o_count);
             pa.rb = ctx->rb;
             pa.nb = ctx->nb;
             pa.S = ctx->S;

@@ -8,22 +8,37 @@ namespace {
 
 constexpr int BY = 8;  // rows per block; blockDim = (32, BY), one warp per row segment
 
-// shifted equilibrium f~eq_i = f_eq_i - w_i (Eq. 2) and the Guo term (Eq. 5),
-// then the BGK relaxation of Eq. 4, all in place on v
+// BGK relaxation of Eq. 4 towards the shifted equilibrium f~eq_i = f_eq_i - w_i
+// (Eq. 2), plus the Guo term (Eq. 5), in place on v.  Written over opposite
+// velocity pairs (i, i'): with e_i' = -e_i, both terms split into a part even
+// in e (shared) and a part odd in e (sign-flipped), so each pair costs one
+// evaluation: f~eq = w (drho + rho (4.5 (e.u)^2 - 1.5 u.u)) +- 3 w rho e.u and
+// G = (1 - omega/2) w [(9 (e.u)(e.F) - 3 u.F) +- 3 e.F].
 template <class C>
 __device__ __forceinline__ void collide(C v[9], C drho, C ux, C uy, C Fx, C Fy, C omega) {
     const C rho = C(1) + drho;
     const C usq = ux * ux + uy * uy;
     const C cf = C(1) - C(0.5) * omega;
+    const C uF = ux * Fx + uy * Fy;
+    {  // rest population
+        const C w = C(4.0 / 9.0);
+        const C feq = w * (drho - C(1.5) * rho * usq);
+        v[0] = v[0] - omega * (v[0] - feq) - C(3) * cf * w * uF;
+    }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
+    for (int p = 0; p < 4; ++p) {
+        // pairs (1,3), (2,4), (5,7), (6,8): i has e = (ex, ey), i' has -e
+        const int i = p == 0 ? 1 : p == 1 ? 2 : p == 2 ? 5 : 6;
+        const int j = p == 0 ? 3 : p == 1 ? 4 : p == 2 ? 7 : 8;
         const C w = C(wt(i));
         const C eu = C(cx(i)) * ux + C(cy(i)) * uy;
-        const C feq = w * (drho + rho * (C(3) * eu + C(4.5) * eu * eu - C(1.5) * usq));
-        const C gi = cf * w *
-                     ((C(3) * (C(cx(i)) - ux) + C(9) * eu * C(cx(i))) * Fx +
-                      (C(3) * (C(cy(i)) - uy) + C(9) * eu * C(cy(i))) * Fy);
-        v[i] = v[i] - omega * (v[i] - feq) + gi;
+        const C eF = C(cx(i)) * Fx + C(cy(i)) * Fy;
+        const C even = w * (drho + rho * (C(4.5) * eu * eu - C(1.5) * usq));
+        const C odd = C(3) * w * rho * eu;
+        const C geven = cf * w * (C(9) * eu * eF - C(3) * uF);
+        const C godd = C(3) * cf * w * eF;
+        v[i] = v[i] - omega * (v[i] - (even + odd)) + (geven + godd);
+        v[j] = v[j] - omega * (v[j] - (even - odd)) + (geven - godd);
     }
 }
 
@@ -81,8 +96,13 @@ __device__ __forceinline__ void cell_update(C v[9], const Geo& G, C fx_ib, C fy_
 // as 16-byte vectors: a pull along +-x is a one-lane shuffle of the
 // neighbouring vector, with one extra element load at the warp's two ends.
 // Cells on a wall or periodic edge take the per-cell general path.
+// resident blocks per SM the register budget is sized for (FP64 values
+// take two registers each)
+template <class S> struct FluidOccupancy { static constexpr int value = 4; };
+template <> struct FluidOccupancy<double> { static constexpr int value = 2; };
+
 template <class S, class C>
-__global__ void __launch_bounds__(32 * BY) k_fluid(FluidArgs a) {
+__global__ void __launch_bounds__(32 * BY, FluidOccupancy<S>::value) k_fluid(FluidArgs a) {
     const Geo& G = a.G;
     const S* __restrict__ fin = static_cast<const S*>(a.fin);
     S* __restrict__ fout = static_cast<S*>(a.fout);
@@ -134,34 +154,50 @@ __global__ void __launch_bounds__(32 * BY) k_fluid(FluidArgs a) {
                     flb[G.plane + row + x0 + k] = C(0);
                 }
         }
-        C out[9][4];
+        // interior cells from the vector values
+        unsigned edge = 0;  // bit k: cell x0 + k lies on an edge (and inside the lattice)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            C c[9];
             const int xk = x0 + k;
             if (rows_in && xk >= 1 && xk <= G.nx - 2) {
+                C c[9];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) c[i] = v[i][k];
+                cell_update<C>(c, G, fxi[k], fyi[k]);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) v[i][k] = c[i];
             } else if (xk < G.nx) {
-                pull_general<S, C>(fin, G, xk, y, c);
-                complete_walls<S, C>(fin, G, xk, y, c);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 9; ++i) c[i] = C(0);
+                edge |= 1u << k;
             }
-            cell_update<C>(c, G, fxi[k], fyi[k]);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) out[i][k] = c[i];
         }
-        if (x0 + 3 < G.nx) {
+        if (edge == 0 && x0 + 3 < G.nx) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) Vec4<S, C>::store(fout + (long long)i * G.plane + row + x0, out[i]);
+            for (int i = 0; i < 9; ++i) Vec4<S, C>::store(fout + (long long)i * G.plane + row + x0, v[i]);
         } else {
 #pragma unroll
-            for (int i = 0; i < 9; ++i)
+            for (int k = 0; k < 4; ++k)
+                if (x0 + k < G.nx && !(edge >> k & 1u)) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (x0 + k < G.nx) st<S, C>(fout + (long long)i * G.plane + row + x0 + k, out[i][k]);
+                    for (int i = 0; i < 9; ++i) st<S, C>(fout + (long long)i * G.plane + row + x0 + k, v[i][k]);
+                }
+            // cells on a wall or periodic edge: general pull, wall completion,
+            // collision, one at a time (emitted once, nothing else live)
+#pragma unroll 1
+            for (int k = 0; k < 4; ++k) {
+                if (!(edge >> k & 1u)) continue;
+                const int xk = x0 + k;
+                C c[9];
+                pull_general<S, C>(fin, G, xk, y, c);
+                complete_walls<S, C>(fin, G, xk, y, c);
+                C gx = C(0), gy = C(0);
+                if (forced) {  // forces of this cell were read (and zeroed) above
+                    gx = k == 0 ? fxi[0] : k == 1 ? fxi[1] : k == 2 ? fxi[2] : fxi[3];
+                    gy = k == 0 ? fyi[0] : k == 1 ? fyi[1] : k == 2 ? fyi[2] : fyi[3];
+                }
+                cell_update<C>(c, G, gx, gy);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) st<S, C>(fout + (long long)i * G.plane + row + xk, c[i]);
+            }
         }
     }
     __syncwarp();

@@ -32,7 +32,7 @@ struct DParticle {
     double X[2][2], th[2], U[2][2], W[2];
     double cs[2][2];          // (cos, sin) of th[0] and th[1]
     double F[2], M;
-    double mass, inertia, area, rho_s;
+    double mass, inertia, area, rho_s, inv_mass, inv_inertia;
     int m0, nm;               // first marker, marker count
     int b0, nblk;             // first marker block, marker blocks (MB markers each)
     long long nupd;           // rigid-body updates done
@@ -43,7 +43,7 @@ constexpr int MB = 8;         // markers per block of the marker kernels (one wa
 // Spreading record of one marker: the unwrapped lower-left node (i0, j0) of
 // its 3x3 support and the 9 contributions S_l phi_k F_l (Eq. 12).
 template <class C>
-struct Rec {
+struct __align__(16) Rec {
     int i0, j0;
     C cx[9], cy[9];
 };
@@ -51,13 +51,16 @@ struct Rec {
 // Device error bits (OR-ed into the error word).
 enum : unsigned { ERR_DOMAIN = 1u, ERR_NONFINITE = 2u, ERR_TIMEOUT = 4u };
 
+// The particle state is double-buffered with the populations: a step that
+// reads populations buffer c reads particles pin = state[c] and writes the
+// updated bodies to pout = state[c ^ 1].
 struct ParticleArgs {
     const void* f;            // post-collision populations (storage type)
     Geo G;
-    DParticle* parts;
+    const DParticle* pin;     // bodies at the start of the step
+    DParticle* pout;          // bodies after the rigid-body update
     const int4* blk;          // per marker block: (particle, first marker, markers, 0)
     double* partial;          // per marker block: F_x, F_y, M partial sums
-    unsigned* count;          // per particle: marker blocks done (reset by the last)
     const double2* rb;        // body-frame marker positions
     const double2* nb;        // body-frame normals
     const double* S;          // marker arc lengths
@@ -70,7 +73,7 @@ struct ParticleArgs {
 
 struct SpreadArgs {
     Geo G;
-    const DParticle* parts;
+    const DParticle* parts;   // either state buffer (marker ranges only)
     const void* recs;
     const int4* boxes;
     void* flb;                // 2 planes of compute type

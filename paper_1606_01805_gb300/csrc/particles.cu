@@ -5,13 +5,13 @@
 // each lane's dependency chain covers only 2-3 of the 9 support nodes.
 // k_probes: probe 1.2 dx along the outward normal of each marker of the body
 //   at its latest level, MLS fit of density and velocity there, surface
-//   traction; warp sums of force and torque per block (Eqs. 13-14).  The
-//   last block of a particle to finish (atomic counter, no waiting) adds the
-//   block sums in block order and applies the two-level rigid-body update
-//   (Eqs. 15-16), all in FP64.
-// k_markers: markers at the new level: MLS interpolation (Eq. 8),
-//   direct-forcing force (Eq. 11), the per-marker spreading record
-//   S_l phi_k F_l of Eq. 12 and the particle's support box.
+//   traction; warp sums of force and torque per block (Eqs. 13-14, FP64).
+// k_markers: every block first adds its particle's block sums (fixed lane
+//   assignment and shuffle tree: the same bits in every block) and applies
+//   the two-level rigid-body update (Eqs. 15-16, FP64); the particle's first
+//   block stores the new body.  Then the markers at the new level: MLS
+//   interpolation (Eq. 8), direct-forcing force (Eq. 11), the per-marker
+//   spreading record S_l phi_k F_l of Eq. 12 and the particle's support box.
 // k_spread (one CTA per 32x16 tile of a particle's box): gathers, cell by
 //   cell and in marker order, the records whose support covers the cell,
 //   then adds the particle's sum into f_lb (the only atomic: one add per
@@ -67,17 +67,22 @@ struct QuadMLS {
     int kk[3];
     C phi[3], dpx[3], dpy[3];
 
-    __device__ __forceinline__ void build(int kind, double px, double py, int q, bool active) {
-        const int ic = (int)floor(px + 0.5), jc = (int)floor(py + 0.5);
-        i0 = ic - 1;
-        j0 = jc - 1;
+    // support of (px, py) and the nodes of lane q
+    __device__ __forceinline__ void support(double px, double py, int q) {
+        i0 = (int)floor(px + 0.5) - 1;
+        j0 = (int)floor(py + 0.5) - 1;
         nk = q == 0 ? 3 : 2;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) kk[j] = q + 4 * j;
+    }
+
+    // weights, moment matrix, FP64 solve (after support())
+    __device__ __forceinline__ void build(int kind, double px, double py, int q, bool active) {
         C W[3], DX[3], DY[3];
         double a00 = 0, a01 = 0, a02 = 0, a11 = 0, a12 = 0, a22 = 0;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            const int k = q + 4 * j;
-            kk[j] = k;
+            const int k = kk[j];
             W[j] = C(0);
             DX[j] = C(0);
             DY[j] = C(0);
@@ -124,11 +129,13 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     const S* __restrict__ f = static_cast<const S*>(a.f);
     const Geo& G = a.G;
     const int4 bk = a.blk[blockIdx.x];
-    DParticle* P = a.parts + bk.x;
+    const DParticle* P = a.pin + bk.x;
     const int lane = threadIdx.x, q = lane & (LPM - 1);
     const int ml = lane / LPM, m = bk.y + ml;  // marker (absolute index)
     const bool active = ml < bk.z;
     unsigned err = 0;
+    if (lane == 0 && bk.y == P->m0)  // the particle's first block resets its box
+        a.boxes[bk.x] = make_int4(INT_MAX, INT_MAX, INT_MIN, INT_MIN);
     // body at its latest level
     const double c0 = P->cs[0][0], s0 = P->cs[0][1];
     double2 rb = make_double2(0, 0), nb = make_double2(1, 0);
@@ -140,23 +147,31 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     const double nx = c0 * nb.x - s0 * nb.y, ny = s0 * nb.x + c0 * nb.y;
     const double px = P->X[0][0] + rx + PROBE * nx, py = P->X[0][1] + ry + PROBE * ny;
     QuadMLS<true, C> M;
+    M.support(px, py, q);
+    // node fields first (their loads overlap the FP64 work of the solve)
+    C rk[3], uk[3], vk[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        rk[j] = C(1); uk[j] = C(0); vk[j] = C(0);
+        if (j < M.nk && active) {
+            const int k = M.kk[j];
+            if (!node_fields<S, C>(f, G, M.i0 + k % 3, M.j0 + k / 3, rk[j], uk[j], vk[j])) {
+                err |= ERR_DOMAIN;
+                rk[j] = C(1); uk[j] = C(0); vk[j] = C(0);
+            }
+        }
+    }
     M.build(a.weight, px, py, q, active);
     // MLS fit of rho and grad u at the probe (Section 2.3)
     C r = C(0), uxx = C(0), uxy = C(0), uyx = C(0), uyy = C(0);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         if (j < M.nk && active) {
-            const int k = M.kk[j];
-            C rk, uk, vk;
-            if (!node_fields<S, C>(f, G, M.i0 + k % 3, M.j0 + k / 3, rk, uk, vk)) {
-                err |= ERR_DOMAIN;
-                rk = C(1); uk = C(0); vk = C(0);
-            }
-            r += M.phi[j] * rk;
-            uxx += M.dpx[j] * uk;
-            uxy += M.dpy[j] * uk;
-            uyx += M.dpx[j] * vk;
-            uyy += M.dpy[j] * vk;
+            r += M.phi[j] * rk[j];
+            uxx += M.dpx[j] * uk[j];
+            uxy += M.dpy[j] * uk[j];
+            uyx += M.dpx[j] * vk[j];
+            uyy += M.dpy[j] * vk[j];
         }
     }
     r = quad_sum(r); uxx = quad_sum(uxx); uxy = quad_sum(uxy); uyx = quad_sum(uyx); uyy = quad_sum(uyy);
@@ -182,67 +197,61 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     Fy = warp_sum(Fy);
     Mz = warp_sum(Mz);
     if (err) atomicOr(a.err, err);
-    unsigned done = 0;
     if (lane == 0) {
         double* part = a.partial + 3 * (long long)blockIdx.x;
         part[0] = Fx;
         part[1] = Fy;
         part[2] = Mz;
-        __threadfence();
-        done = atomicAdd(a.count + bk.x, 1u);
     }
-    done = __shfl_sync(0xffffffffu, done, 0);
-    if (done != (unsigned)P->nblk - 1) return;  // whole warp
-    // ---- last block of this particle: all lanes load the block sums (fixed
-    // lane assignment and shuffle tree, so the sum is deterministic)
-    __threadfence();
+}
+
+// Sum of the block force/torque sums of particle P and its rigid-body update
+// (Eqs. 15-16), computed identically by every lane.
+struct Body {
+    double X, Y, T, U, V, W, c, s, F0, F1, M;
+};
+__device__ __forceinline__ Body update_body(const DParticle* P, const double* partial,
+                                            const double gravity[2], int lane) {
     double F0 = 0, F1 = 0, Mt = 0;
     for (int b = P->b0 + lane; b < P->b0 + P->nblk; b += 32) {
-        F0 += __ldcg(a.partial + 3 * (long long)b);
-        F1 += __ldcg(a.partial + 3 * (long long)b + 1);
-        Mt += __ldcg(a.partial + 3 * (long long)b + 2);
+        F0 += partial[3 * (long long)b];
+        F1 += partial[3 * (long long)b + 1];
+        Mt += partial[3 * (long long)b + 2];
     }
-    F0 = warp_sum(F0);
-    F1 = warp_sum(F1);
-    Mt = warp_sum(Mt);
-    if (lane != 0) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {  // butterfly: every lane ends with the total
+        F0 += __shfl_xor_sync(0xffffffffu, F0, o);
+        F1 += __shfl_xor_sync(0xffffffffu, F1, o);
+        Mt += __shfl_xor_sync(0xffffffffu, Mt, o);
+    }
     const double X0 = P->X[0][0], Y0 = P->X[0][1], th0 = P->th[0];
     const double U0 = P->U[0][0], V0 = P->U[0][1], W0 = P->W[0];
     const double buoy = (P->rho_s - 1.0) * P->area;
-    const double ax = (F0 + buoy * a.gravity[0]) / P->mass;
-    const double ay = (F1 + buoy * a.gravity[1]) / P->mass;
-    const double al = Mt / P->inertia;
-    double U, V, W, X, Y, T;
+    const double ax = (F0 + buoy * gravity[0]) * P->inv_mass;
+    const double ay = (F1 + buoy * gravity[1]) * P->inv_mass;
+    const double al = Mt * P->inv_inertia;
+    Body B;
     if (P->nupd == 0) {  // one stored level: u1 = u0 + a, x1 = x0 + u1
-        U = U0 + ax;
-        V = V0 + ay;
-        W = W0 + al;
-        X = X0 + U;
-        Y = Y0 + V;
-        T = th0 + W;
+        B.U = U0 + ax;
+        B.V = V0 + ay;
+        B.W = W0 + al;
+        B.X = X0 + B.U;
+        B.Y = Y0 + B.V;
+        B.T = th0 + B.W;
     } else {  // Eqs. 15-16 and the same two-level form for position and angle
         const double k = 2.0 / 3.0;
-        U = k * (2.0 * U0 - 0.5 * P->U[1][0] + ax);
-        V = k * (2.0 * V0 - 0.5 * P->U[1][1] + ay);
-        W = k * (2.0 * W0 - 0.5 * P->W[1] + al);
-        X = k * (2.0 * X0 - 0.5 * P->X[1][0] + U);
-        Y = k * (2.0 * Y0 - 0.5 * P->X[1][1] + V);
-        T = k * (2.0 * th0 - 0.5 * P->th[1] + W);
+        B.U = k * (2.0 * U0 - 0.5 * P->U[1][0] + ax);
+        B.V = k * (2.0 * V0 - 0.5 * P->U[1][1] + ay);
+        B.W = k * (2.0 * W0 - 0.5 * P->W[1] + al);
+        B.X = k * (2.0 * X0 - 0.5 * P->X[1][0] + B.U);
+        B.Y = k * (2.0 * Y0 - 0.5 * P->X[1][1] + B.V);
+        B.T = k * (2.0 * th0 - 0.5 * P->th[1] + B.W);
     }
-    P->X[1][0] = X0; P->X[1][1] = Y0; P->th[1] = th0;
-    P->U[1][0] = U0; P->U[1][1] = V0; P->W[1] = W0;
-    P->X[0][0] = X; P->X[0][1] = Y; P->th[0] = T;
-    P->U[0][0] = U; P->U[0][1] = V; P->W[0] = W;
-    P->F[0] = F0; P->F[1] = F1; P->M = Mt;
-    P->cs[1][0] = P->cs[0][0]; P->cs[1][1] = P->cs[0][1];
-    double sT, cT;
-    sincos(T, &sT, &cT);
-    P->cs[0][0] = cT; P->cs[0][1] = sT;
-    P->nupd += 1;
-    if (!isfinite(X) || !isfinite(Y) || !isfinite(T) || !isfinite(U) || !isfinite(W))
-        atomicOr(a.err, ERR_NONFINITE);
-    a.count[bk.x] = 0;
-    a.boxes[bk.x] = make_int4(INT_MAX, INT_MAX, INT_MIN, INT_MIN);
+    sincos(B.T, &B.s, &B.c);
+    B.F0 = F0;
+    B.F1 = F1;
+    B.M = Mt;
+    return B;
 }
 
 template <class S, class C>
@@ -250,40 +259,61 @@ __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
     const S* __restrict__ f = static_cast<const S*>(a.f);
     const Geo& G = a.G;
     const int4 bk = a.blk[blockIdx.x];
-    const DParticle* P = a.parts + bk.x;
+    const DParticle* P = a.pin + bk.x;
     Rec<C>* recs = static_cast<Rec<C>*>(a.recs);
     const int lane = threadIdx.x, q = lane & (LPM - 1);
     const int ml = lane / LPM, m = bk.y + ml;  // marker (absolute index)
     const bool active = ml < bk.z;
     unsigned err = 0;
-    const double X = P->X[0][0], Y = P->X[0][1];
-    const double cn = P->cs[0][0], sn = P->cs[0][1];
     const double2 rb = active ? a.rb[m] : make_double2(0, 0);
+    const Body B = update_body(P, a.partial, a.gravity, lane);
+    if (lane == 0 && bk.y == P->m0) {  // the particle's first block stores it
+        DParticle* Q = a.pout + bk.x;
+        *Q = *P;
+        Q->X[1][0] = P->X[0][0]; Q->X[1][1] = P->X[0][1]; Q->th[1] = P->th[0];
+        Q->U[1][0] = P->U[0][0]; Q->U[1][1] = P->U[0][1]; Q->W[1] = P->W[0];
+        Q->cs[1][0] = P->cs[0][0]; Q->cs[1][1] = P->cs[0][1];
+        Q->X[0][0] = B.X; Q->X[0][1] = B.Y; Q->th[0] = B.T;
+        Q->U[0][0] = B.U; Q->U[0][1] = B.V; Q->W[0] = B.W;
+        Q->cs[0][0] = B.c; Q->cs[0][1] = B.s;
+        Q->F[0] = B.F0; Q->F[1] = B.F1; Q->M = B.M;
+        Q->nupd = P->nupd + 1;
+        if (!isfinite(B.X) || !isfinite(B.Y) || !isfinite(B.T) || !isfinite(B.U) || !isfinite(B.W))
+            err |= ERR_NONFINITE;
+    }
+    const double X = B.X, Y = B.Y, cn = B.c, sn = B.s;
     const double rx = cn * rb.x - sn * rb.y, ry = sn * rb.x + cn * rb.y;
     QuadMLS<false, C> M;
+    M.support(X + rx, Y + ry, q);
+    C uk[3], vk[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        uk[j] = C(0); vk[j] = C(0);
+        if (j < M.nk && active) {
+            const int k = M.kk[j];
+            C rk;
+            if (!node_fields<S, C>(f, G, M.i0 + k % 3, M.j0 + k / 3, rk, uk[j], vk[j])) {
+                err |= ERR_DOMAIN;
+                uk[j] = C(0); vk[j] = C(0);
+            }
+        }
+    }
     M.build(a.weight, X + rx, Y + ry, q, active);
     C ux = C(0), uy = C(0);
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
+    for (int j = 0; j < 3; ++j)
         if (j < M.nk && active) {
-            const int k = M.kk[j];
-            C rk, uk, vk;
-            if (!node_fields<S, C>(f, G, M.i0 + k % 3, M.j0 + k / 3, rk, uk, vk)) {
-                err |= ERR_DOMAIN;
-                uk = C(0); vk = C(0);
-            }
-            ux += M.phi[j] * uk;
-            uy += M.phi[j] * vk;
+            ux += M.phi[j] * uk[j];
+            uy += M.phi[j] * vk[j];
         }
-    }
     ux = quad_sum(ux);  // Eq. 8: U(x_l)
     uy = quad_sum(uy);
     int bx0 = INT_MAX, by0 = INT_MAX, bx1 = INT_MIN, by1 = INT_MIN;
     if (active) {
         // Eq. 11 with dt = 1, times the arc length c_l = S_l of Eq. 12
         const double Sl = a.S[m];
-        const C sx = (C)(Sl * ((P->U[0][0] - P->W[0] * ry) - (double)ux));
-        const C sy = (C)(Sl * ((P->U[0][1] + P->W[0] * rx) - (double)uy));
+        const C sx = (C)(Sl * ((B.U - B.W * ry) - (double)ux));
+        const C sy = (C)(Sl * ((B.V + B.W * rx) - (double)uy));
         Rec<C>* rc = recs + m;
 #pragma unroll
         for (int j = 0; j < 3; ++j)

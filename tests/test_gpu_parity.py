@@ -236,3 +236,16 @@ def test_graph_replay_matches_direct_launches():
     assert a.steps_done == b.steps_done == 70
     np.testing.assert_array_equal(a.populations(), b.populations())
     assert a.particles() == b.particles()
+
+
+def test_timed_steps_match_plain_steps():
+    """lbm_step_timed (one-step graphs with timing events) advances the state
+    exactly as lbm_step does."""
+    wl = _coupled("channel", W.CIRCLE, (12.0,), 30.3, 22.1, n=48).with_(steps=0)
+    a = W.run_with(gpu_factory(FP32), wl)
+    b = W.run_with(gpu_factory(FP32), wl)
+    ms_step, ms_fluid = a.step_timed(9)
+    b.step(9)
+    assert ms_step > ms_fluid > 0
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    assert a.particles() == b.particles()
