@@ -35,7 +35,10 @@ PREC_NAMES = {0: "f64", 1: "f32", 2: "f16-storage/f32"}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per fluid-kernel launch from one
 # ncu capture, keyed by the hash of the kernel sources it was taken on
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # k_fluid<float,float>, sedimentation 400 x 1200 (profiles/k_fluid_sedimentation_400x1200.md)
+    ("6cb43485324753bc", "sedimentation_circle_400x1200", 1): 18064640 + 14336,
+}
 
 
 def kernel_hash():
@@ -278,7 +281,7 @@ def main():
     peak, peak_kind = hbm_peak()
     algo_bytes = BYTES_PER_CELL[prec] * cells
     achieved = algo_bytes / (ms_fluid * 1e-3 / args.steps) / 1e9
-    traffic = NCU_TRAFFIC.get(kernel_hash())
+    traffic = NCU_TRAFFIC.get((kernel_hash(), wl.name, prec))
     out = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step / args.steps, "higher_is_better": True,
