@@ -209,6 +209,23 @@ def cpu_oracle_rate(wl, budget_s=10.0, min_steps=5):
     return wl.cells * n / dt / 1e6, n, dt
 
 
+def replica_throughput(ms_local, cells, steps, world):
+    """Whole-job rate of `world` independent replicas, each advancing `cells`
+    cells `steps` times: the time is the slowest rank's (max over ranks, the
+    only collective of the run), the work is every rank's."""
+    import torch
+
+    t = torch.tensor([float(m) for m in ms_local], dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+
+        if dist.get_backend() == "nccl":
+            t = t.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = t.cpu().tolist()
+    return world * cells * steps / (ms[0] * 1e-3) / 1e6, ms
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -271,13 +288,10 @@ def main():
     flush = 2 * 9 * wl.cells * BYTES_PER_CELL[prec] // 18 < 2 * (129 << 20)
     with ClockSampler(local) as clk:
         ms_step, ms_fluid, launches = time_device(wl, prec, args.steps, args.warmup, flush)
-    T = torch.tensor([ms_step, ms_fluid], dtype=torch.float64, device="cuda")
     if ws > 1:
         dist.barrier()
-        dist.all_reduce(T, op=dist.ReduceOp.MAX)
-    ms_step, ms_fluid = T.tolist()
     cells = wl.cells
-    value = ws * cells * args.steps / (ms_step * 1e-3) / 1e6  # MLUPS over all replicas
+    value, (ms_step, ms_fluid) = replica_throughput([ms_step, ms_fluid], cells, args.steps, ws)
     peak, peak_kind = hbm_peak()
     algo_bytes = BYTES_PER_CELL[prec] * cells
     achieved = algo_bytes / (ms_fluid * 1e-3 / args.steps) / 1e9
