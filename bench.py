@@ -125,6 +125,8 @@ def make_workload(name, steps):
         return W.large_couette(steps=steps)
     if name == "couette2k":  # 2048 x 2048, 4 particles: beyond L2, small enough to profile
         return W.large_couette(nx=2048, ny=2048, n_particles=4, steps=steps)
+    if name == "screening":  # the 512-lattice batch, timed as one context
+        return None
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -166,6 +168,58 @@ def time_device(wl, prec, steps, warmup, flush):
     launches = steps * (4 if wl.particles else 1)
     sim.close()
     return ms_step, ms_fluid, launches
+
+
+def screening_batch(prec, wls):
+    from paper_1606_01805_gb300 import lbib
+    from paper_1606_01805_gb300 import workloads as W
+
+    b = lbib.Batch([dict(W.batch_config(w), precision=prec) for w in wls],
+                   max_particles=len(wls), max_markers=sum(4000 for _ in wls))
+    for k, w in enumerate(wls):
+        for p in w.particles:
+            b.add_particle(k, **p.kwargs())
+    return b
+
+
+def time_batched(prec, steps, warmup, instances=512):
+    """The screening batch (512 uneven lattices, 63 M cells, beyond L2) as
+    one context: device time per step from the library's events."""
+    from paper_1606_01805_gb300 import workloads as W
+
+    wls = W.batched_screening(steps=0)[:instances]
+    b = screening_batch(prec, wls)
+    b.step_timed(warmup)
+    ms_step, ms_fluid = b.step_timed(steps)
+    tile = b.tile()
+    b.close()
+    cells = sum(w.cells for w in wls)
+    return cells, ms_step / steps, ms_fluid / steps, tile
+
+
+def time_per_instance(prec, sweeps):
+    """The same 512 lattices as 512 contexts, stepped one after another
+    (each replays its own captured 32-step graphs): device time per step."""
+    import torch
+
+    from paper_1606_01805_gb300 import workloads as W
+
+    wls = W.batched_screening(steps=0)
+    sims = [gpu_sim(w, prec) for w in wls]
+    for s in sims:
+        s.step(32)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(sweeps):
+        for s in sims:
+            s.step(32)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / (32 * sweeps)
+    for s in sims:
+        s.close()
+    return sum(w.cells for w in wls), ms
 
 
 def time_e2e(wl, prec, steps):
@@ -243,10 +297,15 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16s"])
     ap.add_argument("--no-large", action="store_true", help="skip the 16384 x 4096 roofline run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance screening batch")
+    ap.add_argument("--instances", type=int, default=512,
+                    help="screening workload: first N lattices of the batch (profiling subsets)")
     args = ap.parse_args()
     prec = {"fp64": 0, "fp32": 1, "fp16s": 2}[args.precision]
     ws, rank, local = dist_env()
     wl = make_workload(args.workload, steps=20000)
+    if wl is None:
+        return main_screening(args)
 
     if args.impl == "reference":
         if rank != 0:
@@ -327,6 +386,22 @@ def main():
                                     "fluid_GBps": a2, "frac_of_peak": a2 / peak,
                                     "frac_of_roofline_mlups": big.cells * 10 / (s2 * 1e-3) /
                                     (peak * 1e9 / BYTES_PER_CELL[prec])}
+        if not args.no_batched:
+            batched = {"workload": "screening batch, 512 Couette lattices 256-1024 x 128-256, "
+                                   "one random particle each (seed 3)"}
+            for pname, pv in (("fp32", 1), ("fp16s", 2)):
+                cells, ms, msf, tile = time_batched(pv, 20, 3)
+                bpc = BYTES_PER_CELL[pv]
+                batched[pname] = {"MLUPS": cells / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                                  "fluid_GBps": bpc * cells / (msf * 1e-3) / 1e9,
+                                  "frac_of_roofline_mlups": cells / (ms * 1e-3) / (peak * 1e9 / bpc),
+                                  "tile": tile}
+            cells, ms_pi = time_per_instance(1, 2)
+            batched["fp32_per_instance_contexts"] = {"MLUPS": cells / (ms_pi * 1e-3) / 1e6,
+                                                     "ms_per_step": ms_pi}
+            batched["batched_over_per_instance"] = batched["fp32"]["MLUPS"] / batched[
+                "fp32_per_instance_contexts"]["MLUPS"]
+            out["batched"] = batched
         if not args.no_cpu:
             v, n, dt = cpu_oracle_rate(wl)
             out["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
@@ -334,6 +409,40 @@ def main():
         print(json.dumps(out))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def main_screening(args):
+    """`--workload screening`: the 512-lattice batch is the timed workload
+    (63 M cells, beyond L2: no flush), one context, one launch per kernel."""
+    import torch
+
+    from paper_1606_01805_gb300 import build
+    from paper_1606_01805_gb300 import workloads as W
+
+    prec = {"fp64": 0, "fp32": 1, "fp16s": 2}[args.precision]
+    wls = W.batched_screening(steps=0)[:args.instances]
+    if args.impl == "reference":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle of the 512-lattice batch "
+                          "takes hours per step set on the host; see the default workload"}))
+        return
+    torch.cuda.set_device(0)
+    build.build()
+    with ClockSampler(0) as clk:
+        cells, ms, msf, tile = time_batched(prec, args.steps, args.warmup, args.instances)
+    peak, peak_kind = hbm_peak()
+    bpc = BYTES_PER_CELL[prec]
+    achieved = bpc * cells / (msf * 1e-3) / 1e9
+    print(json.dumps({
+        "metric": METRIC, "value": cells / (ms * 1e-3) / 1e6, "unit": "MLUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAMES[prec], "data": "synthetic",
+        "config": {"workload": f"screening batch: {len(wls)} Couette lattices 256-1024 x 128-256, "
+                               "one random particle each (seed 3)", "cells": cells,
+                   "l2": "inputs larger than L2", "tile": tile},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_fluid (task list)",
+                     "peak_source": f"{peak_kind} (burst copy)"},
+        "gpu_launches": 4 * args.steps, "clocks": clk.summary()}))
 
 
 if __name__ == "__main__":

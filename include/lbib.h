@@ -186,8 +186,8 @@ lbm_status lbm_get_particles(lbm_ctx* ctx, lbm_particle_state* out, int32_t cap,
  * stall or synchronise the device mid-run.  It advances nsteps steps
  * exactly as lbm_step does (same kernels, same order, same results) but
  * keeps the immersed-boundary scratch -- per marker block force/torque
- * sums, per-particle support boxes, per-marker spreading records -- in one
- * static device array of
+ * sums, per-particle completion counters and support boxes, per-marker
+ * spreading records -- in one static device array of
  * LBM_STATIC_SCRATCH_BYTES compiled into the library, instead of in the
  * context's workspace.  It allocates nothing: no cudaMalloc, no cudaFree,
  * no allocating library routine; the populations and particle state it
@@ -200,10 +200,10 @@ lbm_status lbm_get_particles(lbm_ctx* ctx, lbm_particle_state* out, int32_t cap,
  *    address (once per device, with that device current); make that first
  *    call before any stream capture.
  *  - All calls share the one array, which keeps the last call's contents;
- *    nothing in it has to start at zero (every entry is reset or written
- *    before it is read within a step).  Calls that overlap on the GPU
- *    (other streams, other contexts, other threads) race on the array:
- *    serialise them.
+ *    each call clears the counters that must start at zero (every other
+ *    entry is reset or written before it is read within a step).  Calls
+ *    that overlap on the GPU (other streams, other contexts, other threads)
+ *    race on the array: serialise them.
  *  - Launches directly on the context's stream, asynchronously; errors as
  *    for lbm_step.
  */
@@ -211,6 +211,56 @@ lbm_status lbm_get_particles(lbm_ctx* ctx, lbm_particle_state* out, int32_t cap,
 #define LBM_STATIC_MAX_PARTICLES 1024
 #define LBM_STATIC_MAX_MARKERS 16384
 lbm_status lbm_step_static(lbm_ctx* ctx, int32_t nsteps);
+
+/* ---------------------------------------------------------------------
+ * Batches: many independent lattices (instances) of uneven sizes advanced
+ * together, for screening many particle shapes and placements (the "4S"
+ * screening motivation of the Introduction).  One context holds them all:
+ * every step is still the five stages above, for every instance, with one
+ * launch per kernel for the whole batch (the fluid kernel walks a list of
+ * 128 x 8-cell tiles of all instances).  Instances never interact.
+ * The single-lattice calls above are the one-instance case and act on
+ * instance 0 (lbm_step, lbm_step_timed, lbm_sync and lbm_get_particles act
+ * on the whole batch; particle ids run over the whole batch in the order
+ * the particles were added).
+ * ------------------------------------------------------------------- */
+
+/* Device bytes for a batch of n configurations (see lbm_init_batch). */
+lbm_status lbm_batch_workspace_bytes(const lbm_config* cfgs, int32_t n, size_t* bytes);
+
+/*
+ * Create a context holding n >= 1 instances.  cfgs[i] gives instance i its
+ * lattice (nx, ny, tau, bc, wall_u, body_force, gravity, init, init_u,
+ * marker_spacing); cfgs[0] alone gives the stream, the workspace, the
+ * capacities (max_particles, max_markers: totals over the batch), the
+ * precision (all instances must give the same one) and the MLS weight.
+ * Errors as for lbm_init.
+ */
+lbm_status lbm_init_batch(const lbm_config* cfgs, int32_t n, lbm_ctx** out);
+
+/* Instances in the context (1 for lbm_init). */
+int32_t lbm_instances(const lbm_ctx* ctx);
+
+/* lbm_add_particle into instance `instance` (0 <= instance < lbm_instances). */
+lbm_status lbm_add_particle_to(lbm_ctx* ctx, int32_t instance, const lbm_particle_desc* desc,
+                               int32_t* out_id);
+
+/* lbm_get_fields / lbm_get_populations / lbm_set_populations of one instance
+   (arrays sized by that instance's nx, ny). */
+lbm_status lbm_get_instance_fields(lbm_ctx* ctx, int32_t instance, double* rho, double* ux, double* uy);
+lbm_status lbm_get_instance_populations(lbm_ctx* ctx, int32_t instance, double* f);
+lbm_status lbm_set_instance_populations(lbm_ctx* ctx, int32_t instance, const double* f);
+
+/*
+ * Tile shape of the fused fluid kernel.  lbm_init / lbm_init_batch time each
+ * shape on the context's own lattices and keep the fastest (all shapes give
+ * bit-identical results); lbm_get_tile reports the choice (index, cells per
+ * thread, rows per block) and lbm_set_tile forces shape `variant`
+ * (0 .. 2; LBM_EINVAL otherwise).
+ */
+lbm_status lbm_get_tile(const lbm_ctx* ctx, int32_t* variant, int32_t* cells_per_thread,
+                        int32_t* rows_per_block);
+lbm_status lbm_set_tile(lbm_ctx* ctx, int32_t variant);
 
 /* Steps done since lbm_init. */
 int64_t lbm_steps_done(const lbm_ctx* ctx);

@@ -1,10 +1,12 @@
 // api.cu -- host side of the C ABI declared in include/lbib.h: configuration
-// checks, the device workspace layout, particle set-up and the per-step
-// launch sequence (particles -> spreading -> fused fluid step).
+// checks, the device workspace layout of one lattice or a batch of them,
+// particle set-up, the fluid-tile autotuner and the per-step launch sequence
+// (probes -> markers -> spreading -> fused fluid step).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -15,10 +17,12 @@
 using namespace lbib;
 
 struct lbm_ctx {
-    lbm_config cfg;
-    Geo G;
+    lbm_config cfg;                 // first configuration: stream, workspace, capacities
+    std::vector<lbm_config> icfg;   // per instance
+    std::vector<Inst> hinst;        // per instance, host copy
+    int ninst = 0;
     int prec;
-    size_t sb, cb;            // bytes per stored / computed element
+    size_t sb, cb;                  // bytes per stored / computed element
     cudaStream_t stream;
     void* ws = nullptr;
     bool owns_ws = false;
@@ -26,9 +30,15 @@ struct lbm_ctx {
     int cur = 0;
     void* flb;
     uint8_t* flags;
-    DParticle* parts;         // two state buffers of cap_particles each
+    Inst* insts;
+    int4* tasks[N_FLUID_VARIANTS];
+    int ntasks[N_FLUID_VARIANTS];
+    int variant = 0;                // fluid tile shape in use
+    int sms = 1;
+    DParticle* parts;               // two state buffers of cap_particles each
     int4* blk;
     double* partial;
+    unsigned* count;
     double2* rb;
     double2* nb;
     double* S;
@@ -40,7 +50,6 @@ struct lbm_ctx {
     int np = 0, nmark = 0, nblk = 0;
     double rc_max = 0;
     int64_t steps = 0;
-    std::vector<DParticle> hparts;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // GRAPH_STEPS steps from buffer 0 / 1
     bool graphs_ok = true;
@@ -53,11 +62,6 @@ namespace {
 
 constexpr size_t ALIGN = 256;
 size_t up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
-
-struct Layout {
-    size_t f0, f1, flb, flags, parts, blk, partial, rb, nb, S, recs, boxes, err, scratch, total;
-    int pitch, nseg, scratch_rows;
-};
 
 int cap_particles(const lbm_config& c) { return c.max_particles > 0 ? c.max_particles : 16; }
 int cap_markers(const lbm_config& c) { return c.max_markers > 0 ? c.max_markers : 16384; }
@@ -80,31 +84,106 @@ const char* check_config(const lbm_config* c) {
     return nullptr;
 }
 
-Layout layout(const lbm_config& c) {
+const char* check_batch(const lbm_config* cfgs, int n) {
+    if (!cfgs || n < 1) return "a batch needs at least one configuration";
+    for (int i = 0; i < n; ++i) {
+        if (const char* why = check_config(cfgs + i)) return why;
+        if (cfgs[i].precision != cfgs[0].precision) return "all instances must share one precision";
+    }
+    return nullptr;
+}
+
+Geo make_geo(const lbm_config& c) {
+    Geo G;
+    std::memset(&G, 0, sizeof G);
+    G.nx = c.nx;
+    G.ny = c.ny;
+    G.pitch = (c.nx + 31) / 32 * 32;
+    G.nseg = G.pitch / 32;
+    G.plane = (long long)G.pitch * c.ny;
+    G.px = c.bc[0] == LBM_BC_PERIODIC;
+    G.py = c.bc[2] == LBM_BC_PERIODIC;
+    for (int i = 0; i < 4; ++i) {
+        G.uw[i][0] = c.wall_u[i][0];
+        G.uw[i][1] = c.wall_u[i][1];
+        G.uwf[i][0] = (float)c.wall_u[i][0];
+        G.uwf[i][1] = (float)c.wall_u[i][1];
+    }
+    G.g[0] = c.body_force[0];
+    G.g[1] = c.body_force[1];
+    G.gf[0] = (float)G.g[0];
+    G.gf[1] = (float)G.g[1];
+    G.grav[0] = c.gravity[0];
+    G.grav[1] = c.gravity[1];
+    G.tau = c.tau;
+    G.omega = 1.0 / c.tau;
+    G.omegaf = (float)G.omega;
+    return G;
+}
+
+// fluid tiles of variant v over all instances
+std::vector<int4> make_tasks(const std::vector<Inst>& insts, int v) {
+    const int w = 32 * FLUID_VARIANTS[v].cpt, by = FLUID_VARIANTS[v].by;
+    std::vector<int4> t;
+    for (int i = 0; i < (int)insts.size(); ++i) {
+        const Geo& G = insts[i].G;
+        for (int ty = 0; ty < (G.ny + by - 1) / by; ++ty)
+            for (int tx = 0; tx < (G.nx + w - 1) / w; ++tx) t.push_back(make_int4(i, tx, ty, 0));
+    }
+    return t;
+}
+
+struct Layout {
+    std::vector<Inst> insts;
+    size_t f0, f1, flb, flags, insts_off, tasks[N_FLUID_VARIANTS], parts, blk, partial, count, rb, nb,
+        S, recs, boxes, err, scratch, total;
+    int ntasks[N_FLUID_VARIANTS];
+    int scratch_rows;
+};
+
+Layout layout(const lbm_config* cfgs, int n) {
     Layout L;
-    const int prec = c.precision;
-    L.pitch = (c.nx + 31) / 32 * 32;
-    L.nseg = L.pitch / 32;
-    const size_t plane = (size_t)L.pitch * c.ny;
-    const size_t P = cap_particles(c), M = cap_markers(c);
+    const lbm_config& c0 = cfgs[0];
+    const int prec = c0.precision;
+    long long fe = 0, fle = 0, fge = 0;  // elements / bytes so far
+    int max_nx = 0;
+    for (int i = 0; i < n; ++i) {
+        Inst I;
+        I.G = make_geo(cfgs[i]);
+        I.f_off = fe;
+        I.flb_off = fle;
+        I.flags_off = fge;
+        fe += 9 * I.G.plane;
+        fle += 2 * I.G.plane;
+        fge += (long long)I.G.ny * I.G.nseg;
+        max_nx = std::max(max_nx, I.G.nx);
+        L.insts.push_back(I);
+    }
+    const size_t P = cap_particles(c0), M = cap_markers(c0), NB = cap_blocks(c0);
     // rows of FP64 field output staged per lbm_get_fields chunk (<= 24 MB)
-    L.scratch_rows = (int)std::max<size_t>(1, std::min<size_t>(c.ny, (size_t)(1u << 20) / c.nx));
+    L.scratch_rows = (int)std::max<size_t>(1, (size_t)(1u << 20) / max_nx);
     size_t o = 0;
-    L.f0 = o; o = up(o + 9 * plane * storage_bytes(prec));
-    L.f1 = o; o = up(o + 9 * plane * storage_bytes(prec));
-    L.flb = o; o = up(o + 2 * plane * compute_bytes(prec));
-    L.flags = o; o = up(o + (size_t)c.ny * L.nseg);
+    L.f0 = o; o = up(o + fe * storage_bytes(prec));
+    L.f1 = o; o = up(o + fe * storage_bytes(prec));
+    L.flb = o; o = up(o + fle * compute_bytes(prec));
+    L.flags = o; o = up(o + fge);
+    L.insts_off = o; o = up(o + n * sizeof(Inst));
+    for (int v = 0; v < N_FLUID_VARIANTS; ++v) {
+        L.ntasks[v] = (int)make_tasks(L.insts, v).size();
+        L.tasks[v] = o;
+        o = up(o + (size_t)L.ntasks[v] * sizeof(int4));
+    }
     L.parts = o; o = up(o + 2 * P * sizeof(DParticle));
-    const size_t NB = cap_blocks(c);
     L.blk = o; o = up(o + NB * sizeof(int4));
     L.partial = o; o = up(o + 3 * NB * sizeof(double));
+    L.count = o; o = up(o + P * sizeof(unsigned));
     L.rb = o; o = up(o + M * sizeof(double2));
     L.nb = o; o = up(o + M * sizeof(double2));
     L.S = o; o = up(o + M * sizeof(double));
     L.recs = o; o = up(o + M * rec_bytes(prec));
     L.boxes = o; o = up(o + P * sizeof(int4));
     L.err = o; o = up(o + 16);
-    L.scratch = o; o = up(o + 3 * (size_t)L.scratch_rows * c.nx * sizeof(double));
+    L.scratch = o; o = up(o + 3 * (size_t)L.scratch_rows * max_nx * sizeof(double));
     L.total = o;
     return L;
 }
@@ -136,52 +215,70 @@ lbm_status device_error(lbm_ctx* ctx) {
 
 constexpr int GRAPH_STEPS = 32;  // even, so a replay returns to the same buffer
 
-// Part of one time step from buffer `cur` on stream `st`: the immersed-
-// boundary kernels (ib = true: probes / rigid update / markers, spreading)
-// or the fused fluid kernel (ib = false).  Bookkeeping is the caller's.
-lbm_status enqueue_step_part(lbm_ctx* ctx, cudaStream_t st, int cur, bool ib) {
-    const void* fcur = ctx->f[cur];
-    if (ib) {
-        if (ctx->np == 0) return LBM_OK;
-        ParticleArgs pa;
-        pa.f = fcur;
-        pa.G = ctx->G;
-        pa.pin = ctx->parts + (size_t)cur * cap_particles(ctx->cfg);
-        pa.pout = ctx->parts + (size_t)(cur ^ 1) * cap_particles(ctx->cfg);
-        pa.blk = ctx->blk;
-        pa.partial = ctx->partial;
-        pa.rb = ctx->rb;
-        pa.nb = ctx->nb;
-        pa.S = ctx->S;
-        pa.recs = ctx->recs;
-        pa.boxes = ctx->boxes;
-        pa.err = ctx->err;
-        pa.gravity[0] = ctx->cfg.gravity[0];
-        pa.gravity[1] = ctx->cfg.gravity[1];
-        pa.weight = ctx->cfg.weight;
-        CK(launch_probes(ctx->prec, pa, ctx->nblk, st));
-        CK(launch_markers(ctx->prec, pa, ctx->nblk, st));
-        SpreadArgs sa;
-        sa.G = ctx->G;
-        sa.parts = ctx->parts;
-        sa.recs = ctx->recs;
-        sa.boxes = ctx->boxes;
-        sa.flb = ctx->flb;
-        sa.flags = ctx->flags;
-        sa.err = ctx->err;
-        // tiles of 32 x 16 cells covering the largest support box
-        const double ext = 2.0 * ctx->rc_max + 4.0;
-        const int tiles = ((int)std::ceil(ext / 32.0) + 1) * ((int)std::ceil(ext / 16.0) + 1);
-        CK(launch_spread(ctx->prec, sa, ctx->np, tiles, st));
-        return LBM_OK;
-    }
+ParticleArgs particle_args(lbm_ctx* ctx, int cur) {
+    ParticleArgs pa;
+    pa.f = ctx->f[cur];
+    pa.insts = ctx->insts;
+    pa.pin = ctx->parts + (size_t)cur * cap_particles(ctx->cfg);
+    pa.pout = ctx->parts + (size_t)(cur ^ 1) * cap_particles(ctx->cfg);
+    pa.blk = ctx->blk;
+    pa.partial = ctx->partial;
+    pa.count = ctx->count;
+    pa.rb = ctx->rb;
+    pa.nb = ctx->nb;
+    pa.S = ctx->S;
+    pa.recs = ctx->recs;
+    pa.boxes = ctx->boxes;
+    pa.err = ctx->err;
+    pa.weight = ctx->cfg.weight;
+    return pa;
+}
+
+SpreadArgs spread_args(lbm_ctx* ctx, const ParticleArgs& pa) {
+    SpreadArgs sa;
+    sa.insts = ctx->insts;
+    sa.parts = ctx->parts;
+    sa.recs = pa.recs;
+    sa.boxes = pa.boxes;
+    sa.flb = ctx->flb;
+    sa.flags = ctx->flags;
+    sa.err = ctx->err;
+    return sa;
+}
+
+// tiles of 32 x 16 cells covering the largest support box
+int spread_tiles(const lbm_ctx* ctx) {
+    const double ext = 2.0 * ctx->rc_max + 4.0;
+    return ((int)std::ceil(ext / 32.0) + 1) * ((int)std::ceil(ext / 16.0) + 1);
+}
+
+lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v) {
     FluidArgs fa;
-    fa.fin = fcur;
+    fa.fin = ctx->f[cur];
     fa.fout = ctx->f[cur ^ 1];
     fa.flb = ctx->flb;
     fa.flags = ctx->flags;
-    fa.G = ctx->G;
-    CK(launch_fluid(ctx->prec, fa, st));
+    fa.insts = ctx->insts;
+    fa.tasks = ctx->tasks[v];
+    fa.ntasks = ctx->ntasks[v];
+    // one CTA per tile: the block scheduler keeps every SM filled as tiles
+    // finish (the kernel's task loop then runs once per CTA)
+    const int grid = std::max(1, fa.ntasks);
+    CK(launch_fluid(ctx->prec, v, fa, ctx->ninst == 1 ? &ctx->hinst[0] : nullptr, grid, st));
+    return LBM_OK;
+}
+
+// Part of one time step from buffer `cur` on stream `st`: the immersed-
+// boundary kernels (ib = true: probes / rigid update / markers, spreading)
+// or the fused fluid kernel over every instance (ib = false).  Bookkeeping
+// is the caller's.
+lbm_status enqueue_step_part(lbm_ctx* ctx, cudaStream_t st, int cur, bool ib) {
+    if (!ib) return launch_fluid_step(ctx, st, cur, ctx->variant);
+    if (ctx->np == 0) return LBM_OK;
+    const ParticleArgs pa = particle_args(ctx, cur);
+    CK(launch_probes(ctx->prec, pa, ctx->nblk, st));
+    CK(launch_markers(ctx->prec, pa, ctx->nblk, st));
+    CK(launch_spread(ctx->prec, spread_args(ctx, pa), ctx->np, spread_tiles(ctx), st));
     return LBM_OK;
 }
 
@@ -247,40 +344,73 @@ bool capture_timed(lbm_ctx* ctx, int cur) {
     return ok;
 }
 
-}  // namespace
+void drop_graphs(lbm_ctx* ctx) {
+    for (auto* set : {ctx->graph, ctx->timed})
+        for (int k = 0; k < 2; ++k)
+            if (set[k]) {
+                cudaGraphExecDestroy(set[k]);
+                set[k] = nullptr;
+            }
+}
 
-extern "C" {
-
-lbm_status lbm_workspace_bytes(const lbm_config* cfg, size_t* bytes) {
-    if (const char* why = check_config(cfg)) {
-        (void)why;
-        return LBM_EINVAL;
+// Autotuner of the fluid tile shape: times every variant on the context's
+// own lattices (fluid kernel only; it reads buffer cur and writes the other
+// one, which the next step overwrites, and no force flag is set yet) and
+// keeps the fastest.  All variants compute the same cells with the same
+// arithmetic, so the choice changes speed only.
+lbm_status autotune(lbm_ctx* ctx) {
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    float best[N_FLUID_VARIANTS];
+    for (int v = 0; v < N_FLUID_VARIANTS; ++v) {  // warm every shape first
+        best[v] = 1e30f;
+        lbm_status s = launch_fluid_step(ctx, ctx->stream, ctx->cur, v);
+        if (s != LBM_OK) return s;
     }
-    if (!bytes) return LBM_EINVAL;
-    *bytes = layout(*cfg).total;
+    for (int round = 0; round < 2; ++round)
+        for (int v = 0; v < N_FLUID_VARIANTS; ++v) {
+            CK(cudaEventRecord(a, ctx->stream));
+            for (int k = 0; k < 2; ++k) {
+                lbm_status s = launch_fluid_step(ctx, ctx->stream, ctx->cur, v);
+                if (s != LBM_OK) return s;
+            }
+            CK(cudaEventRecord(b, ctx->stream));
+            CK(cudaEventSynchronize(b));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            best[v] = std::min(best[v], ms);
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->variant = (int)(std::min_element(best, best + N_FLUID_VARIANTS) - best);
     return LBM_OK;
 }
 
-lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
+lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
     if (!out) return LBM_EINVAL;
-    cudaGetLastError();  // a stale error of earlier work must not fail this context
     *out = nullptr;
-    if (check_config(cfg)) return LBM_EINVAL;
-    const Layout L = layout(*cfg);
+    if (check_batch(cfgs, n)) return LBM_EINVAL;
+    cudaGetLastError();  // a stale error of earlier work must not fail this context
+    Layout L = layout(cfgs, n);
     lbm_ctx* ctx = new lbm_ctx();
-    ctx->cfg = *cfg;
-    ctx->prec = cfg->precision;
+    ctx->cfg = cfgs[0];
+    ctx->icfg.assign(cfgs, cfgs + n);
+    ctx->ninst = n;
+    ctx->hinst = L.insts;
+    ctx->prec = cfgs[0].precision;
     ctx->sb = storage_bytes(ctx->prec);
     ctx->cb = compute_bytes(ctx->prec);
-    ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
-    if (cfg->d_workspace) {
-        if (cfg->workspace_bytes < L.total) {
+    ctx->stream = static_cast<cudaStream_t>(cfgs[0].cuda_stream);
+    if (cfgs[0].d_workspace) {
+        if (cfgs[0].workspace_bytes < L.total) {
             delete ctx;
             return LBM_ENOMEM;
         }
-        ctx->ws = cfg->d_workspace;
+        ctx->ws = cfgs[0].d_workspace;
     } else {
         if (cudaMalloc(&ctx->ws, L.total) != cudaSuccess) {
+            cudaGetLastError();
             delete ctx;
             return LBM_ENOMEM;
         }
@@ -291,9 +421,15 @@ lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
     ctx->f[1] = b + L.f1;
     ctx->flb = b + L.flb;
     ctx->flags = reinterpret_cast<uint8_t*>(b + L.flags);
+    ctx->insts = reinterpret_cast<Inst*>(b + L.insts_off);
+    for (int v = 0; v < N_FLUID_VARIANTS; ++v) {
+        ctx->tasks[v] = reinterpret_cast<int4*>(b + L.tasks[v]);
+        ctx->ntasks[v] = L.ntasks[v];
+    }
     ctx->parts = reinterpret_cast<DParticle*>(b + L.parts);
     ctx->blk = reinterpret_cast<int4*>(b + L.blk);
     ctx->partial = reinterpret_cast<double*>(b + L.partial);
+    ctx->count = reinterpret_cast<unsigned*>(b + L.count);
     ctx->rb = reinterpret_cast<double2*>(b + L.rb);
     ctx->nb = reinterpret_cast<double2*>(b + L.nb);
     ctx->S = reinterpret_cast<double*>(b + L.S);
@@ -302,34 +438,27 @@ lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
     ctx->err = reinterpret_cast<unsigned*>(b + L.err);
     ctx->scratch = reinterpret_cast<double*>(b + L.scratch);
     ctx->scratch_rows = L.scratch_rows;
-    Geo& G = ctx->G;
-    G.nx = cfg->nx;
-    G.ny = cfg->ny;
-    G.pitch = L.pitch;
-    G.nseg = L.nseg;
-    G.plane = (long long)L.pitch * cfg->ny;
-    G.px = cfg->bc[0] == LBM_BC_PERIODIC;
-    G.py = cfg->bc[2] == LBM_BC_PERIODIC;
-    for (int i = 0; i < 4; ++i) {
-        G.uw[i][0] = cfg->wall_u[i][0];
-        G.uw[i][1] = cfg->wall_u[i][1];
-    }
-    G.g[0] = cfg->body_force[0];
-    G.g[1] = cfg->body_force[1];
-    G.tau = cfg->tau;
-    G.omega = 1.0 / cfg->tau;
-    for (int i = 0; i < 4; ++i) {
-        G.uwf[i][0] = (float)G.uw[i][0];
-        G.uwf[i][1] = (float)G.uw[i][1];
-    }
-    G.gf[0] = (float)G.g[0];
-    G.gf[1] = (float)G.g[1];
-    G.omegaf = (float)G.omega;
-    // zero everything (padding columns, force field, flags, error word)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ctx->sms < 1) ctx->sms = 1;
+    std::vector<std::vector<int4>> tasks(N_FLUID_VARIANTS);
+    for (int v = 0; v < N_FLUID_VARIANTS; ++v) tasks[v] = make_tasks(L.insts, v);
+    // zero everything (padding columns, force fields, flags, error word),
+    // then the instance table, the tile lists and the initial fields
     cudaError_t e = cudaMemsetAsync(ctx->ws, 0, L.total, ctx->stream);
-    if (e == cudaSuccess) e = launch_init(ctx->prec, ctx->f[0], G, cfg->init, cfg->init_u, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->insts, L.insts.data(), n * sizeof(Inst), cudaMemcpyHostToDevice, ctx->stream);
+    for (int v = 0; v < N_FLUID_VARIANTS && e == cudaSuccess; ++v)
+        e = cudaMemcpyAsync(ctx->tasks[v], tasks[v].data(), tasks[v].size() * sizeof(int4),
+                            cudaMemcpyHostToDevice, ctx->stream);
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        e = launch_init(ctx->prec, ctx->f[0], L.insts[i], cfgs[i].init, cfgs[i].init_u, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess && autotune(ctx) != LBM_OK) e = cudaErrorUnknown;
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
+        cudaGetLastError();
         if (ctx->owns_ws) cudaFree(ctx->ws);
         delete ctx;
         return LBM_ECUDA;
@@ -338,8 +467,9 @@ lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
     return LBM_OK;
 }
 
-lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* d, int32_t* out_id) {
+lbm_status add_particle(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, int32_t* out_id) {
     if (!ctx || !d) return LBM_EINVAL;
+    if (inst < 0 || inst >= ctx->ninst) return fail(ctx, LBM_EINVAL, "no such instance");
     if (ctx->steps > 0) return fail(ctx, LBM_EINVAL, "particles must be added before the first step");
     if (ctx->np >= cap_particles(ctx->cfg)) return fail(ctx, LBM_EINVAL, "particle capacity exceeded");
     if (d->shape < LBM_SHAPE_CIRCLE || d->shape > LBM_SHAPE_TRIANGLE || !(d->dim[0] > 0) ||
@@ -347,10 +477,11 @@ lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* d, int32_t* o
         return fail(ctx, LBM_EINVAL, "bad particle shape, size or density");
     if ((d->shape == LBM_SHAPE_ELLIPSE || d->shape == LBM_SHAPE_RECT) && !(d->dim[1] > 0))
         return fail(ctx, LBM_EINVAL, "shape needs two dimensions");
+    const Geo& G = ctx->hinst[inst].G;
     const int room = cap_markers(ctx->cfg) - ctx->nmark;
-    std::vector<double> rb(2 * (size_t)room + 2), nb(2 * (size_t)room + 2), S((size_t)room + 1);
+    std::vector<double> rb(2 * (size_t)std::max(room, 0) + 2), nb(rb.size()), S(rb.size() / 2);
     ShapeOut so;
-    if (make_shape(*d, ctx->cfg.marker_spacing, rb.data(), nb.data(), S.data(), room, &so) < 0)
+    if (make_shape(*d, ctx->icfg[inst].marker_spacing, rb.data(), nb.data(), S.data(), room, &so) < 0)
         return fail(ctx, LBM_EINVAL, "marker capacity exceeded");
     const int n = so.n;
     // every marker and probe support must stay inside the walls
@@ -362,9 +493,9 @@ lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* d, int32_t* o
         for (int pass = 0; pass < 2; ++pass) {
             const double px = x + pass * 1.2 * nx, py = y + pass * 1.2 * ny;
             const int i0 = (int)std::floor(px + 0.5), j0 = (int)std::floor(py + 0.5);
-            if (!ctx->G.px && (i0 - 1 < 0 || i0 + 1 > ctx->G.nx - 1))
+            if (!G.px && (i0 - 1 < 0 || i0 + 1 > G.nx - 1))
                 return fail(ctx, LBM_EINVAL, "particle support crosses an x wall");
-            if (!ctx->G.py && (j0 - 1 < 0 || j0 + 1 > ctx->G.ny - 1))
+            if (!G.py && (j0 - 1 < 0 || j0 + 1 > G.ny - 1))
                 return fail(ctx, LBM_EINVAL, "particle support crosses a y wall");
         }
     }
@@ -374,8 +505,8 @@ lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* d, int32_t* o
         P.X[h][0] = d->xc;
         P.X[h][1] = d->yc;
         P.th[h] = d->theta;
-        P.cs[h][0] = std::cos(d->theta);
-        P.cs[h][1] = std::sin(d->theta);
+        P.cs[h][0] = c;
+        P.cs[h][1] = s;
         P.U[h][0] = d->u0[0];
         P.U[h][1] = d->u0[1];
         P.W[h] = d->omega0;
@@ -390,6 +521,7 @@ lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* d, int32_t* o
     P.nm = n;
     P.b0 = ctx->nblk;
     P.nblk = (n + MB - 1) / MB;
+    P.inst = inst;
     if (P.b0 + P.nblk > cap_blocks(ctx->cfg)) return fail(ctx, LBM_EINVAL, "marker capacity exceeded");
     std::vector<int4> blocks(P.nblk);
     for (int k = 0; k < P.nblk; ++k)
@@ -408,13 +540,119 @@ lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* d, int32_t* o
     CK(cudaMemcpyAsync(ctx->blk + P.b0, blocks.data(), P.nblk * sizeof(int4), cudaMemcpyHostToDevice,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    ctx->hparts.push_back(P);
+    drop_graphs(ctx);  // captured steps do not know this particle
     ctx->rc_max = std::max(ctx->rc_max, so.rcirc);
     ctx->nmark += n;
     ctx->nblk += P.nblk;
     if (out_id) *out_id = ctx->np;
     ctx->np += 1;
     return LBM_OK;
+}
+
+lbm_status get_fields(lbm_ctx* ctx, int inst, double* rho, double* ux, double* uy) {
+    if (!ctx) return LBM_EINVAL;
+    if (inst < 0 || inst >= ctx->ninst) return fail(ctx, LBM_EINVAL, "no such instance");
+    lbm_status s = device_error(ctx);
+    if (s != LBM_OK) return s;
+    const Inst& I = ctx->hinst[inst];
+    const int nx = I.G.nx, ny = I.G.ny;
+    const size_t chunk = (size_t)ctx->scratch_rows * nx;
+    for (int y0 = 0; y0 < ny; y0 += ctx->scratch_rows) {
+        const int rows = std::min(ctx->scratch_rows, ny - y0);
+        FieldArgs fa;
+        fa.f = ctx->f[ctx->cur];
+        fa.I = I;
+        fa.y0 = y0;
+        fa.rows = rows;
+        fa.rho = ctx->scratch;
+        fa.ux = ctx->scratch + chunk;
+        fa.uy = ctx->scratch + 2 * chunk;
+        CK(launch_fields(ctx->prec, fa, ctx->stream));
+        const size_t n = (size_t)rows * nx, off = (size_t)y0 * nx;
+        if (rho) CK(cudaMemcpyAsync(rho + off, fa.rho, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        if (ux) CK(cudaMemcpyAsync(ux + off, fa.ux, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        if (uy) CK(cudaMemcpyAsync(uy + off, fa.uy, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return LBM_OK;
+}
+
+double weight_of(int i) { return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+lbm_status get_populations(lbm_ctx* ctx, int inst, double* f) {
+    if (!ctx || !f) return LBM_EINVAL;
+    if (inst < 0 || inst >= ctx->ninst) return fail(ctx, LBM_EINVAL, "no such instance");
+    const Inst& I = ctx->hinst[inst];
+    const int nx = I.G.nx, ny = I.G.ny, pitch = I.G.pitch;
+    const size_t n = 9 * (size_t)I.G.plane;
+    std::vector<unsigned char> h(n * ctx->sb);
+    const char* src = static_cast<const char*>(ctx->f[ctx->cur]) + I.f_off * ctx->sb;
+    CK(cudaMemcpyAsync(h.data(), src, h.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < 9; ++i)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const size_t k = (size_t)i * I.G.plane + (size_t)y * pitch + x;
+                double v;
+                if (ctx->prec == LBM_FP64) v = reinterpret_cast<double*>(h.data())[k];
+                else if (ctx->prec == LBM_FP32) v = reinterpret_cast<float*>(h.data())[k];
+                else v = __half2float(reinterpret_cast<__half*>(h.data())[k]);
+                f[((size_t)i * ny + y) * nx + x] = v + weight_of(i);
+            }
+    return LBM_OK;
+}
+
+lbm_status set_populations(lbm_ctx* ctx, int inst, const double* f) {
+    if (!ctx || !f) return LBM_EINVAL;
+    if (inst < 0 || inst >= ctx->ninst) return fail(ctx, LBM_EINVAL, "no such instance");
+    const Inst& I = ctx->hinst[inst];
+    const int nx = I.G.nx, ny = I.G.ny, pitch = I.G.pitch;
+    const size_t n = 9 * (size_t)I.G.plane;
+    std::vector<unsigned char> h(n * ctx->sb, 0);
+    for (int i = 0; i < 9; ++i)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const size_t k = (size_t)i * I.G.plane + (size_t)y * pitch + x;
+                const double v = f[((size_t)i * ny + y) * nx + x] - weight_of(i);
+                if (ctx->prec == LBM_FP64) reinterpret_cast<double*>(h.data())[k] = v;
+                else if (ctx->prec == LBM_FP32) reinterpret_cast<float*>(h.data())[k] = (float)v;
+                else reinterpret_cast<__half*>(h.data())[k] = __float2half_rn((float)v);
+            }
+    char* dst = static_cast<char*>(ctx->f[ctx->cur]) + I.f_off * ctx->sb;
+    CK(cudaMemcpyAsync(dst, h.data(), h.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_workspace_bytes(const lbm_config* cfgs, int32_t n, size_t* bytes) {
+    if (check_batch(cfgs, n) || !bytes) return LBM_EINVAL;
+    *bytes = layout(cfgs, n).total;
+    return LBM_OK;
+}
+
+lbm_status lbm_workspace_bytes(const lbm_config* cfg, size_t* bytes) {
+    return lbm_batch_workspace_bytes(cfg, 1, bytes);
+}
+
+lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) { return init_contexts(cfg, 1, out); }
+
+lbm_status lbm_init_batch(const lbm_config* cfgs, int32_t n, lbm_ctx** out) {
+    return init_contexts(cfgs, n, out);
+}
+
+int32_t lbm_instances(const lbm_ctx* ctx) { return ctx ? ctx->ninst : 0; }
+
+lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* d, int32_t* out_id) {
+    return add_particle(ctx, 0, d, out_id);
+}
+
+lbm_status lbm_add_particle_to(lbm_ctx* ctx, int32_t instance, const lbm_particle_desc* d,
+                               int32_t* out_id) {
+    return add_particle(ctx, instance, d, out_id);
 }
 
 lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps) {
@@ -476,72 +714,23 @@ lbm_status lbm_sync(lbm_ctx* ctx) {
 }
 
 lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* ux, double* uy) {
-    if (!ctx) return LBM_EINVAL;
-    lbm_status s = device_error(ctx);
-    if (s != LBM_OK) return s;
-    const int nx = ctx->G.nx, ny = ctx->G.ny;
-    const size_t chunk = (size_t)ctx->scratch_rows * nx;
-    for (int y0 = 0; y0 < ny; y0 += ctx->scratch_rows) {
-        const int rows = std::min(ctx->scratch_rows, ny - y0);
-        FieldArgs fa;
-        fa.f = ctx->f[ctx->cur];
-        fa.G = ctx->G;
-        fa.y0 = y0;
-        fa.rows = rows;
-        fa.rho = ctx->scratch;
-        fa.ux = ctx->scratch + chunk;
-        fa.uy = ctx->scratch + 2 * chunk;
-        CK(launch_fields(ctx->prec, fa, ctx->stream));
-        const size_t n = (size_t)rows * nx, off = (size_t)y0 * nx;
-        if (rho) CK(cudaMemcpyAsync(rho + off, fa.rho, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
-        if (ux) CK(cudaMemcpyAsync(ux + off, fa.ux, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
-        if (uy) CK(cudaMemcpyAsync(uy + off, fa.uy, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
-    }
-    return LBM_OK;
+    return get_fields(ctx, 0, rho, ux, uy);
 }
 
-lbm_status lbm_get_populations(lbm_ctx* ctx, double* f) {
-    if (!ctx || !f) return LBM_EINVAL;
-    const int nx = ctx->G.nx, ny = ctx->G.ny, pitch = ctx->G.pitch;
-    const size_t n = 9 * (size_t)ctx->G.plane;
-    std::vector<unsigned char> h(n * ctx->sb);
-    CK(cudaMemcpyAsync(h.data(), ctx->f[ctx->cur], h.size(), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    for (int i = 0; i < 9; ++i) {
-        const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x) {
-                const size_t k = (size_t)i * ctx->G.plane + (size_t)y * pitch + x;
-                double v;
-                if (ctx->prec == LBM_FP64) v = reinterpret_cast<double*>(h.data())[k];
-                else if (ctx->prec == LBM_FP32) v = reinterpret_cast<float*>(h.data())[k];
-                else v = __half2float(reinterpret_cast<__half*>(h.data())[k]);
-                f[((size_t)i * ny + y) * nx + x] = v + w;
-            }
-    }
-    return LBM_OK;
+lbm_status lbm_get_instance_fields(lbm_ctx* ctx, int32_t instance, double* rho, double* ux, double* uy) {
+    return get_fields(ctx, instance, rho, ux, uy);
 }
 
-lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f) {
-    if (!ctx || !f) return LBM_EINVAL;
-    const int nx = ctx->G.nx, ny = ctx->G.ny, pitch = ctx->G.pitch;
-    const size_t n = 9 * (size_t)ctx->G.plane;
-    std::vector<unsigned char> h(n * ctx->sb, 0);
-    for (int i = 0; i < 9; ++i) {
-        const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x) {
-                const size_t k = (size_t)i * ctx->G.plane + (size_t)y * pitch + x;
-                const double v = f[((size_t)i * ny + y) * nx + x] - w;
-                if (ctx->prec == LBM_FP64) reinterpret_cast<double*>(h.data())[k] = v;
-                else if (ctx->prec == LBM_FP32) reinterpret_cast<float*>(h.data())[k] = (float)v;
-                else reinterpret_cast<__half*>(h.data())[k] = __float2half_rn((float)v);
-            }
-    }
-    CK(cudaMemcpyAsync(ctx->f[ctx->cur], h.data(), h.size(), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    return LBM_OK;
+lbm_status lbm_get_populations(lbm_ctx* ctx, double* f) { return get_populations(ctx, 0, f); }
+
+lbm_status lbm_get_instance_populations(lbm_ctx* ctx, int32_t instance, double* f) {
+    return get_populations(ctx, instance, f);
+}
+
+lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f) { return set_populations(ctx, 0, f); }
+
+lbm_status lbm_set_instance_populations(lbm_ctx* ctx, int32_t instance, const double* f) {
+    return set_populations(ctx, instance, f);
 }
 
 lbm_status lbm_get_particles(lbm_ctx* ctx, lbm_particle_state* out, int32_t cap, int32_t* n) {
@@ -569,6 +758,25 @@ lbm_status lbm_get_particles(lbm_ctx* ctx, lbm_particle_state* out, int32_t cap,
     return s;
 }
 
+lbm_status lbm_get_tile(const lbm_ctx* ctx, int32_t* variant, int32_t* cells_per_thread,
+                        int32_t* rows_per_block) {
+    if (!ctx) return LBM_EINVAL;
+    if (variant) *variant = ctx->variant;
+    if (cells_per_thread) *cells_per_thread = FLUID_VARIANTS[ctx->variant].cpt;
+    if (rows_per_block) *rows_per_block = FLUID_VARIANTS[ctx->variant].by;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_tile(lbm_ctx* ctx, int32_t variant) {
+    if (!ctx) return LBM_EINVAL;
+    if (variant < 0 || variant >= N_FLUID_VARIANTS) return fail(ctx, LBM_EINVAL, "no such tile variant");
+    if (variant != ctx->variant) {
+        ctx->variant = variant;
+        drop_graphs(ctx);  // captured steps launch the old shape
+    }
+    return LBM_OK;
+}
+
 int64_t lbm_steps_done(const lbm_ctx* ctx) { return ctx ? ctx->steps : 0; }
 
 const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->msg.c_str() : "null context"; }
@@ -578,10 +786,7 @@ void lbm_destroy(lbm_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
-    for (auto& g : ctx->graph)
-        if (g) cudaGraphExecDestroy(g);
-    for (auto& g : ctx->timed)
-        if (g) cudaGraphExecDestroy(g);
+    drop_graphs(ctx);
     if (ctx->owns_ws) cudaFree(ctx->ws);
     delete ctx;
 }
@@ -592,8 +797,6 @@ void lbm_destroy(lbm_ctx* ctx) {
 // lbm_step_static: the step with the immersed-boundary scratch in a static
 // device array instead of the context's workspace (see include/lbib.h).
 // ---------------------------------------------------------------------------
-#include <mutex>
-
 namespace {
 
 // Scratch shared by every lbm_step_static call in the process, on every
@@ -634,6 +837,7 @@ extern "C" lbm_status lbm_step_static(lbm_ctx* ctx, int32_t nsteps) {
     // layout of this context's scratch inside the static array
     size_t o = 0;
     const size_t o_partial = o; o = up(o + 3 * (size_t)ctx->nblk * sizeof(double));
+    const size_t o_count = o;   o = up(o + (size_t)ctx->np * sizeof(unsigned));
     const size_t o_boxes = o;   o = up(o + (size_t)ctx->np * sizeof(int4));
     const size_t o_recs = o;    o = up(o + (size_t)ctx->nmark * rec_bytes(ctx->prec));
     if (o > LBM_STATIC_SCRATCH_BYTES)
@@ -641,49 +845,24 @@ extern "C" lbm_status lbm_step_static(lbm_ctx* ctx, int32_t nsteps) {
     void* base = nullptr;
     CK(static_scratch(&base));
     char* sb = static_cast<char*>(base);
-    // nothing in the scratch has to start at zero: within each step the
-    // probe kernel resets the boxes and every other entry is written before
-    // it is read
+    // the per-particle completion counters must start at zero (each step's
+    // last probe block resets them, but the array keeps whatever an earlier
+    // call left); the boxes are reset by the probe kernel and every other
+    // entry is written before it is read
+    if (ctx->np > 0) CK(cudaMemsetAsync(sb + o_count, 0, (size_t)ctx->np * sizeof(unsigned), ctx->stream));
     for (int32_t k = 0; k < nsteps; ++k) {
-        const void* fcur = ctx->f[ctx->cur];
         if (ctx->np > 0) {
-            ParticleArgs pa;
-            pa.f = fcur;
-            pa.G = ctx->G;
-            pa.pin = ctx->parts + (size_t)ctx->cur * cap_particles(ctx->cfg);
-            pa.pout = ctx->parts + (size_t)(ctx->cur ^ 1) * cap_particles(ctx->cfg);
-            pa.blk = ctx->blk;
+            ParticleArgs pa = particle_args(ctx, ctx->cur);
             pa.partial = reinterpret_cast<double*>(sb + o_partial);
-            pa.rb = ctx->rb;
-            pa.nb = ctx->nb;
-            pa.S = ctx->S;
+            pa.count = reinterpret_cast<unsigned*>(sb + o_count);
             pa.recs = sb + o_recs;
             pa.boxes = reinterpret_cast<int4*>(sb + o_boxes);
-            pa.err = ctx->err;
-            pa.gravity[0] = ctx->cfg.gravity[0];
-            pa.gravity[1] = ctx->cfg.gravity[1];
-            pa.weight = ctx->cfg.weight;
             CK(launch_probes(ctx->prec, pa, ctx->nblk, ctx->stream));
             CK(launch_markers(ctx->prec, pa, ctx->nblk, ctx->stream));
-            SpreadArgs sa;
-            sa.G = ctx->G;
-            sa.parts = ctx->parts;
-            sa.recs = pa.recs;
-            sa.boxes = pa.boxes;
-            sa.flb = ctx->flb;
-            sa.flags = ctx->flags;
-            sa.err = ctx->err;
-            const double ext = 2.0 * ctx->rc_max + 4.0;
-            const int tiles = ((int)std::ceil(ext / 32.0) + 1) * ((int)std::ceil(ext / 16.0) + 1);
-            CK(launch_spread(ctx->prec, sa, ctx->np, tiles, ctx->stream));
+            CK(launch_spread(ctx->prec, spread_args(ctx, pa), ctx->np, spread_tiles(ctx), ctx->stream));
         }
-        FluidArgs fa;
-        fa.fin = fcur;
-        fa.fout = ctx->f[ctx->cur ^ 1];
-        fa.flb = ctx->flb;
-        fa.flags = ctx->flags;
-        fa.G = ctx->G;
-        CK(launch_fluid(ctx->prec, fa, ctx->stream));
+        lbm_status s = launch_fluid_step(ctx, ctx->stream, ctx->cur, ctx->variant);
+        if (s != LBM_OK) return s;
         ctx->cur ^= 1;
         ctx->steps += 1;
     }

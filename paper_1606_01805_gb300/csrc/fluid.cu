@@ -6,7 +6,7 @@ namespace lbib {
 
 namespace {
 
-constexpr int BY = 8;  // rows per block; blockDim = (32, BY), one warp per row segment
+constexpr int BY = 8;  // rows per block of the init and field kernels
 
 // BGK relaxation of Eq. 4 towards the shifted equilibrium f~eq_i = f_eq_i - w_i
 // (Eq. 2), plus the Guo term (Eq. 5), in place on v.  Written over opposite
@@ -42,9 +42,13 @@ __device__ __forceinline__ void collide(C v[9], C drho, C ux, C uy, C Fx, C Fy, 
     }
 }
 
-// four consecutive storage elements starting at a 4-aligned index
-template <class S, class C> struct Vec4;
-template <> struct Vec4<float, float> {
+// N consecutive storage elements starting at an N-aligned index
+template <class S, class C, int N> struct Vec;
+template <class S, class C> struct Vec<S, C, 1> {
+    static __device__ __forceinline__ void load(const S* p, C v[1]) { v[0] = ld<S, C>(p); }
+    static __device__ __forceinline__ void store(S* p, const C v[1]) { st<S, C>(p, v[0]); }
+};
+template <> struct Vec<float, float, 4> {
     static __device__ __forceinline__ void load(const float* p, float v[4]) {
         const float4 q = __ldg(reinterpret_cast<const float4*>(p));
         v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
@@ -53,7 +57,7 @@ template <> struct Vec4<float, float> {
         *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
     }
 };
-template <> struct Vec4<double, double> {
+template <> struct Vec<double, double, 4> {
     static __device__ __forceinline__ void load(const double* p, double v[4]) {
         const double2 a = __ldg(reinterpret_cast<const double2*>(p));
         const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
@@ -64,7 +68,7 @@ template <> struct Vec4<double, double> {
         reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
     }
 };
-template <> struct Vec4<__half, float> {
+template <> struct Vec<__half, float, 4> {
     static __device__ __forceinline__ void load(const __half* p, float v[4]) {
         const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
         const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
@@ -91,62 +95,79 @@ __device__ __forceinline__ void cell_update(C v[9], const Geo& G, C fx_ib, C fy_
     collide<C>(v, drho, ux, uy, Fx, Fy, geo_omega<C>(G));
 }
 
-// Fused step, four consecutive cells (x0 .. x0+3, x0 = 4 * lane index) of
-// one row per thread; a warp covers 128 cells of a row.  Populations move
-// as 16-byte vectors: a pull along +-x is a one-lane shuffle of the
-// neighbouring vector, with one extra element load at the warp's two ends.
-// Cells on a wall or periodic edge take the per-cell general path.
-// resident blocks per SM the register budget is sized for (FP64 values
-// take two registers each)
-template <class S> struct FluidOccupancy { static constexpr int value = 4; };
-template <> struct FluidOccupancy<double> { static constexpr int value = 2; };
-
-template <class S, class C>
-__global__ void __launch_bounds__(32 * BY, FluidOccupancy<S>::value) k_fluid(FluidArgs a) {
-    const Geo& G = a.G;
-    const S* __restrict__ fin = static_cast<const S*>(a.fin);
-    S* __restrict__ fout = static_cast<S*>(a.fout);
-    C* __restrict__ flb = static_cast<C*>(a.flb);
+// Fused step of one tile: N consecutive cells (x0 .. x0+N-1, x0 = N * lane
+// index) of one row per thread, a warp covering 32 N cells of a row, the
+// block BY rows.  Populations move as vectors of N elements: a pull along
+// +-x is a one-lane shuffle of the neighbouring vector, with one extra
+// element load at the warp's two ends.  Cells on a wall or periodic edge
+// take the per-cell general path (emitted once, after the fast cells).
+template <class S, class C, int N>
+__device__ __forceinline__ void fluid_tile(const Geo& G, const S* __restrict__ fin,
+                                           S* __restrict__ fout, C* __restrict__ flb,
+                                           uint8_t* __restrict__ flags, int tx, int y) {
     const int lane = threadIdx.x;
-    const int x0 = (blockIdx.x * 32 + lane) * 4;
-    const int y = blockIdx.y * BY + threadIdx.y;
+    const int x0 = (tx * 32 + lane) * N;
     if (y >= G.ny) return;  // whole warp (one row)
     const long long row = (long long)y * G.pitch;
     // the vector values of cell x0 + k are its pulled populations whenever
     // the cell is interior (all 9 sources inside, none of them clamped)
     const bool rows_in = y >= 1 && y <= G.ny - 2;
     const bool any = x0 < G.nx;
-    // force flags of the 32-cell segment of this thread (8 threads share one)
+    // force flags of the 32-cell segment of this thread
     const int seg = y * G.nseg + (x0 >> 5);
-    const bool forced = any && a.flags[seg] != 0;
+    const bool forced = any && flags[seg] != 0;
 
-    C v[9][4];
+    C v[9][N];
     // vector loads for every lane (addresses clamped in-bounds), shuffles by all
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int ys = min(max(y - cy(i), 0), G.ny - 1);
         const S* rp = fin + (long long)i * G.plane + (long long)ys * G.pitch;
-        const int xa = min(x0, G.pitch - 4);
-        C q[4];
-        Vec4<S, C>::load(rp + xa, q);
+        const int xa = min(x0, G.pitch - N);
+        C q[N];
+        Vec<S, C, N>::load(rp + xa, q);
         if (cx(i) == 0) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) v[i][k] = q[k];
+            for (int k = 0; k < N; ++k) v[i][k] = q[k];
         } else if (cx(i) > 0) {  // source x - 1
-            C left = __shfl_up_sync(0xffffffffu, q[3], 1);
+            C left = __shfl_up_sync(0xffffffffu, q[N - 1], 1);
             if (lane == 0) left = ld<S, C>(rp + max(xa - 1, 0));
-            v[i][0] = left; v[i][1] = q[0]; v[i][2] = q[1]; v[i][3] = q[2];
+            v[i][0] = left;
+#pragma unroll
+            for (int k = 1; k < N; ++k) v[i][k] = q[k - 1];
         } else {  // source x + 1
             C right = __shfl_down_sync(0xffffffffu, q[0], 1);
-            if (lane == 31) right = ld<S, C>(rp + min(xa + 4, G.pitch - 1));
-            v[i][0] = q[1]; v[i][1] = q[2]; v[i][2] = q[3]; v[i][3] = right;
+            if (lane == 31) right = ld<S, C>(rp + min(xa + N, G.pitch - 1));
+#pragma unroll
+            for (int k = 0; k < N - 1; ++k) v[i][k] = q[k + 1];
+            v[i][N - 1] = right;
+        }
+    }
+    // periodic x: the cells x = 0 and x = nx - 1 get the three populations
+    // that cross the periodic edge by scalar loads; their other six are
+    // already in the vectors, so they stay on the fast path
+    const bool wrap = G.px && rows_in && any;
+    const int ke = G.nx - 1 - x0;  // position of x = nx - 1 in this thread's cells
+    if (wrap && (x0 == 0 || (ke >= 0 && ke < N))) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const S* rp = fin + (long long)i * G.plane + (long long)(y - cy(i)) * G.pitch;
+            if (cx(i) > 0 && x0 == 0) v[i][0] = ld<S, C>(rp + (G.nx - 1));
+            if (cx(i) < 0 && ke >= 0 && ke < N) {
+                const C w0 = ld<S, C>(rp);
+#pragma unroll
+                for (int k = 0; k < N; ++k)
+                    if (k == ke) v[i][k] = w0;
+            }
         }
     }
     if (any) {
-        C fxi[4] = {C(0), C(0), C(0), C(0)}, fyi[4] = {C(0), C(0), C(0), C(0)};
+        C fxi[N], fyi[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) fxi[k] = fyi[k] = C(0);
         if (forced) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < N; ++k)
                 if (x0 + k < G.nx) {
                     fxi[k] = flb[row + x0 + k];
                     fyi[k] = flb[G.plane + row + x0 + k];
@@ -157,9 +178,9 @@ __global__ void __launch_bounds__(32 * BY, FluidOccupancy<S>::value) k_fluid(Flu
         // interior cells from the vector values
         unsigned edge = 0;  // bit k: cell x0 + k lies on an edge (and inside the lattice)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < N; ++k) {
             const int xk = x0 + k;
-            if (rows_in && xk >= 1 && xk <= G.nx - 2) {
+            if (rows_in && xk < G.nx && (wrap || (xk >= 1 && xk <= G.nx - 2))) {
                 C c[9];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) c[i] = v[i][k];
@@ -170,12 +191,12 @@ __global__ void __launch_bounds__(32 * BY, FluidOccupancy<S>::value) k_fluid(Flu
                 edge |= 1u << k;
             }
         }
-        if (edge == 0 && x0 + 3 < G.nx) {
+        if (edge == 0 && x0 + N - 1 < G.nx) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) Vec4<S, C>::store(fout + (long long)i * G.plane + row + x0, v[i]);
+            for (int i = 0; i < 9; ++i) Vec<S, C, N>::store(fout + (long long)i * G.plane + row + x0, v[i]);
         } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < N; ++k)
                 if (x0 + k < G.nx && !(edge >> k & 1u)) {
 #pragma unroll
                     for (int i = 0; i < 9; ++i) st<S, C>(fout + (long long)i * G.plane + row + x0 + k, v[i][k]);
@@ -183,7 +204,7 @@ __global__ void __launch_bounds__(32 * BY, FluidOccupancy<S>::value) k_fluid(Flu
             // cells on a wall or periodic edge: general pull, wall completion,
             // collision, one at a time (emitted once, nothing else live)
 #pragma unroll 1
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < N; ++k) {
                 if (!(edge >> k & 1u)) continue;
                 const int xk = x0 + k;
                 C c[9];
@@ -191,8 +212,12 @@ __global__ void __launch_bounds__(32 * BY, FluidOccupancy<S>::value) k_fluid(Flu
                 complete_walls<S, C>(fin, G, xk, y, c);
                 C gx = C(0), gy = C(0);
                 if (forced) {  // forces of this cell were read (and zeroed) above
-                    gx = k == 0 ? fxi[0] : k == 1 ? fxi[1] : k == 2 ? fxi[2] : fxi[3];
-                    gy = k == 0 ? fyi[0] : k == 1 ? fyi[1] : k == 2 ? fyi[2] : fyi[3];
+#pragma unroll
+                    for (int j = 0; j < N; ++j)
+                        if (j == k) {
+                            gx = fxi[j];
+                            gy = fyi[j];
+                        }
                 }
                 cell_update<C>(c, G, gx, gy);
 #pragma unroll
@@ -201,7 +226,40 @@ __global__ void __launch_bounds__(32 * BY, FluidOccupancy<S>::value) k_fluid(Flu
         }
     }
     __syncwarp();
-    if (forced && (lane & 7) == 0) a.flags[seg] = 0;
+    if (forced && (lane & (32 / N - 1)) == 0) flags[seg] = 0;  // one lane per segment
+}
+
+// resident blocks per SM the register budget is sized for: 1024 threads per
+// SM for 4 FP32 / FP16 cells per thread, 512 for FP64 (two registers per
+// value), 1280 (FP64: 768) for one cell per thread
+template <class S, int N, int BYt> struct FluidOccupancy {
+    static constexpr int value =
+        (N == 1 ? (sizeof(S) == 8 ? 3 : 5) : (sizeof(S) == 8 ? 2 : 4)) * 8 / BYt;
+};
+
+// persistent fused fluid step over the task list (all instances)
+template <class S, class C, int N, int BYt>
+__global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value) k_fluid(FluidArgs a) {
+    const S* fin = static_cast<const S*>(a.fin);
+    S* fout = static_cast<S*>(a.fout);
+    C* flb = static_cast<C*>(a.flb);
+    for (int t = blockIdx.x; t < a.ntasks; t += gridDim.x) {
+        const int4 task = a.tasks[t];
+        const Inst& I = a.insts[task.x];
+        fluid_tile<S, C, N>(I.G, fin + I.f_off, fout + I.f_off, flb + I.flb_off,
+                            a.flags + I.flags_off, task.y, task.z * BYt + threadIdx.y);
+    }
+}
+
+// the same step for a context holding one lattice: its descriptor arrives
+// by value (constant bank) and the grid is the tile grid itself, so no load
+// stands in front of the population loads
+template <class S, class C, int N, int BYt>
+__global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value)
+    k_fluid_one(FluidArgs a, Inst I) {
+    fluid_tile<S, C, N>(I.G, static_cast<const S*>(a.fin) + I.f_off, static_cast<S*>(a.fout) + I.f_off,
+                        static_cast<C*>(a.flb) + I.flb_off, a.flags + I.flags_off, blockIdx.x,
+                        blockIdx.y * BYt + threadIdx.y);
 }
 
 // initial post-collision field f* = f^eq(rho, u) (Eq. 2), shifted
@@ -232,16 +290,55 @@ __global__ void k_init(S* f, Geo G, int kind, double U0) {
 template <class S, class C>
 __global__ void k_fields(FieldArgs a) {
     const int x = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * BY + threadIdx.y;
-    if (x >= a.G.nx || r >= a.rows) return;
+    if (x >= a.I.G.nx || r >= a.rows) return;
     C rho, ux, uy;
-    node_fields<S, C>(static_cast<const S*>(a.f), a.G, x, a.y0 + r, rho, ux, uy);
-    const long long k = (long long)r * a.G.nx + x;
+    node_fields<S, C>(static_cast<const S*>(a.f) + a.I.f_off, a.I.G, x, a.y0 + r, rho, ux, uy);
+    const long long k = (long long)r * a.I.G.nx + x;
     a.rho[k] = (double)rho;
     a.ux[k] = (double)ux;
     a.uy[k] = (double)uy;
 }
 
 dim3 grid_for(int nx, int rows) { return dim3((nx + 31) / 32, (rows + BY - 1) / BY); }
+
+template <class S, class C, int V>
+cudaError_t launch_fluid_v(const FluidArgs& a, const Inst* one, int grid, cudaStream_t s) {
+    constexpr int N = FLUID_VARIANTS[V].cpt, BYt = FLUID_VARIANTS[V].by;
+    if (one) {
+        const dim3 g((one->G.nx + 32 * N - 1) / (32 * N), (one->G.ny + BYt - 1) / BYt);
+        k_fluid_one<S, C, N, BYt><<<g, dim3(32, BYt), 0, s>>>(a, *one);
+    } else {
+        k_fluid<S, C, N, BYt><<<grid, dim3(32, BYt), 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <class S, class C>
+cudaError_t launch_fluid_t(int variant, const FluidArgs& a, const Inst* one, int grid, cudaStream_t s) {
+    switch (variant) {
+        case 1: return launch_fluid_v<S, C, 1>(a, one, grid, s);
+        case 2: return launch_fluid_v<S, C, 2>(a, one, grid, s);
+        default: return launch_fluid_v<S, C, 0>(a, one, grid, s);
+    }
+}
+
+template <class S, class C, int V>
+int blocks_v() {
+    constexpr int N = FLUID_VARIANTS[V].cpt, BYt = FLUID_VARIANTS[V].by;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fluid<S, C, N, BYt>, 32 * BYt, 0) != cudaSuccess)
+        n = 1;
+    return n > 0 ? n : 1;
+}
+
+template <class S, class C>
+int blocks_t(int variant) {
+    switch (variant) {
+        case 1: return blocks_v<S, C, 1>();
+        case 2: return blocks_v<S, C, 2>();
+        default: return blocks_v<S, C, 0>();
+    }
+}
 
 }  // namespace
 
@@ -250,24 +347,30 @@ size_t storage_bytes(int prec) {
 }
 size_t compute_bytes(int prec) { return prec == LBM_FP64 ? sizeof(double) : sizeof(float); }
 
-cudaError_t launch_init(int prec, void* f, const Geo& G, int kind, double init_u, cudaStream_t s) {
-    const dim3 b(32, BY), g = grid_for(G.nx, G.ny);
-    if (prec == LBM_FP64) k_init<double, double><<<g, b, 0, s>>>((double*)f, G, kind, init_u);
-    else if (prec == LBM_FP32) k_init<float, float><<<g, b, 0, s>>>((float*)f, G, kind, init_u);
-    else k_init<__half, float><<<g, b, 0, s>>>((__half*)f, G, kind, init_u);
+cudaError_t launch_init(int prec, void* fbuf, const Inst& I, int kind, double init_u, cudaStream_t s) {
+    const dim3 b(32, BY), g = grid_for(I.G.nx, I.G.ny);
+    if (prec == LBM_FP64) k_init<double, double><<<g, b, 0, s>>>((double*)fbuf + I.f_off, I.G, kind, init_u);
+    else if (prec == LBM_FP32) k_init<float, float><<<g, b, 0, s>>>((float*)fbuf + I.f_off, I.G, kind, init_u);
+    else k_init<__half, float><<<g, b, 0, s>>>((__half*)fbuf + I.f_off, I.G, kind, init_u);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fluid(int prec, const FluidArgs& a, cudaStream_t s) {
-    const dim3 b(32, BY), g((a.G.nx + 127) / 128, (a.G.ny + BY - 1) / BY);
-    if (prec == LBM_FP64) k_fluid<double, double><<<g, b, 0, s>>>(a);
-    else if (prec == LBM_FP32) k_fluid<float, float><<<g, b, 0, s>>>(a);
-    else k_fluid<__half, float><<<g, b, 0, s>>>(a);
-    return cudaGetLastError();
+cudaError_t launch_fluid(int prec, int variant, const FluidArgs& a, const Inst* one, int grid,
+                         cudaStream_t s) {
+    if (a.ntasks <= 0) return cudaSuccess;
+    if (prec == LBM_FP64) return launch_fluid_t<double, double>(variant, a, one, grid, s);
+    if (prec == LBM_FP32) return launch_fluid_t<float, float>(variant, a, one, grid, s);
+    return launch_fluid_t<__half, float>(variant, a, one, grid, s);
+}
+
+int fluid_blocks_per_sm(int prec, int variant) {
+    if (prec == LBM_FP64) return blocks_t<double, double>(variant);
+    if (prec == LBM_FP32) return blocks_t<float, float>(variant);
+    return blocks_t<__half, float>(variant);
 }
 
 cudaError_t launch_fields(int prec, const FieldArgs& a, cudaStream_t s) {
-    const dim3 b(32, BY), g = grid_for(a.G.nx, a.rows);
+    const dim3 b(32, BY), g = grid_for(a.I.G.nx, a.rows);
     if (prec == LBM_FP64) k_fields<double, double><<<g, b, 0, s>>>(a);
     else if (prec == LBM_FP32) k_fields<float, float><<<g, b, 0, s>>>(a);
     else k_fields<__half, float><<<g, b, 0, s>>>(a);

@@ -11,19 +11,28 @@
 
 namespace lbib {
 
-// Lattice geometry and the constants of the fluid step, passed by value to
-// every lattice kernel.  Populations are stored shifted, f~_i = f_i - w_i,
-// in 9 planes of ny rows of `pitch` elements (pitch a multiple of 32).
+// Lattice geometry and the constants of the fluid step of one instance.
+// Populations are stored shifted, f~_i = f_i - w_i, in 9 planes of ny rows
+// of `pitch` elements (pitch a multiple of 32).
 struct Geo {
     int nx, ny, pitch, nseg;  // nseg = pitch / 32 force-flag segments per row
     long long plane;          // elements per population plane
     int px, py;               // periodic in x / y
     double uw[4][2];          // wall velocities, sides x-, x+, y-, y+
     double g[2];              // constant fluid body force
+    double grav[2];           // gravity on the particles of this lattice
     double tau, omega;        // relaxation time and its inverse
     // the same constants in FP32, precomputed on the host: the FP32 kernels
     // must not touch FP64 (a small fraction of the FP32 rate on this part)
     float uwf[4][2], gf[2], omegaf;
+};
+
+// One lattice of a context (a context holds one or a batch of them).  Its
+// populations start at element f_off of each population buffer, its force
+// field at element flb_off of the force buffer, its flags at byte flags_off.
+struct Inst {
+    Geo G;
+    long long f_off, flb_off, flags_off;
 };
 
 // Rigid particle on the device (all FP64).  Index 0 of the history arrays
@@ -35,6 +44,7 @@ struct DParticle {
     double mass, inertia, area, rho_s, inv_mass, inv_inertia;
     int m0, nm;               // first marker, marker count
     int b0, nblk;             // first marker block, marker blocks (MB markers each)
+    int inst, pad_;           // lattice the particle lives in
     long long nupd;           // rigid-body updates done
 };
 
@@ -55,50 +65,66 @@ enum : unsigned { ERR_DOMAIN = 1u, ERR_NONFINITE = 2u, ERR_TIMEOUT = 4u };
 // reads populations buffer c reads particles pin = state[c] and writes the
 // updated bodies to pout = state[c ^ 1].
 struct ParticleArgs {
-    const void* f;            // post-collision populations (storage type)
-    Geo G;
+    const void* f;            // post-collision populations buffer (storage type)
+    const Inst* insts;
     const DParticle* pin;     // bodies at the start of the step
     DParticle* pout;          // bodies after the rigid-body update
     const int4* blk;          // per marker block: (particle, first marker, markers, 0)
     double* partial;          // per marker block: F_x, F_y, M partial sums
+    unsigned* count;          // per particle: probe blocks done (the last one resets it)
     const double2* rb;        // body-frame marker positions
     const double2* nb;        // body-frame normals
     const double* S;          // marker arc lengths
     void* recs;               // Rec<C>[max_markers]
     int4* boxes;              // per particle: support box (x0, y0, x1, y1)
     unsigned* err;
-    double gravity[2];
     int weight;
 };
 
 struct SpreadArgs {
-    Geo G;
-    const DParticle* parts;   // either state buffer (marker ranges only)
+    const Inst* insts;
+    const DParticle* parts;   // either state buffer (marker ranges, instance)
     const void* recs;
     const int4* boxes;
-    void* flb;                // 2 planes of compute type
-    uint8_t* flags;           // [ny][nseg]
+    void* flb;                // force buffer (2 planes of compute type per instance)
+    uint8_t* flags;           // flags buffer ([ny][nseg] bytes per instance)
     unsigned* err;
 };
 
+// Fluid step over a list of tiles: task t = (instance, tile x, tile y, 0),
+// a tile being 32 * CPT cells of BY rows.  One launch covers every tile of
+// every instance; a CTA takes tasks blockIdx.x, blockIdx.x + gridDim.x, ...
 struct FluidArgs {
     const void* fin;
     void* fout;
     void* flb;
     uint8_t* flags;
-    Geo G;
+    const Inst* insts;
+    const int4* tasks;
+    int ntasks;
 };
 
+// fluid tile shapes: (cells per thread, rows per block); the autotuner picks one
+constexpr int N_FLUID_VARIANTS = 3;
+struct FluidVariant {
+    int cpt, by;
+};
+constexpr FluidVariant FLUID_VARIANTS[N_FLUID_VARIANTS] = {{4, 8}, {4, 4}, {1, 8}};
+
 struct FieldArgs {
-    const void* f;
-    Geo G;
+    const void* f;            // population buffer
+    Inst I;
     int y0, rows;
     double *rho, *ux, *uy;    // [rows][nx]
 };
 
 // kernel launchers (fluid.cu / particles.cu); prec is an lbm_precision
-cudaError_t launch_init(int prec, void* f, const Geo& G, int kind, double init_u, cudaStream_t s);
-cudaError_t launch_fluid(int prec, const FluidArgs& a, cudaStream_t s);
+cudaError_t launch_init(int prec, void* fbuf, const Inst& I, int kind, double init_u, cudaStream_t s);
+// one != nullptr: the context holds that single lattice (2-D tile grid,
+// descriptor by value); otherwise the task list over all instances
+cudaError_t launch_fluid(int prec, int variant, const FluidArgs& a, const Inst* one, int grid,
+                         cudaStream_t s);
+int fluid_blocks_per_sm(int prec, int variant);
 cudaError_t launch_fields(int prec, const FieldArgs& a, cudaStream_t s);
 cudaError_t launch_probes(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s);
 cudaError_t launch_markers(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s);

@@ -6,12 +6,13 @@
 // k_probes: probe 1.2 dx along the outward normal of each marker of the body
 //   at its latest level, MLS fit of density and velocity there, surface
 //   traction; warp sums of force and torque per block (Eqs. 13-14, FP64).
-// k_markers: every block first adds its particle's block sums (fixed lane
-//   assignment and shuffle tree: the same bits in every block) and applies
-//   the two-level rigid-body update (Eqs. 15-16, FP64); the particle's first
-//   block stores the new body.  Then the markers at the new level: MLS
-//   interpolation (Eq. 8), direct-forcing force (Eq. 11), the per-marker
-//   spreading record S_l phi_k F_l of Eq. 12 and the particle's support box.
+//   The last block of a particle to finish (a completion counter; nothing
+//   waits) adds the block sums (fixed lane assignment and shuffle tree, so
+//   deterministic) and applies the two-level rigid-body update (Eqs. 15-16,
+//   FP64), once per particle, into the other state buffer.
+// k_markers: the markers at the new level: MLS interpolation (Eq. 8),
+//   direct-forcing force (Eq. 11), the per-marker spreading record
+//   S_l phi_k F_l of Eq. 12 and the particle's support box.
 // k_spread (one CTA per 32x16 tile of a particle's box): gathers, cell by
 //   cell and in marker order, the records whose support covers the cell,
 //   then adds the particle's sum into f_lb (the only atomic: one add per
@@ -56,9 +57,9 @@ __device__ __forceinline__ T quad_sum(T v) {  // sum over the 4 lanes of a marke
 
 // The MLS operator of Eqs. 8-10 split over the 4 lanes of a marker: lane q
 // holds support nodes k = q, q + 4, q + 8 (k < 9) of the 3x3 block around
-// the nearest node of (px, py).  Weights in precision C; the moment matrix
-// A = sum W p p^T is reduced across the lanes and inverted (adjugate) in
-// FP64.  On return the lane has, for its nodes, W (in w[]), the offsets,
+// the nearest node of (px, py).  Weights and the moment matrix
+// A = sum W p p^T in precision C (reduced across the lanes); A is inverted
+// (adjugate) in FP64.  On return the lane has, for its nodes, W (in w[]), the offsets,
 // and the first (phi) and, if D, second/third rows of A^-1 [W p].
 template <bool D, class C>
 struct QuadMLS {
@@ -76,10 +77,11 @@ struct QuadMLS {
         for (int j = 0; j < 3; ++j) kk[j] = q + 4 * j;
     }
 
-    // weights, moment matrix, FP64 solve (after support())
+    // weights and moment matrix in precision C, the 3x3 solve in FP64
+    // (after support())
     __device__ __forceinline__ void build(int kind, double px, double py, int q, bool active) {
         C W[3], DX[3], DY[3];
-        double a00 = 0, a01 = 0, a02 = 0, a11 = 0, a12 = 0, a22 = 0;
+        C b00 = C(0), b01 = C(0), b02 = C(0), b11 = C(0), b12 = C(0), b22 = C(0);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int k = kk[j];
@@ -87,22 +89,21 @@ struct QuadMLS {
             DX[j] = C(0);
             DY[j] = C(0);
             if (j < nk && active) {
-                const double dx = (double)(i0 + k % 3) - px, dy = (double)(j0 + k / 3) - py;
-                const C dxw = (C)dx, dyw = (C)dy;
+                const C dxw = (C)((double)(i0 + k % 3) - px), dyw = (C)((double)(j0 + k / 3) - py);
                 W[j] = mls_weight<C>(kind, sqrt(dxw * dxw + dyw * dyw) * C(1.0 / 2.6));
                 DX[j] = dxw;
                 DY[j] = dyw;
-                const double w = (double)W[j], ddx = (double)dxw, ddy = (double)dyw;
-                a00 += w;
-                a01 += w * ddx;
-                a02 += w * ddy;
-                a11 += w * ddx * ddx;
-                a12 += w * ddx * ddy;
-                a22 += w * ddy * ddy;
+                const C w = W[j], wx = w * dxw, wy = w * dyw;
+                b00 += w;
+                b01 += wx;
+                b02 += wy;
+                b11 += wx * dxw;
+                b12 += wx * dyw;
+                b22 += wy * dyw;
             }
         }
-        a00 = quad_sum(a00); a01 = quad_sum(a01); a02 = quad_sum(a02);
-        a11 = quad_sum(a11); a12 = quad_sum(a12); a22 = quad_sum(a22);
+        double a00 = (double)quad_sum(b00), a01 = (double)quad_sum(b01), a02 = (double)quad_sum(b02);
+        double a11 = (double)quad_sum(b11), a12 = (double)quad_sum(b12), a22 = (double)quad_sum(b22);
         if (!active) a00 = a11 = a22 = 1.0;  // keep idle lanes finite
         const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
         const double id = 1.0 / (a00 * c00 + a01 * c01 + a02 * c02);
@@ -124,12 +125,62 @@ struct QuadMLS {
     }
 };
 
+// Sum of the block force/torque sums of particle P and its rigid-body update
+// (Eqs. 15-16), computed identically by every lane.
+struct Body {
+    double X, Y, T, U, V, W, c, s, F0, F1, M;
+};
+__device__ __forceinline__ Body update_body(const DParticle* P, const double* partial,
+                                            const double gravity[2], int lane) {
+    double F0 = 0, F1 = 0, Mt = 0;
+    for (int b = P->b0 + lane; b < P->b0 + P->nblk; b += 32) {  // L2: other blocks wrote them
+        F0 += __ldcg(partial + 3 * (long long)b);
+        F1 += __ldcg(partial + 3 * (long long)b + 1);
+        Mt += __ldcg(partial + 3 * (long long)b + 2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {  // butterfly: every lane ends with the total
+        F0 += __shfl_xor_sync(0xffffffffu, F0, o);
+        F1 += __shfl_xor_sync(0xffffffffu, F1, o);
+        Mt += __shfl_xor_sync(0xffffffffu, Mt, o);
+    }
+    const double X0 = P->X[0][0], Y0 = P->X[0][1], th0 = P->th[0];
+    const double U0 = P->U[0][0], V0 = P->U[0][1], W0 = P->W[0];
+    const double buoy = (P->rho_s - 1.0) * P->area;
+    const double ax = (F0 + buoy * gravity[0]) * P->inv_mass;
+    const double ay = (F1 + buoy * gravity[1]) * P->inv_mass;
+    const double al = Mt * P->inv_inertia;
+    Body B;
+    if (P->nupd == 0) {  // one stored level: u1 = u0 + a, x1 = x0 + u1
+        B.U = U0 + ax;
+        B.V = V0 + ay;
+        B.W = W0 + al;
+        B.X = X0 + B.U;
+        B.Y = Y0 + B.V;
+        B.T = th0 + B.W;
+    } else {  // Eqs. 15-16 and the same two-level form for position and angle
+        const double k = 2.0 / 3.0;
+        B.U = k * (2.0 * U0 - 0.5 * P->U[1][0] + ax);
+        B.V = k * (2.0 * V0 - 0.5 * P->U[1][1] + ay);
+        B.W = k * (2.0 * W0 - 0.5 * P->W[1] + al);
+        B.X = k * (2.0 * X0 - 0.5 * P->X[1][0] + B.U);
+        B.Y = k * (2.0 * Y0 - 0.5 * P->X[1][1] + B.V);
+        B.T = k * (2.0 * th0 - 0.5 * P->th[1] + B.W);
+    }
+    sincos(B.T, &B.s, &B.c);
+    B.F0 = F0;
+    B.F1 = F1;
+    B.M = Mt;
+    return B;
+}
+
 template <class S, class C>
 __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
-    const S* __restrict__ f = static_cast<const S*>(a.f);
-    const Geo& G = a.G;
     const int4 bk = a.blk[blockIdx.x];
     const DParticle* P = a.pin + bk.x;
+    const Inst& I = a.insts[P->inst];
+    const Geo& G = I.G;
+    const S* __restrict__ f = static_cast<const S*>(a.f) + I.f_off;
     const int lane = threadIdx.x, q = lane & (LPM - 1);
     const int ml = lane / LPM, m = bk.y + ml;  // marker (absolute index)
     const bool active = ml < bk.z;
@@ -193,81 +244,28 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
         Fy = ty * Sl;
         Mz = (rx * ty - ry * tx) * Sl;
     }
-    Fx = warp_sum(Fx);
-    Fy = warp_sum(Fy);
-    Mz = warp_sum(Mz);
+    // only the quad leaders (lanes 0, 4, ..., 28) hold a contribution
+#pragma unroll
+    for (int o = 16; o >= LPM; o >>= 1) {
+        Fx += __shfl_down_sync(0xffffffffu, Fx, o);
+        Fy += __shfl_down_sync(0xffffffffu, Fy, o);
+        Mz += __shfl_down_sync(0xffffffffu, Mz, o);
+    }
     if (err) atomicOr(a.err, err);
+    unsigned done = 0;
     if (lane == 0) {
         double* part = a.partial + 3 * (long long)blockIdx.x;
         part[0] = Fx;
         part[1] = Fy;
         part[2] = Mz;
+        __threadfence();  // the block sums are visible before the count says so
+        done = atomicAdd(a.count + bk.x, 1u);
     }
-}
-
-// Sum of the block force/torque sums of particle P and its rigid-body update
-// (Eqs. 15-16), computed identically by every lane.
-struct Body {
-    double X, Y, T, U, V, W, c, s, F0, F1, M;
-};
-__device__ __forceinline__ Body update_body(const DParticle* P, const double* partial,
-                                            const double gravity[2], int lane) {
-    double F0 = 0, F1 = 0, Mt = 0;
-    for (int b = P->b0 + lane; b < P->b0 + P->nblk; b += 32) {
-        F0 += partial[3 * (long long)b];
-        F1 += partial[3 * (long long)b + 1];
-        Mt += partial[3 * (long long)b + 2];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {  // butterfly: every lane ends with the total
-        F0 += __shfl_xor_sync(0xffffffffu, F0, o);
-        F1 += __shfl_xor_sync(0xffffffffu, F1, o);
-        Mt += __shfl_xor_sync(0xffffffffu, Mt, o);
-    }
-    const double X0 = P->X[0][0], Y0 = P->X[0][1], th0 = P->th[0];
-    const double U0 = P->U[0][0], V0 = P->U[0][1], W0 = P->W[0];
-    const double buoy = (P->rho_s - 1.0) * P->area;
-    const double ax = (F0 + buoy * gravity[0]) * P->inv_mass;
-    const double ay = (F1 + buoy * gravity[1]) * P->inv_mass;
-    const double al = Mt * P->inv_inertia;
-    Body B;
-    if (P->nupd == 0) {  // one stored level: u1 = u0 + a, x1 = x0 + u1
-        B.U = U0 + ax;
-        B.V = V0 + ay;
-        B.W = W0 + al;
-        B.X = X0 + B.U;
-        B.Y = Y0 + B.V;
-        B.T = th0 + B.W;
-    } else {  // Eqs. 15-16 and the same two-level form for position and angle
-        const double k = 2.0 / 3.0;
-        B.U = k * (2.0 * U0 - 0.5 * P->U[1][0] + ax);
-        B.V = k * (2.0 * V0 - 0.5 * P->U[1][1] + ay);
-        B.W = k * (2.0 * W0 - 0.5 * P->W[1] + al);
-        B.X = k * (2.0 * X0 - 0.5 * P->X[1][0] + B.U);
-        B.Y = k * (2.0 * Y0 - 0.5 * P->X[1][1] + B.V);
-        B.T = k * (2.0 * th0 - 0.5 * P->th[1] + B.W);
-    }
-    sincos(B.T, &B.s, &B.c);
-    B.F0 = F0;
-    B.F1 = F1;
-    B.M = Mt;
-    return B;
-}
-
-template <class S, class C>
-__global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
-    const S* __restrict__ f = static_cast<const S*>(a.f);
-    const Geo& G = a.G;
-    const int4 bk = a.blk[blockIdx.x];
-    const DParticle* P = a.pin + bk.x;
-    Rec<C>* recs = static_cast<Rec<C>*>(a.recs);
-    const int lane = threadIdx.x, q = lane & (LPM - 1);
-    const int ml = lane / LPM, m = bk.y + ml;  // marker (absolute index)
-    const bool active = ml < bk.z;
-    unsigned err = 0;
-    const double2 rb = active ? a.rb[m] : make_double2(0, 0);
-    const Body B = update_body(P, a.partial, a.gravity, lane);
-    if (lane == 0 && bk.y == P->m0) {  // the particle's first block stores it
+    done = __shfl_sync(0xffffffffu, done, 0);
+    if (done != (unsigned)P->nblk - 1) return;  // not the last block (whole warp)
+    __threadfence();
+    const Body B = update_body(P, a.partial, G.grav, lane);
+    if (lane == 0) {
         DParticle* Q = a.pout + bk.x;
         *Q = *P;
         Q->X[1][0] = P->X[0][0]; Q->X[1][1] = P->X[0][1]; Q->th[1] = P->th[0];
@@ -279,9 +277,27 @@ __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
         Q->F[0] = B.F0; Q->F[1] = B.F1; Q->M = B.M;
         Q->nupd = P->nupd + 1;
         if (!isfinite(B.X) || !isfinite(B.Y) || !isfinite(B.T) || !isfinite(B.U) || !isfinite(B.W))
-            err |= ERR_NONFINITE;
+            atomicOr(a.err, ERR_NONFINITE);
+        a.count[bk.x] = 0;
     }
-    const double X = B.X, Y = B.Y, cn = B.c, sn = B.s;
+}
+
+template <class S, class C>
+__global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
+    const int4 bk = a.blk[blockIdx.x];
+    const DParticle* P = a.pin + bk.x;
+    const Inst& I = a.insts[P->inst];
+    const Geo& G = I.G;
+    const S* __restrict__ f = static_cast<const S*>(a.f) + I.f_off;
+    Rec<C>* recs = static_cast<Rec<C>*>(a.recs);
+    const int lane = threadIdx.x, q = lane & (LPM - 1);
+    const int ml = lane / LPM, m = bk.y + ml;  // marker (absolute index)
+    const bool active = ml < bk.z;
+    unsigned err = 0;
+    const double2 rb = active ? a.rb[m] : make_double2(0, 0);
+    const DParticle* Q = a.pout + bk.x;  // the body after this step's update
+    const double X = Q->X[0][0], Y = Q->X[0][1], cn = Q->cs[0][0], sn = Q->cs[0][1];
+    const double BU = Q->U[0][0], BV = Q->U[0][1], BW = Q->W[0];
     const double rx = cn * rb.x - sn * rb.y, ry = sn * rb.x + cn * rb.y;
     QuadMLS<false, C> M;
     M.support(X + rx, Y + ry, q);
@@ -312,8 +328,8 @@ __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
     if (active) {
         // Eq. 11 with dt = 1, times the arc length c_l = S_l of Eq. 12
         const double Sl = a.S[m];
-        const C sx = (C)(Sl * ((B.U - B.W * ry) - (double)ux));
-        const C sy = (C)(Sl * ((B.V + B.W * rx) - (double)uy));
+        const C sx = (C)(Sl * ((BU - BW * ry) - (double)ux));
+        const C sy = (C)(Sl * ((BV + BW * rx) - (double)uy));
         Rec<C>* rc = recs + m;
 #pragma unroll
         for (int j = 0; j < 3; ++j)
@@ -348,10 +364,12 @@ template <class C>
 __global__ void __launch_bounds__(TX * TY) k_spread(SpreadArgs a) {
     // records examined per round: as many as fit the static shared list
     constexpr int CAP = sizeof(Rec<C>) * TX * TY <= 48 * 1024 ? TX * TY : TX * TY / 2;
-    const Geo& G = a.G;
     const DParticle* P = a.parts + blockIdx.y;
+    const Inst& I = a.insts[P->inst];
+    const Geo& G = I.G;
     const Rec<C>* recs = static_cast<const Rec<C>*>(a.recs);
-    C* flb = static_cast<C*>(a.flb);
+    C* flb = static_cast<C*>(a.flb) + I.flb_off;
+    uint8_t* flags = a.flags + I.flags_off;
     __shared__ Rec<C> list[CAP];
     __shared__ int wcount[TX * TY / 32];
     const int4 box = a.boxes[blockIdx.y];
@@ -407,7 +425,7 @@ __global__ void __launch_bounds__(TX * TY) k_spread(SpreadArgs a) {
     const long long c = (long long)gy * G.pitch + gx;
     atomicAdd(flb + c, ax);
     atomicAdd(flb + G.plane + c, ay);
-    a.flags[gy * G.nseg + (gx >> 5)] = 1;
+    flags[gy * G.nseg + (gx >> 5)] = 1;
 }
 
 }  // namespace

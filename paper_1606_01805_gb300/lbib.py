@@ -30,7 +30,9 @@ LBM_W_EXP, LBM_W_CUBIC, LBM_W_QUARTIC, LBM_W_COSINE, LBM_W_POLY = range(5)
 EXPORTS = ["lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "lbm_step_timed",
            "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
            "lbm_get_particles", "lbm_steps_done", "lbm_last_error", "lbm_destroy",
-           "lbm_step_static"]
+           "lbm_step_static", "lbm_batch_workspace_bytes", "lbm_init_batch", "lbm_instances",
+           "lbm_add_particle_to", "lbm_get_instance_fields", "lbm_get_instance_populations",
+           "lbm_set_instance_populations", "lbm_get_tile", "lbm_set_tile"]
 LBM_STATIC_MAX_PARTICLES, LBM_STATIC_MAX_MARKERS = 1024, 16384
 
 
@@ -98,9 +100,23 @@ def load(path: os.PathLike | str | None = None):
     L.lbm_destroy.argtypes = [C.c_void_p]
     L.lbm_destroy.restype = None
     L.lbm_step_static.argtypes = [C.c_void_p, C.c_int32]
+    L.lbm_batch_workspace_bytes.argtypes = [C.POINTER(lbm_config), C.c_int32, C.POINTER(C.c_size_t)]
+    L.lbm_init_batch.argtypes = [C.POINTER(lbm_config), C.c_int32, C.POINTER(C.c_void_p)]
+    L.lbm_instances.restype = C.c_int32
+    L.lbm_instances.argtypes = [C.c_void_p]
+    L.lbm_add_particle_to.argtypes = [C.c_void_p, C.c_int32, C.POINTER(lbm_particle_desc),
+                                      C.POINTER(C.c_int32)]
+    L.lbm_get_instance_fields.argtypes = [C.c_void_p, C.c_int32, _dp, _dp, _dp]
+    L.lbm_get_instance_populations.argtypes = [C.c_void_p, C.c_int32, _dp]
+    L.lbm_set_instance_populations.argtypes = [C.c_void_p, C.c_int32, _dp]
+    L.lbm_get_tile.argtypes = [C.c_void_p] + [C.POINTER(C.c_int32)] * 3
+    L.lbm_set_tile.argtypes = [C.c_void_p, C.c_int32]
     for fn in ("lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "lbm_step_timed",
                "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
-               "lbm_get_particles", "lbm_step_static"):
+               "lbm_get_particles", "lbm_step_static", "lbm_batch_workspace_bytes",
+               "lbm_init_batch", "lbm_add_particle_to", "lbm_get_instance_fields",
+               "lbm_get_instance_populations", "lbm_set_instance_populations", "lbm_get_tile",
+               "lbm_set_tile"):
         getattr(L, fn).restype = C.c_int
     _lib = L
     return L
@@ -222,3 +238,114 @@ class Simulation:
         self._check(load().lbm_get_particles(self._h, arr, n, C.byref(cnt)), "lbm_get_particles")
         return [dict(xc=p.xc, yc=p.yc, theta=p.theta, u=(p.u[0], p.u[1]), omega=p.omega,
                      F=(p.F[0], p.F[1]), M=p.M) for p in arr[: cnt.value]]
+
+
+class Batch:
+    """Many independent lattices advanced together (lbm_init_batch).
+
+    `configs` is a list of dicts of make_config keyword arguments (nx, ny,
+    tau, bc, wall_u, ...); the first one also gives precision, weight and
+    the batch-wide capacities."""
+
+    def __init__(self, configs, stream=None, max_particles=None, max_markers=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        L = load()
+        n = len(configs)
+        arr = (lbm_config * n)()
+        for i, kw in enumerate(configs):
+            kw = dict(kw)
+            nx, ny, tau = kw.pop("nx"), kw.pop("ny"), kw.pop("tau")
+            arr[i] = make_config(nx, ny, tau, **kw)
+        if max_particles is not None:
+            arr[0].max_particles = max_particles
+        if max_markers is not None:
+            arr[0].max_markers = max_markers
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        arr[0].cuda_stream = C.c_void_p(self.stream.cuda_stream)
+        nbytes = C.c_size_t()
+        rc = L.lbm_batch_workspace_bytes(arr, n, C.byref(nbytes))
+        if rc != LBM_OK:
+            raise LbmError(rc, "batch workspace size")
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+        arr[0].d_workspace = C.c_void_p(self.workspace.data_ptr())
+        arr[0].workspace_bytes = nbytes.value
+        self._cfgs = arr
+        h = C.c_void_p()
+        rc = L.lbm_init_batch(arr, n, C.byref(h))
+        if rc != LBM_OK:
+            raise LbmError(rc, "lbm_init_batch")
+        self._h = h
+        self.shapes = [(c["ny"], c["nx"]) for c in configs]
+        self.np = 0
+
+    _check = Simulation._check
+    close = Simulation.close
+    __del__ = Simulation.__del__
+    step = Simulation.step
+    step_timed = Simulation.step_timed
+    sync = Simulation.sync
+    particles = Simulation.particles
+    steps_done = Simulation.steps_done
+
+    def __len__(self):
+        return load().lbm_instances(self._h)
+
+    def add_particle(self, instance, shape, dim, xc, yc, theta=0.0, rho_s=1.0, u0=(0.0, 0.0),
+                     omega0=0.0, n_markers=0):
+        d = lbm_particle_desc()
+        d.shape = shape
+        d.dim[0] = dim[0]
+        d.dim[1] = dim[1] if len(dim) > 1 else 0.0
+        d.xc, d.yc, d.theta, d.rho_s = xc, yc, theta, rho_s
+        d.u0[0], d.u0[1] = u0
+        d.omega0, d.n_markers = omega0, n_markers
+        pid = C.c_int32()
+        self._check(load().lbm_add_particle_to(self._h, instance, C.byref(d), C.byref(pid)),
+                    "lbm_add_particle_to")
+        self.np += 1
+        return pid.value
+
+    def fields(self, instance):
+        ny, nx = self.shapes[instance]
+        r = np.empty((ny, nx))
+        ux = np.empty_like(r)
+        uy = np.empty_like(r)
+        self._check(load().lbm_get_instance_fields(self._h, instance, _ptr(r), _ptr(ux), _ptr(uy)),
+                    "lbm_get_instance_fields")
+        return r, ux, uy
+
+    def populations(self, instance):
+        ny, nx = self.shapes[instance]
+        f = np.empty((9, ny, nx))
+        self._check(load().lbm_get_instance_populations(self._h, instance, _ptr(f)),
+                    "lbm_get_instance_populations")
+        return f
+
+    def set_populations(self, instance, f):
+        ny, nx = self.shapes[instance]
+        f = np.ascontiguousarray(f, np.float64)
+        assert f.shape == (9, ny, nx)
+        self._check(load().lbm_set_instance_populations(self._h, instance, _ptr(f)),
+                    "lbm_set_instance_populations")
+
+    tile = None  # set below
+    set_tile = None
+
+
+def _tile(self):
+    v, c, b = C.c_int32(), C.c_int32(), C.c_int32()
+    self._check(load().lbm_get_tile(self._h, C.byref(v), C.byref(c), C.byref(b)), "lbm_get_tile")
+    return v.value, c.value, b.value
+
+
+def _set_tile(self, variant):
+    self._check(load().lbm_set_tile(self._h, variant), "lbm_set_tile")
+
+
+Simulation.tile = _tile
+Simulation.set_tile = _set_tile
+Batch.tile = _tile
+Batch.set_tile = _set_tile

@@ -21,6 +21,12 @@ Workloads (lattice units, dx = dt = 1, fluid reference density 1):
   U = Re nu / H with Re = 20, tau = 0.8; one particle per instance from
   circle D32, ellipse 48 x 24, rectangle 64 x 16, square 32, triangle 40,
   y0 ~ U[0.2H, 0.8H] and angle ~ U[0, pi) from seed 2 (Section 4.3 set-up).
+* ``batched_screening``: 512 independent Couette channels of uneven sizes
+  (nx ~ U{256..1024}, ny ~ U{128..256}, bottom wall at rest, top at
+  U = Re nu / H, Re = 20, tau = 0.8), one particle each of a random shape
+  of the set, aspect ratio ~ U[1, 4] (ellipse, rectangle), circumscribed
+  radius 0.1 H .. 0.2 H, centred in x, y0 uniform between the walls with a
+  4-node clearance, angle ~ U[0, pi); seed 3 (the screening use case).
 * ``large_couette``: 16384 x 4096 antisymmetric Couette channel (cfg of the
   first workload scaled up) with 64 circles D = 20 on a seeded jittered
   grid: a lattice well beyond the 129 MB L2 for the bandwidth roofline.
@@ -139,6 +145,47 @@ def large_couette(nx=16384, ny=4096, n_particles=64, seed=5, steps=100):
     return Workload(f"large_couette_{nx}x{ny}", nx, ny, tau,
                     wall_u=((0, 0), (0, 0), (-U, 0.0), (U, 0.0)), init=COUETTE, steps=steps,
                     particles=parts)
+
+
+def shape_for(shape, rc, ar):
+    """dims of `shape` with circumscribed radius rc and aspect ratio ar"""
+    if shape == CIRCLE:
+        return (2 * rc,)
+    if shape == ELLIPSE:
+        return (2 * rc, 2 * rc / ar)
+    if shape == RECT:
+        w = 2 * rc * ar / math.sqrt(1 + ar * ar)
+        return (w, w / ar)
+    if shape == SQUARE:
+        return (2 * rc / math.sqrt(2),)
+    return (rc * math.sqrt(3),)
+
+
+def batched_screening(n=512, seed=3, nx_range=(256, 1024), ny_range=(128, 256), steps=10000,
+                      tau=0.8):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        nx = int(rng.integers(nx_range[0], nx_range[1] + 1))
+        ny = int(rng.integers(ny_range[0], ny_range[1] + 1))
+        H = ny - 1
+        U = 20.0 * (tau - 0.5) / 3.0 / H
+        shape = int(rng.integers(0, 5))
+        ar = float(rng.uniform(1.0, 4.0))
+        rc = float(rng.uniform(0.1, 0.2)) * H
+        th = float(rng.uniform(0.0, math.pi))
+        y0 = float(rng.uniform(rc + 4.0, H - rc - 4.0))
+        out.append(Workload(f"screen_{k}_{SHAPE_NAMES[shape]}_{nx}x{ny}", nx, ny, tau,
+                            wall_u=((0, 0), (0, 0), (0.0, 0.0), (U, 0.0)), init=COUETTE,
+                            steps=steps,
+                            particles=[Particle(shape, shape_for(shape, rc, ar), nx / 2, y0,
+                                                theta=th)]))
+    return out
+
+
+def batch_config(wl: Workload):
+    """make_config keyword arguments of one instance of a batch"""
+    return dict(nx=wl.nx, ny=wl.ny, tau=wl.tau, **wl.lattice_kwargs())
 
 
 def random_populations(nx, ny, seed, base, amp=0.02, smooth=0.05):

@@ -260,11 +260,12 @@ def test_fp16_shifted_storage_error_per_field(name):
     no parity target; the error against the FP64 oracle is measured per
     field and bounded at about three times the values observed on GB300
     (2000-step Couette: u 3.4e-3, rho 5.4e-5, centroid 1.9e-3 lu, omega
-    1.4e-3; 120-step sedimentation: u 1.6e-3; 500-step Taylor-Green: u 1e-3)."""
+    1.4e-3; 120-step sedimentation: u 1.6e-3, omega 7.1e-5 relative to the
+    1e-6 floor of a circle that barely turns; 500-step Taylor-Green: u 1e-3)."""
     if name == "couette":
         wl, bounds = W.couette_circle(steps=2000), dict(u=1e-2, rho=2e-4, pos=6e-3, om=5e-3)
     elif name == "sedimentation":
-        wl, bounds = W.sedimentation(steps=120), dict(u=5e-3, rho=6e-6, pos=1e-5, om=4e-5)
+        wl, bounds = W.sedimentation(steps=120), dict(u=5e-3, rho=6e-6, pos=1e-5, om=2.2e-4)
     else:
         wl = W.Workload("tg", 64, 64, 0.8, bc=(0, 0, 0, 0), init=W.TAYLOR_GREEN, init_u=0.01, steps=500)
         bounds = dict(u=3e-3, rho=1.2e-5)
