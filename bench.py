@@ -30,8 +30,9 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "MLUPS incl. IBM coupling, % of HBM roofline; batched & adjoint vs plain"
 FALLBACK_HBM_GBS = 6800.0
-BYTES_PER_CELL = {0: 144, 1: 72, 2: 36}  # read + write 9 populations (FP64 / FP32 / FP16)
-PREC_NAMES = {0: "f64", 1: "f32", 2: "f16-storage/f32"}
+# read + write 9 populations (FP64 / FP32 / FP16 / FP32 with 3 tangents)
+BYTES_PER_CELL = {0: 144, 1: 72, 2: 36, 3: 288}
+PREC_NAMES = {0: "f64", 1: "f32", 2: "f16-storage/f32", 3: "f32+3 tangents"}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per fluid-kernel launch from one
 # ncu capture, keyed by the hash of the kernel sources it was taken on
@@ -195,6 +196,31 @@ def time_batched(prec, steps, warmup, instances=512):
     b.close()
     cells = sum(w.cells for w in wls)
     return cells, ms_step / steps, ms_fluid / steps, tile
+
+
+def time_sensitivity(prec, steps, warmup, n=64):
+    """The sensitivity batch (64 Couette channels 400 x 100 with an ellipse
+    each, inputs (aspect ratio, y0, wall speed) from seed 4) as one context,
+    in the tangent mode (values and the 3 derivative directions) or plain
+    FP32: device time per step from the library's events."""
+    from paper_1606_01805_gb300 import lbib
+    from paper_1606_01805_gb300 import sensitivity as S
+    from paper_1606_01805_gb300 import workloads as W
+
+    P, T = W.sensitivity_batch(n=n)
+    wls = [W.sensitivity_ellipse(*P[b], steps=0, theta=float(T[b])) for b in range(n)]
+    sim = lbib.Batch([dict(W.batch_config(w), precision=prec) for w in wls], max_particles=n,
+                     max_markers=n * (W.SENS_MARKERS + 8))
+    tangent = prec == lbib.LBM_FP32_TANGENT
+    for b, w in enumerate(wls):
+        seed, dwall = S.seeds(P[b, 0])
+        if tangent:
+            sim.set_wall_tangents(dwall, b)
+        sim.add_particle(b, **w.particles[0].kwargs(), tangent=seed if tangent else None)
+    sim.step_timed(warmup)
+    ms, msf = sim.step_timed(steps)
+    sim.close()
+    return sum(w.cells for w in wls), ms / steps, msf / steps
 
 
 def time_per_instance(prec, sweeps):
@@ -402,6 +428,17 @@ def main():
             batched["batched_over_per_instance"] = batched["fp32"]["MLUPS"] / batched[
                 "fp32_per_instance_contexts"]["MLUPS"]
             out["batched"] = batched
+            tan = {"workload": "sensitivity batch: 64 Couette channels 400 x 100, one ellipse each; "
+                               "d(final y, mean omega)/d(aspect ratio, y0, wall speed)",
+                   "method": "forward-mode tangent (3 directions) of every step"}
+            for pname, pv in (("plain_fp32", 1), ("tangent", 3)):
+                cells, ms, msf = time_sensitivity(pv, 100, 10)
+                bpc = BYTES_PER_CELL[pv]
+                tan[pname] = {"MLUPS": cells / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                              "fluid_GBps": bpc * cells / (msf * 1e-3) / 1e9,
+                              "bytes_per_cell": bpc}
+            tan["tangent_over_plain_time"] = tan["tangent"]["ms_per_step"] / tan["plain_fp32"]["ms_per_step"]
+            out["tangent"] = tan
         if not args.no_cpu:
             v, n, dt = cpu_oracle_rate(wl)
             out["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",

@@ -57,12 +57,17 @@ typedef enum {
 typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_VELOCITY = 1 } lbm_bc;
 
 /* storage / arithmetic of the populations.  Particle work (probes, force
-   and torque reduction, MLS 3x3 solves, rigid-body update) is always FP64. */
+   and torque reduction, MLS 3x3 solves, rigid-body update) is always FP64
+   (FP64 with derivatives in the tangent mode). */
 typedef enum {
-    LBM_FP64 = 0,        /* FP64 populations, FP64 collision */
-    LBM_FP32 = 1,        /* FP32 populations stored as f - w_i, FP32 collision */
-    LBM_FP16_SHIFTED = 2 /* FP16 storage of f - w_i, FP32 collision */
+    LBM_FP64 = 0,         /* FP64 populations, FP64 collision */
+    LBM_FP32 = 1,         /* FP32 populations stored as f - w_i, FP32 collision */
+    LBM_FP16_SHIFTED = 2, /* FP16 storage of f - w_i, FP32 collision */
+    LBM_FP32_TANGENT = 3  /* LBM_FP32 plus forward-mode derivatives along
+                             LBM_TANGENTS directions (see lbm_add_particle_tangent) */
 } lbm_precision;
+
+#define LBM_TANGENTS 3
 
 typedef enum { LBM_INIT_REST = 0, LBM_INIT_COUETTE = 1, LBM_INIT_TAYLOR_GREEN = 2 } lbm_init_kind;
 
@@ -112,6 +117,8 @@ typedef struct {
     double xc, yc, theta;   /* centroid (unwrapped in periodic x) and angle */
     double u[2], omega;     /* velocity and angular velocity */
     double F[2], M;         /* hydrodynamic force and torque of the last step */
+    double omega_sum;       /* sum of omega over the rigid-body updates done
+                               (mean angular velocity = omega_sum / steps) */
 } lbm_particle_state;
 
 /*
@@ -256,11 +263,55 @@ lbm_status lbm_set_instance_populations(lbm_ctx* ctx, int32_t instance, const do
  * shape on the context's own lattices and keep the fastest (all shapes give
  * bit-identical results); lbm_get_tile reports the choice (index, cells per
  * thread, rows per block) and lbm_set_tile forces shape `variant`
- * (0 .. 2; LBM_EINVAL otherwise).
+ * (0 .. 2; LBM_EINVAL otherwise).  The tangent mode has shape 2 only.
  */
 lbm_status lbm_get_tile(const lbm_ctx* ctx, int32_t* variant, int32_t* cells_per_thread,
                         int32_t* rows_per_block);
 lbm_status lbm_set_tile(lbm_ctx* ctx, int32_t variant);
+
+/*
+ * Tangent mode (precision LBM_FP32_TANGENT) -- forward-mode
+ * differentiation of the whole step (the paper has no counterpart; it
+ * serves sensitivity studies of the transport results of Sections 4.1-4.3,
+ * e.g. of the equilibrium position or the rotation rate to the aspect ratio,
+ * the initial position or the wall speed).  Every population, force-field
+ * value and particle quantity carries, besides its value, its derivatives
+ * along LBM_TANGENTS input directions p_1..p_K; each step propagates them
+ * through Eqs. 2-16 by the chain rule, so after n steps they are the exact
+ * derivatives of the discrete n-step map (the choice of the 3x3 MLS support
+ * is piecewise constant and contributes none).  Values are those of
+ * LBM_FP32 (populations FP32 stored as f - w_i, particle work FP64);
+ * derivatives of the populations are FP32, of the particle state FP64.
+ * A population element is 16 bytes (value, K derivatives).
+ *
+ * Seeds, all before the first step:
+ *  - lbm_set_wall_tangents: dwall[(side * 2 + c) * LBM_TANGENTS + k] =
+ *    d(wall_u[side][c]) / dp_k (sides x-, x+, y-, y+).  Re-creates the
+ *    initial field of the instance (the Couette profile then carries the
+ *    derivatives of the wall speeds).
+ *  - lbm_add_particle_tangent: as lbm_add_particle_to, with
+ *    seed[k * 6 + j] = d(q_j) / dp_k for q = (dim[0], dim[1], xc, yc,
+ *    theta, rho_s).  The marker count is fixed by the values of the
+ *    dimensions (it does not change under a perturbation); markers, normals,
+ *    arc lengths, area and inertia carry the derivatives.
+ * Outputs:
+ *  - lbm_get_particle_tangents: out[(i * LBM_TANGENTS + k) *
+ *    LBM_TANGENT_FIELDS + j] = d(s_j) / dp_k of particle i, for
+ *    s = (xc, yc, theta, u[0], u[1], omega, F[0], F[1], M, omega_sum) of
+ *    lbm_particle_state; out holds cap * LBM_TANGENTS * LBM_TANGENT_FIELDS
+ *    doubles, *n receives the particle count.
+ *  - lbm_get_field_tangents: d(rho, ux, uy)/dp_k of lbm_get_fields, each
+ *    output [LBM_TANGENTS][ny][nx] doubles (any may be NULL, not all).
+ * Errors: LBM_EINVAL when the context is not in the tangent mode, after the
+ * first step (seeds), or for a bad instance or missing seeds.
+ */
+#define LBM_TANGENT_FIELDS 10
+lbm_status lbm_set_wall_tangents(lbm_ctx* ctx, int32_t instance, const double* dwall);
+lbm_status lbm_add_particle_tangent(lbm_ctx* ctx, int32_t instance, const lbm_particle_desc* desc,
+                                    const double* seed, int32_t* out_id);
+lbm_status lbm_get_particle_tangents(lbm_ctx* ctx, double* out, int32_t cap, int32_t* n);
+lbm_status lbm_get_field_tangents(lbm_ctx* ctx, int32_t instance, double* drho, double* dux,
+                                  double* duy);
 
 /* Steps done since lbm_init. */
 int64_t lbm_steps_done(const lbm_ctx* ctx);

@@ -35,13 +35,14 @@ struct lbm_ctx {
     int ntasks[N_FLUID_VARIANTS];
     int variant = 0;                // fluid tile shape in use
     int sms = 1;
-    DParticle* parts;               // two state buffers of cap_particles each
+    size_t rsz, psz;                // bytes of the particle real type R / of DParticleT<R>
+    char* parts;                    // two state buffers of cap_particles DParticleT<R> each
     int4* blk;
-    double* partial;
+    void* partial;                  // R[3][blocks]
     unsigned* count;
-    double2* rb;
-    double2* nb;
-    double* S;
+    void* rb;                       // Vec2<R>[markers]
+    void* nb;                       // Vec2<R>[markers]
+    void* S;                        // R[markers]
     void* recs;
     int4* boxes;
     unsigned* err;
@@ -76,7 +77,7 @@ const char* check_config(const lbm_config* c) {
         if (c->bc[i] != LBM_BC_PERIODIC && c->bc[i] != LBM_BC_VELOCITY) return "unknown side kind";
     if ((c->bc[0] == LBM_BC_PERIODIC) != (c->bc[1] == LBM_BC_PERIODIC)) return "x sides differ";
     if ((c->bc[2] == LBM_BC_PERIODIC) != (c->bc[3] == LBM_BC_PERIODIC)) return "y sides differ";
-    if (c->precision < LBM_FP64 || c->precision > LBM_FP16_SHIFTED) return "unknown precision";
+    if (c->precision < LBM_FP64 || c->precision > LBM_FP32_TANGENT) return "unknown precision";
     if (c->init < LBM_INIT_REST || c->init > LBM_INIT_TAYLOR_GREEN) return "unknown init";
     if (c->weight < LBM_W_EXP || c->weight > LBM_W_POLY) return "unknown weight";
     if (c->init == LBM_INIT_COUETTE && c->bc[2] != LBM_BC_VELOCITY) return "Couette needs y walls";
@@ -160,8 +161,11 @@ Layout layout(const lbm_config* cfgs, int n) {
         L.insts.push_back(I);
     }
     const size_t P = cap_particles(c0), M = cap_markers(c0), NB = cap_blocks(c0);
-    // rows of FP64 field output staged per lbm_get_fields chunk (<= 24 MB)
-    L.scratch_rows = (int)std::max<size_t>(1, (size_t)(1u << 20) / max_nx);
+    // rows of FP64 field output staged per lbm_get_fields chunk (<= 24 MB;
+    // the tangent mode adds KT derivative planes per field)
+    const int fplanes = prec == LBM_FP32_TANGENT ? 3 * (1 + KT) : 3;
+    L.scratch_rows = (int)std::max<size_t>(1, (size_t)(3u << 20) / fplanes / max_nx);
+    const size_t R = real_bytes(prec);
     size_t o = 0;
     L.f0 = o; o = up(o + fe * storage_bytes(prec));
     L.f1 = o; o = up(o + fe * storage_bytes(prec));
@@ -173,17 +177,17 @@ Layout layout(const lbm_config* cfgs, int n) {
         L.tasks[v] = o;
         o = up(o + (size_t)L.ntasks[v] * sizeof(int4));
     }
-    L.parts = o; o = up(o + 2 * P * sizeof(DParticle));
+    L.parts = o; o = up(o + 2 * P * particle_bytes(prec));
     L.blk = o; o = up(o + NB * sizeof(int4));
-    L.partial = o; o = up(o + 3 * NB * sizeof(double));
+    L.partial = o; o = up(o + 3 * NB * R);
     L.count = o; o = up(o + P * sizeof(unsigned));
-    L.rb = o; o = up(o + M * sizeof(double2));
-    L.nb = o; o = up(o + M * sizeof(double2));
-    L.S = o; o = up(o + M * sizeof(double));
+    L.rb = o; o = up(o + M * 2 * R);
+    L.nb = o; o = up(o + M * 2 * R);
+    L.S = o; o = up(o + M * R);
     L.recs = o; o = up(o + M * rec_bytes(prec));
     L.boxes = o; o = up(o + P * sizeof(int4));
     L.err = o; o = up(o + 16);
-    L.scratch = o; o = up(o + 3 * (size_t)L.scratch_rows * max_nx * sizeof(double));
+    L.scratch = o; o = up(o + fplanes * (size_t)L.scratch_rows * max_nx * sizeof(double));
     L.total = o;
     return L;
 }
@@ -215,12 +219,17 @@ lbm_status device_error(lbm_ctx* ctx) {
 
 constexpr int GRAPH_STEPS = 32;  // even, so a replay returns to the same buffer
 
+// particle state buffer `buf` (0 or 1)
+char* state(const lbm_ctx* ctx, int buf) {
+    return ctx->parts + (size_t)buf * cap_particles(ctx->cfg) * ctx->psz;
+}
+
 ParticleArgs particle_args(lbm_ctx* ctx, int cur) {
     ParticleArgs pa;
     pa.f = ctx->f[cur];
     pa.insts = ctx->insts;
-    pa.pin = ctx->parts + (size_t)cur * cap_particles(ctx->cfg);
-    pa.pout = ctx->parts + (size_t)(cur ^ 1) * cap_particles(ctx->cfg);
+    pa.pin = state(ctx, cur);
+    pa.pout = state(ctx, cur ^ 1);
     pa.blk = ctx->blk;
     pa.partial = ctx->partial;
     pa.count = ctx->count;
@@ -363,6 +372,10 @@ lbm_status autotune(lbm_ctx* ctx) {
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
     float best[N_FLUID_VARIANTS];
+    if (ctx->prec == LBM_FP32_TANGENT) {  // one tile shape only
+        ctx->variant = 2;
+        return LBM_OK;
+    }
     for (int v = 0; v < N_FLUID_VARIANTS; ++v) {  // warm every shape first
         best[v] = 1e30f;
         lbm_status s = launch_fluid_step(ctx, ctx->stream, ctx->cur, v);
@@ -426,13 +439,15 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
         ctx->tasks[v] = reinterpret_cast<int4*>(b + L.tasks[v]);
         ctx->ntasks[v] = L.ntasks[v];
     }
-    ctx->parts = reinterpret_cast<DParticle*>(b + L.parts);
+    ctx->rsz = real_bytes(ctx->prec);
+    ctx->psz = particle_bytes(ctx->prec);
+    ctx->parts = b + L.parts;
     ctx->blk = reinterpret_cast<int4*>(b + L.blk);
-    ctx->partial = reinterpret_cast<double*>(b + L.partial);
+    ctx->partial = b + L.partial;
     ctx->count = reinterpret_cast<unsigned*>(b + L.count);
-    ctx->rb = reinterpret_cast<double2*>(b + L.rb);
-    ctx->nb = reinterpret_cast<double2*>(b + L.nb);
-    ctx->S = reinterpret_cast<double*>(b + L.S);
+    ctx->rb = b + L.rb;
+    ctx->nb = b + L.nb;
+    ctx->S = b + L.S;
     ctx->recs = b + L.recs;
     ctx->boxes = reinterpret_cast<int4*>(b + L.boxes);
     ctx->err = reinterpret_cast<unsigned*>(b + L.err);
@@ -467,29 +482,40 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
     return LBM_OK;
 }
 
-lbm_status add_particle(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, int32_t* out_id) {
-    if (!ctx || !d) return LBM_EINVAL;
-    if (inst < 0 || inst >= ctx->ninst) return fail(ctx, LBM_EINVAL, "no such instance");
-    if (ctx->steps > 0) return fail(ctx, LBM_EINVAL, "particles must be added before the first step");
-    if (ctx->np >= cap_particles(ctx->cfg)) return fail(ctx, LBM_EINVAL, "particle capacity exceeded");
-    if (d->shape < LBM_SHAPE_CIRCLE || d->shape > LBM_SHAPE_TRIANGLE || !(d->dim[0] > 0) ||
-        !(d->rho_s > 0))
-        return fail(ctx, LBM_EINVAL, "bad particle shape, size or density");
-    if ((d->shape == LBM_SHAPE_ELLIPSE || d->shape == LBM_SHAPE_RECT) && !(d->dim[1] > 0))
-        return fail(ctx, LBM_EINVAL, "shape needs two dimensions");
+// seeds of the tangent mode: d(dim0, dim1, xc, yc, theta, rho_s)/dp_k
+constexpr int NSEED = 6;
+template <class R> R seeded(double v, const double* seed, int j);
+template <> double seeded<double>(double v, const double*, int) { return v; }
+template <> TD seeded<TD>(double v, const double* seed, int j) {
+    TD r(v);
+    for (int k = 0; k < KT; ++k) r.d[k] = seed ? seed[k * NSEED + j] : 0.0;
+    return r;
+}
+
+template <class R>
+lbm_status add_particle_t(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, const double* seed,
+                          int32_t* out_id) {
+    using std::cos;
+    using std::sin;
     const Geo& G = ctx->hinst[inst].G;
     const int room = cap_markers(ctx->cfg) - ctx->nmark;
-    std::vector<double> rb(2 * (size_t)std::max(room, 0) + 2), nb(rb.size()), S(rb.size() / 2);
-    ShapeOut so;
-    if (make_shape(*d, ctx->icfg[inst].marker_spacing, rb.data(), nb.data(), S.data(), room, &so) < 0)
+    const size_t cap = (size_t)std::max(room, 0) + 1;
+    std::vector<R> rb(2 * cap), nb(2 * cap), S(cap);
+    const R dim[2] = {seeded<R>(d->dim[0], seed, 0), seeded<R>(d->dim[1], seed, 1)};
+    ShapeOutT<R> so;
+    if (make_shape_t<R>(*d, dim, ctx->icfg[inst].marker_spacing, rb.data(), nb.data(), S.data(), room, &so) < 0)
         return fail(ctx, LBM_EINVAL, "marker capacity exceeded");
     const int n = so.n;
+    const R xc = seeded<R>(d->xc, seed, 2), yc = seeded<R>(d->yc, seed, 3);
+    const R th = seeded<R>(d->theta, seed, 4), rho_s = seeded<R>(d->rho_s, seed, 5);
+    const R c = cos(th), s = sin(th);
     // every marker and probe support must stay inside the walls
-    const double c = std::cos(d->theta), s = std::sin(d->theta);
     for (int l = 0; l < n; ++l) {
-        const double x = d->xc + c * rb[2 * l] - s * rb[2 * l + 1];
-        const double y = d->yc + s * rb[2 * l] + c * rb[2 * l + 1];
-        const double nx = c * nb[2 * l] - s * nb[2 * l + 1], ny = s * nb[2 * l] + c * nb[2 * l + 1];
+        const double cv = value_of(c), sv = value_of(s);
+        const double rx = value_of(rb[2 * l]), ry = value_of(rb[2 * l + 1]);
+        const double nx0 = value_of(nb[2 * l]), ny0 = value_of(nb[2 * l + 1]);
+        const double x = d->xc + cv * rx - sv * ry, y = d->yc + sv * rx + cv * ry;
+        const double nx = cv * nx0 - sv * ny0, ny = sv * nx0 + cv * ny0;
         for (int pass = 0; pass < 2; ++pass) {
             const double px = x + pass * 1.2 * nx, py = y + pass * 1.2 * ny;
             const int i0 = (int)std::floor(px + 0.5), j0 = (int)std::floor(py + 0.5);
@@ -499,24 +525,24 @@ lbm_status add_particle(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, int3
                 return fail(ctx, LBM_EINVAL, "particle support crosses a y wall");
         }
     }
-    DParticle P;
+    DParticleT<R> P;
     std::memset(&P, 0, sizeof P);
     for (int h = 0; h < 2; ++h) {
-        P.X[h][0] = d->xc;
-        P.X[h][1] = d->yc;
-        P.th[h] = d->theta;
+        P.X[h][0] = xc;
+        P.X[h][1] = yc;
+        P.th[h] = th;
         P.cs[h][0] = c;
         P.cs[h][1] = s;
-        P.U[h][0] = d->u0[0];
-        P.U[h][1] = d->u0[1];
-        P.W[h] = d->omega0;
+        P.U[h][0] = R(d->u0[0]);
+        P.U[h][1] = R(d->u0[1]);
+        P.W[h] = R(d->omega0);
     }
     P.area = so.area;
-    P.rho_s = d->rho_s;
-    P.mass = d->rho_s * so.area;
+    P.rho_s = rho_s;
+    P.mass = rho_s * so.area;
     P.inertia = P.mass * so.inertia_per_mass;
-    P.inv_mass = 1.0 / P.mass;
-    P.inv_inertia = 1.0 / P.inertia;
+    P.inv_mass = R(1.0) / P.mass;
+    P.inv_inertia = R(1.0) / P.inertia;
     P.m0 = ctx->nmark;
     P.nm = n;
     P.b0 = ctx->nblk;
@@ -526,17 +552,17 @@ lbm_status add_particle(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, int3
     std::vector<int4> blocks(P.nblk);
     for (int k = 0; k < P.nblk; ++k)
         blocks[k] = make_int4(ctx->np, P.m0 + k * MB, std::min(MB, n - k * MB), 0);
-    std::vector<double2> r2(n), n2(n);
-    for (int l = 0; l < n; ++l) {
-        r2[l] = make_double2(rb[2 * l], rb[2 * l + 1]);
-        n2[l] = make_double2(nb[2 * l], nb[2 * l + 1]);
-    }
-    CK(cudaMemcpyAsync(ctx->rb + P.m0, r2.data(), n * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->nb + P.m0, n2.data(), n * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->S + P.m0, S.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    const size_t v2 = sizeof(Vec2<R>);
+    static_assert(sizeof(Vec2<R>) == 2 * sizeof(R), "marker arrays are packed pairs");
+    CK(cudaMemcpyAsync(static_cast<char*>(ctx->rb) + P.m0 * v2, rb.data(), n * v2, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(static_cast<char*>(ctx->nb) + P.m0 * v2, nb.data(), n * v2, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(static_cast<char*>(ctx->S) + P.m0 * sizeof(R), S.data(), n * sizeof(R),
+                       cudaMemcpyHostToDevice, ctx->stream));
     for (int buf = 0; buf < 2; ++buf)
-        CK(cudaMemcpyAsync(ctx->parts + (size_t)buf * cap_particles(ctx->cfg) + ctx->np, &P, sizeof P,
-                           cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(state(ctx, buf) + (size_t)ctx->np * sizeof P, &P, sizeof P, cudaMemcpyHostToDevice,
+                           ctx->stream));
     CK(cudaMemcpyAsync(ctx->blk + P.b0, blocks.data(), P.nblk * sizeof(int4), cudaMemcpyHostToDevice,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -549,8 +575,29 @@ lbm_status add_particle(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, int3
     return LBM_OK;
 }
 
-lbm_status get_fields(lbm_ctx* ctx, int inst, double* rho, double* ux, double* uy) {
+lbm_status add_particle(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, const double* seed,
+                        int32_t* out_id) {
+    if (!ctx || !d) return LBM_EINVAL;
+    if (inst < 0 || inst >= ctx->ninst) return fail(ctx, LBM_EINVAL, "no such instance");
+    if (ctx->steps > 0) return fail(ctx, LBM_EINVAL, "particles must be added before the first step");
+    if (ctx->np >= cap_particles(ctx->cfg)) return fail(ctx, LBM_EINVAL, "particle capacity exceeded");
+    if (d->shape < LBM_SHAPE_CIRCLE || d->shape > LBM_SHAPE_TRIANGLE || !(d->dim[0] > 0) ||
+        !(d->rho_s > 0))
+        return fail(ctx, LBM_EINVAL, "bad particle shape, size or density");
+    if ((d->shape == LBM_SHAPE_ELLIPSE || d->shape == LBM_SHAPE_RECT) && !(d->dim[1] > 0))
+        return fail(ctx, LBM_EINVAL, "shape needs two dimensions");
+    if (seed && ctx->prec != LBM_FP32_TANGENT)
+        return fail(ctx, LBM_EINVAL, "tangent seeds need the LBM_FP32_TANGENT precision");
+    if (ctx->prec == LBM_FP32_TANGENT) return add_particle_t<TD>(ctx, inst, d, seed, out_id);
+    return add_particle_t<double>(ctx, inst, d, nullptr, out_id);
+}
+
+lbm_status get_fields(lbm_ctx* ctx, int inst, double* rho, double* ux, double* uy,
+                      double* drho = nullptr, double* dux = nullptr, double* duy = nullptr) {
     if (!ctx) return LBM_EINVAL;
+    const bool tan = drho || dux || duy;
+    if (tan && ctx->prec != LBM_FP32_TANGENT)
+        return fail(ctx, LBM_EINVAL, "field tangents need the LBM_FP32_TANGENT precision");
     if (inst < 0 || inst >= ctx->ninst) return fail(ctx, LBM_EINVAL, "no such instance");
     lbm_status s = device_error(ctx);
     if (s != LBM_OK) return s;
@@ -567,11 +614,17 @@ lbm_status get_fields(lbm_ctx* ctx, int inst, double* rho, double* ux, double* u
         fa.rho = ctx->scratch;
         fa.ux = ctx->scratch + chunk;
         fa.uy = ctx->scratch + 2 * chunk;
+        fa.tan = tan ? ctx->scratch + 3 * chunk : nullptr;  // [3][KT][rows][nx]
         CK(launch_fields(ctx->prec, fa, ctx->stream));
         const size_t n = (size_t)rows * nx, off = (size_t)y0 * nx;
         if (rho) CK(cudaMemcpyAsync(rho + off, fa.rho, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
         if (ux) CK(cudaMemcpyAsync(ux + off, fa.ux, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
         if (uy) CK(cudaMemcpyAsync(uy + off, fa.uy, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        double* outs[3] = {drho, dux, duy};
+        for (int q = 0; q < 3 && tan; ++q)
+            for (int k = 0; k < KT && outs[q]; ++k)
+                CK(cudaMemcpyAsync(outs[q] + (size_t)k * nx * ny + off, fa.tan + (size_t)(q * KT + k) * n, n * 8,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
     }
     return LBM_OK;
@@ -596,7 +649,8 @@ lbm_status get_populations(lbm_ctx* ctx, int inst, double* f) {
                 double v;
                 if (ctx->prec == LBM_FP64) v = reinterpret_cast<double*>(h.data())[k];
                 else if (ctx->prec == LBM_FP32) v = reinterpret_cast<float*>(h.data())[k];
-                else v = __half2float(reinterpret_cast<__half*>(h.data())[k]);
+                else if (ctx->prec == LBM_FP16_SHIFTED) v = __half2float(reinterpret_cast<__half*>(h.data())[k]);
+                else v = reinterpret_cast<TF*>(h.data())[k].v;
                 f[((size_t)i * ny + y) * nx + x] = v + weight_of(i);
             }
     return LBM_OK;
@@ -616,11 +670,44 @@ lbm_status set_populations(lbm_ctx* ctx, int inst, const double* f) {
                 const double v = f[((size_t)i * ny + y) * nx + x] - weight_of(i);
                 if (ctx->prec == LBM_FP64) reinterpret_cast<double*>(h.data())[k] = v;
                 else if (ctx->prec == LBM_FP32) reinterpret_cast<float*>(h.data())[k] = (float)v;
-                else reinterpret_cast<__half*>(h.data())[k] = __float2half_rn((float)v);
+                else if (ctx->prec == LBM_FP16_SHIFTED) reinterpret_cast<__half*>(h.data())[k] = __float2half_rn((float)v);
+                else reinterpret_cast<TF*>(h.data())[k] = TF((float)v);  // no derivative
             }
     char* dst = static_cast<char*>(ctx->f[ctx->cur]) + I.f_off * ctx->sb;
     CK(cudaMemcpyAsync(dst, h.data(), h.size(), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+// the first m particles of the current state buffer: values into `out`,
+// and in the tangent mode d(state)/dp_k into `tan` ([m][KT][LBM_TANGENT_FIELDS])
+template <class R>
+lbm_status read_particles(lbm_ctx* ctx, int m, lbm_particle_state* out, double* tan) {
+    std::vector<DParticleT<R>> h(m);
+    CK(cudaMemcpyAsync(h.data(), state(ctx, ctx->cur), m * sizeof(DParticleT<R>), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < m; ++i) {
+        const DParticleT<R>& P = h[i];
+        const R* q[LBM_TANGENT_FIELDS] = {&P.X[0][0], &P.X[0][1], &P.th[0], &P.U[0][0], &P.U[0][1],
+                                          &P.W[0],    &P.F[0],    &P.F[1],  &P.M,       &P.wsum};
+        if (out) {
+            out[i].xc = value_of(*q[0]);
+            out[i].yc = value_of(*q[1]);
+            out[i].theta = value_of(*q[2]);
+            out[i].u[0] = value_of(*q[3]);
+            out[i].u[1] = value_of(*q[4]);
+            out[i].omega = value_of(*q[5]);
+            out[i].F[0] = value_of(*q[6]);
+            out[i].F[1] = value_of(*q[7]);
+            out[i].M = value_of(*q[8]);
+            out[i].omega_sum = value_of(*q[9]);
+        }
+        if (tan)
+            for (int k = 0; k < KT; ++k)
+                for (int j = 0; j < LBM_TANGENT_FIELDS; ++j)
+                    tan[((size_t)i * KT + k) * LBM_TANGENT_FIELDS + j] = derivative(*q[j], k);
+    }
     return LBM_OK;
 }
 
@@ -647,12 +734,40 @@ lbm_status lbm_init_batch(const lbm_config* cfgs, int32_t n, lbm_ctx** out) {
 int32_t lbm_instances(const lbm_ctx* ctx) { return ctx ? ctx->ninst : 0; }
 
 lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* d, int32_t* out_id) {
-    return add_particle(ctx, 0, d, out_id);
+    return add_particle(ctx, 0, d, nullptr, out_id);
 }
 
 lbm_status lbm_add_particle_to(lbm_ctx* ctx, int32_t instance, const lbm_particle_desc* d,
                                int32_t* out_id) {
-    return add_particle(ctx, instance, d, out_id);
+    return add_particle(ctx, instance, d, nullptr, out_id);
+}
+
+lbm_status lbm_add_particle_tangent(lbm_ctx* ctx, int32_t instance, const lbm_particle_desc* d,
+                                    const double* seed, int32_t* out_id) {
+    if (!seed) return fail(ctx, LBM_EINVAL, "no tangent seeds");
+    return add_particle(ctx, instance, d, seed, out_id);
+}
+
+lbm_status lbm_set_wall_tangents(lbm_ctx* ctx, int32_t instance, const double* dwall) {
+    if (!ctx || !dwall) return LBM_EINVAL;
+    if (ctx->prec != LBM_FP32_TANGENT) return fail(ctx, LBM_EINVAL, "wall tangents need LBM_FP32_TANGENT");
+    if (instance < 0 || instance >= ctx->ninst) return fail(ctx, LBM_EINVAL, "no such instance");
+    if (ctx->steps > 0) return fail(ctx, LBM_EINVAL, "wall tangents must be set before the first step");
+    Inst& I = ctx->hinst[instance];
+    for (int sd = 0; sd < 4; ++sd)
+        for (int c = 0; c < 2; ++c)
+            for (int k = 0; k < KT; ++k) {
+                const double v = dwall[(sd * 2 + c) * KT + k];
+                I.G.uwd[sd][c][k] = v;
+                I.G.uwdf[sd][c][k] = (float)v;
+            }
+    CK(cudaMemcpyAsync(ctx->insts + instance, &I, sizeof(Inst), cudaMemcpyHostToDevice, ctx->stream));
+    // the initial field (a Couette profile) follows the wall speeds
+    CK(launch_init(ctx->prec, ctx->f[ctx->cur], I, ctx->icfg[instance].init, ctx->icfg[instance].init_u,
+                   ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    drop_graphs(ctx);  // a single-lattice step carries the descriptor by value
+    return LBM_OK;
 }
 
 lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps) {
@@ -721,6 +836,11 @@ lbm_status lbm_get_instance_fields(lbm_ctx* ctx, int32_t instance, double* rho, 
     return get_fields(ctx, instance, rho, ux, uy);
 }
 
+lbm_status lbm_get_field_tangents(lbm_ctx* ctx, int32_t instance, double* drho, double* dux, double* duy) {
+    if (!drho && !dux && !duy) return fail(ctx, LBM_EINVAL, "no output");
+    return get_fields(ctx, instance, nullptr, nullptr, nullptr, drho, dux, duy);
+}
+
 lbm_status lbm_get_populations(lbm_ctx* ctx, double* f) { return get_populations(ctx, 0, f); }
 
 lbm_status lbm_get_instance_populations(lbm_ctx* ctx, int32_t instance, double* f) {
@@ -739,23 +859,21 @@ lbm_status lbm_get_particles(lbm_ctx* ctx, lbm_particle_state* out, int32_t cap,
     if (s != LBM_OK && s != LBM_EDOMAIN) return s;
     if (n) *n = ctx->np;
     if (ctx->np == 0 || !out || cap <= 0) return s;
-    std::vector<DParticle> h(ctx->np);
-    const DParticle* cur_state = ctx->parts + (size_t)ctx->cur * cap_particles(ctx->cfg);
-    CK(cudaMemcpyAsync(h.data(), cur_state, ctx->np * sizeof(DParticle), cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    for (int i = 0; i < std::min<int>(cap, ctx->np); ++i) {
-        out[i].xc = h[i].X[0][0];
-        out[i].yc = h[i].X[0][1];
-        out[i].theta = h[i].th[0];
-        out[i].u[0] = h[i].U[0][0];
-        out[i].u[1] = h[i].U[0][1];
-        out[i].omega = h[i].W[0];
-        out[i].F[0] = h[i].F[0];
-        out[i].F[1] = h[i].F[1];
-        out[i].M = h[i].M;
-    }
-    return s;
+    const int m = std::min<int>(cap, ctx->np);
+    lbm_status r = ctx->prec == LBM_FP32_TANGENT ? read_particles<TD>(ctx, m, out, nullptr)
+                                                 : read_particles<double>(ctx, m, out, nullptr);
+    return r != LBM_OK ? r : s;
+}
+
+lbm_status lbm_get_particle_tangents(lbm_ctx* ctx, double* out, int32_t cap, int32_t* n) {
+    if (!ctx) return LBM_EINVAL;
+    if (ctx->prec != LBM_FP32_TANGENT) return fail(ctx, LBM_EINVAL, "particle tangents need LBM_FP32_TANGENT");
+    lbm_status s = device_error(ctx);
+    if (s != LBM_OK && s != LBM_EDOMAIN) return s;
+    if (n) *n = ctx->np;
+    if (ctx->np == 0 || !out || cap <= 0) return s;
+    lbm_status r = read_particles<TD>(ctx, std::min<int>(cap, ctx->np), nullptr, out);
+    return r != LBM_OK ? r : s;
 }
 
 lbm_status lbm_get_tile(const lbm_ctx* ctx, int32_t* variant, int32_t* cells_per_thread,
@@ -770,6 +888,8 @@ lbm_status lbm_get_tile(const lbm_ctx* ctx, int32_t* variant, int32_t* cells_per
 lbm_status lbm_set_tile(lbm_ctx* ctx, int32_t variant) {
     if (!ctx) return LBM_EINVAL;
     if (variant < 0 || variant >= N_FLUID_VARIANTS) return fail(ctx, LBM_EINVAL, "no such tile variant");
+    if (ctx->prec == LBM_FP32_TANGENT && variant != 2)
+        return fail(ctx, LBM_EINVAL, "the tangent mode has tile variant 2 only");
     if (variant != ctx->variant) {
         ctx->variant = variant;
         drop_graphs(ctx);  // captured steps launch the old shape
@@ -836,7 +956,7 @@ extern "C" lbm_status lbm_step_static(lbm_ctx* ctx, int32_t nsteps) {
                         " markers do not fit its static scratch");
     // layout of this context's scratch inside the static array
     size_t o = 0;
-    const size_t o_partial = o; o = up(o + 3 * (size_t)ctx->nblk * sizeof(double));
+    const size_t o_partial = o; o = up(o + 3 * (size_t)ctx->nblk * ctx->rsz);
     const size_t o_count = o;   o = up(o + (size_t)ctx->np * sizeof(unsigned));
     const size_t o_boxes = o;   o = up(o + (size_t)ctx->np * sizeof(int4));
     const size_t o_recs = o;    o = up(o + (size_t)ctx->nmark * rec_bytes(ctx->prec));
@@ -853,7 +973,7 @@ extern "C" lbm_status lbm_step_static(lbm_ctx* ctx, int32_t nsteps) {
     for (int32_t k = 0; k < nsteps; ++k) {
         if (ctx->np > 0) {
             ParticleArgs pa = particle_args(ctx, ctx->cur);
-            pa.partial = reinterpret_cast<double*>(sb + o_partial);
+            pa.partial = sb + o_partial;
             pa.count = reinterpret_cast<unsigned*>(sb + o_count);
             pa.recs = sb + o_recs;
             pa.boxes = reinterpret_cast<int4*>(sb + o_boxes);

@@ -231,10 +231,11 @@ __device__ __forceinline__ void fluid_tile(const Geo& G, const S* __restrict__ f
 
 // resident blocks per SM the register budget is sized for: 1024 threads per
 // SM for 4 FP32 / FP16 cells per thread, 512 for FP64 (two registers per
-// value), 1280 (FP64: 768) for one cell per thread
+// value), 1280 (FP64: 768) for one cell per thread; 512 for one tangent-mode
+// cell (four registers per value)
 template <class S, int N, int BYt> struct FluidOccupancy {
     static constexpr int value =
-        (N == 1 ? (sizeof(S) == 8 ? 3 : 5) : (sizeof(S) == 8 ? 2 : 4)) * 8 / BYt;
+        (sizeof(S) == 16 ? 2 : (N == 1 ? (sizeof(S) == 8 ? 3 : 5) : (sizeof(S) == 8 ? 2 : 4))) * 8 / BYt;
 };
 
 // persistent fused fluid step over the task list (all instances)
@@ -262,29 +263,38 @@ __global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value)
                         blockIdx.y * BYt + threadIdx.y);
 }
 
-// initial post-collision field f* = f^eq(rho, u) (Eq. 2), shifted
-template <class S, class C>
+// initial post-collision field f* = f^eq(rho, u) (Eq. 2), shifted; R is the
+// real type of the field (with tangents, the Couette profile carries the
+// derivatives of the wall speeds)
+template <class S, class C, class R>
 __global__ void k_init(S* f, Geo G, int kind, double U0) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
     if (x >= G.nx || y >= G.ny) return;
-    double rho = 1.0, ux = 0.0, uy = 0.0;
+    R rho = R(1.0), ux = R(0.0), uy = R(0.0);
     if (kind == LBM_INIT_COUETTE) {
-        const double ub = G.uw[2][0], ut = G.uw[3][0];
-        ux = ub + (ut - ub) * (double)y / (double)(G.ny - 1);
+        const R ub = geo_uw_r<R>(G, 2, 0), ut = geo_uw_r<R>(G, 3, 0);
+        ux = ub + (ut - ub) * ((double)y / (double)(G.ny - 1));
     } else if (kind == LBM_INIT_TAYLOR_GREEN) {
         const double kx = 2.0 * M_PI / G.nx, ky = 2.0 * M_PI / G.ny;
-        ux = -U0 * cos(kx * x) * sin(ky * y);
-        uy = U0 * (kx / ky) * sin(kx * x) * cos(ky * y);
-        rho = 1.0 - 0.75 * U0 * U0 * (cos(2.0 * kx * x) + (kx * kx) / (ky * ky) * cos(2.0 * ky * y));
+        ux = R(-U0 * cos(kx * x) * sin(ky * y));
+        uy = R(U0 * (kx / ky) * sin(kx * x) * cos(ky * y));
+        rho = R(1.0 - 0.75 * U0 * U0 * (cos(2.0 * kx * x) + (kx * kx) / (ky * ky) * cos(2.0 * ky * y)));
     }
-    const double usq = ux * ux + uy * uy;
+    const R usq = ux * ux + uy * uy;
     const long long c = (long long)y * G.pitch + x;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const double eu = cx(i) * ux + cy(i) * uy;
-        const double feq = wt(i) * ((rho - 1.0) + rho * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq));
+        const R eu = (double)cx(i) * ux + (double)cy(i) * uy;
+        const R feq = wt(i) * ((rho - 1.0) + rho * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq));
         st<S, C>(f + (long long)i * G.plane + c, (C)feq);
     }
+}
+
+__device__ __forceinline__ void put_tangents(double, double*, long long) {}
+__device__ __forceinline__ void put_tangents(float, double*, long long) {}
+__device__ __forceinline__ void put_tangents(const TF& v, double* out, long long stride) {
+#pragma unroll
+    for (int j = 0; j < KT; ++j) out[j * stride] = (double)v.d[j];
 }
 
 template <class S, class C>
@@ -294,9 +304,15 @@ __global__ void k_fields(FieldArgs a) {
     C rho, ux, uy;
     node_fields<S, C>(static_cast<const S*>(a.f) + a.I.f_off, a.I.G, x, a.y0 + r, rho, ux, uy);
     const long long k = (long long)r * a.I.G.nx + x;
-    a.rho[k] = (double)rho;
-    a.ux[k] = (double)ux;
-    a.uy[k] = (double)uy;
+    a.rho[k] = (double)value_of(rho);
+    a.ux[k] = (double)value_of(ux);
+    a.uy[k] = (double)value_of(uy);
+    if (a.tan) {  // tangent mode: d(rho, ux, uy)/dp_j as planes [3][K][rows][nx]
+        const long long pl = (long long)a.rows * a.I.G.nx;
+        put_tangents(rho, a.tan + k, pl);
+        put_tangents(ux, a.tan + DualTraits<C>::K * pl + k, pl);
+        put_tangents(uy, a.tan + 2 * DualTraits<C>::K * pl + k, pl);
+    }
 }
 
 dim3 grid_for(int nx, int rows) { return dim3((nx + 31) / 32, (rows + BY - 1) / BY); }
@@ -343,37 +359,54 @@ int blocks_t(int variant) {
 }  // namespace
 
 size_t storage_bytes(int prec) {
-    return prec == LBM_FP64 ? sizeof(double) : (prec == LBM_FP32 ? sizeof(float) : sizeof(__half));
+    switch (prec) {
+        case LBM_FP64: return sizeof(double);
+        case LBM_FP32: return sizeof(float);
+        case LBM_FP16_SHIFTED: return sizeof(__half);
+        default: return sizeof(TF);
+    }
 }
-size_t compute_bytes(int prec) { return prec == LBM_FP64 ? sizeof(double) : sizeof(float); }
+size_t compute_bytes(int prec) {
+    return prec == LBM_FP64 ? sizeof(double) : (prec == LBM_FP32_TANGENT ? sizeof(TF) : sizeof(float));
+}
 
 cudaError_t launch_init(int prec, void* fbuf, const Inst& I, int kind, double init_u, cudaStream_t s) {
     const dim3 b(32, BY), g = grid_for(I.G.nx, I.G.ny);
-    if (prec == LBM_FP64) k_init<double, double><<<g, b, 0, s>>>((double*)fbuf + I.f_off, I.G, kind, init_u);
-    else if (prec == LBM_FP32) k_init<float, float><<<g, b, 0, s>>>((float*)fbuf + I.f_off, I.G, kind, init_u);
-    else k_init<__half, float><<<g, b, 0, s>>>((__half*)fbuf + I.f_off, I.G, kind, init_u);
+    if (prec == LBM_FP64)
+        k_init<double, double, double><<<g, b, 0, s>>>((double*)fbuf + I.f_off, I.G, kind, init_u);
+    else if (prec == LBM_FP32)
+        k_init<float, float, double><<<g, b, 0, s>>>((float*)fbuf + I.f_off, I.G, kind, init_u);
+    else if (prec == LBM_FP16_SHIFTED)
+        k_init<__half, float, double><<<g, b, 0, s>>>((__half*)fbuf + I.f_off, I.G, kind, init_u);
+    else
+        k_init<TF, TF, TD><<<g, b, 0, s>>>((TF*)fbuf + I.f_off, I.G, kind, init_u);
     return cudaGetLastError();
 }
 
+// the tangent mode has the one-cell tile only (variant 2): a cell's 9
+// populations with their derivatives already take 36 registers
 cudaError_t launch_fluid(int prec, int variant, const FluidArgs& a, const Inst* one, int grid,
                          cudaStream_t s) {
     if (a.ntasks <= 0) return cudaSuccess;
     if (prec == LBM_FP64) return launch_fluid_t<double, double>(variant, a, one, grid, s);
     if (prec == LBM_FP32) return launch_fluid_t<float, float>(variant, a, one, grid, s);
-    return launch_fluid_t<__half, float>(variant, a, one, grid, s);
+    if (prec == LBM_FP16_SHIFTED) return launch_fluid_t<__half, float>(variant, a, one, grid, s);
+    return launch_fluid_v<TF, TF, 2>(a, one, grid, s);
 }
 
 int fluid_blocks_per_sm(int prec, int variant) {
     if (prec == LBM_FP64) return blocks_t<double, double>(variant);
     if (prec == LBM_FP32) return blocks_t<float, float>(variant);
-    return blocks_t<__half, float>(variant);
+    if (prec == LBM_FP16_SHIFTED) return blocks_t<__half, float>(variant);
+    return blocks_v<TF, TF, 2>();
 }
 
 cudaError_t launch_fields(int prec, const FieldArgs& a, cudaStream_t s) {
     const dim3 b(32, BY), g = grid_for(a.I.G.nx, a.rows);
     if (prec == LBM_FP64) k_fields<double, double><<<g, b, 0, s>>>(a);
     else if (prec == LBM_FP32) k_fields<float, float><<<g, b, 0, s>>>(a);
-    else k_fields<__half, float><<<g, b, 0, s>>>(a);
+    else if (prec == LBM_FP16_SHIFTED) k_fields<__half, float><<<g, b, 0, s>>>(a);
+    else k_fields<TF, TF><<<g, b, 0, s>>>(a);
     return cudaGetLastError();
 }
 

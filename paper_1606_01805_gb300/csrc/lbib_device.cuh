@@ -34,7 +34,19 @@ template <> __device__ __forceinline__ float ld<float, float>(const float* p) { 
 template <> __device__ __forceinline__ float ld<__half, float>(const __half* p) {
     return __half2float(__ldg(p));
 }
+template <> __device__ __forceinline__ TF ld<TF, TF>(const TF* p) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    TF r;
+    r.v = q.x;
+    r.d[0] = q.y;
+    r.d[1] = q.z;
+    r.d[2] = q.w;
+    return r;
+}
 template <class S, class C> __device__ __forceinline__ void st(S* p, C v);
+template <> __device__ __forceinline__ void st<TF, TF>(TF* p, TF v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v.v, v.d[0], v.d[1], v.d[2]);
+}
 template <> __device__ __forceinline__ void st<double, double>(double* p, double v) { *p = v; }
 template <> __device__ __forceinline__ void st<float, float>(float* p, float v) { *p = v; }
 template <> __device__ __forceinline__ void st<__half, float>(__half* p, float v) {
@@ -51,6 +63,23 @@ template <> __device__ __forceinline__ float geo_uw<float>(const Geo& G, int s, 
 template <class C> __device__ __forceinline__ C geo_omega(const Geo& G);
 template <> __device__ __forceinline__ double geo_omega<double>(const Geo& G) { return G.omega; }
 template <> __device__ __forceinline__ float geo_omega<float>(const Geo& G) { return G.omegaf; }
+// tangent mode: the body force and relaxation rate carry no derivative, the
+// wall velocities carry the seeds of lbm_set_wall_tangents
+template <> __device__ __forceinline__ TF geo_g<TF>(const Geo& G, int k) { return TF(G.gf[k]); }
+template <> __device__ __forceinline__ TF geo_omega<TF>(const Geo& G) { return TF(G.omegaf); }
+template <> __device__ __forceinline__ TF geo_uw<TF>(const Geo& G, int s, int k) {
+    TF r(G.uwf[s][k]);
+    for (int j = 0; j < KT; ++j) r.d[j] = G.uwdf[s][k][j];
+    return r;
+}
+// the same in the particle real type
+template <class R> __device__ __forceinline__ R geo_uw_r(const Geo& G, int s, int k);
+template <> __device__ __forceinline__ double geo_uw_r<double>(const Geo& G, int s, int k) { return G.uw[s][k]; }
+template <> __device__ __forceinline__ TD geo_uw_r<TD>(const Geo& G, int s, int k) {
+    TD r(G.uw[s][k]);
+    for (int j = 0; j < KT; ++j) r.d[j] = G.uwd[s][k][j];
+    return r;
+}
 
 // ------------------------------------------------- streaming + walls ----
 // Pull the populations arriving at (x, y) (Eq. 4 in pull form).  Sources

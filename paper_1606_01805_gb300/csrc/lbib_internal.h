@@ -8,8 +8,20 @@
 #include <cuda_runtime.h>
 
 #include "../../include/lbib.h"
+#include "dual.h"
 
 namespace lbib {
+
+// tangent mode: K directions; FP32 populations and FP64 particle work
+constexpr int KT = LBM_TANGENTS;
+using TF = Dual<float, KT>;
+using TD = Dual<double, KT>;
+
+// two-component vector of a real type (double2-compatible for double)
+template <class R>
+struct Vec2 {
+    R x, y;
+};
 
 // Lattice geometry and the constants of the fluid step of one instance.
 // Populations are stored shifted, f~_i = f_i - w_i, in 9 planes of ny rows
@@ -25,6 +37,9 @@ struct Geo {
     // the same constants in FP32, precomputed on the host: the FP32 kernels
     // must not touch FP64 (a small fraction of the FP32 rate on this part)
     float uwf[4][2], gf[2], omegaf;
+    // tangent mode: derivatives of the wall velocities along the K directions
+    double uwd[4][2][KT];
+    float uwdf[4][2][KT];
 };
 
 // One lattice of a context (a context holds one or a batch of them).  Its
@@ -35,18 +50,22 @@ struct Inst {
     long long f_off, flb_off, flags_off;
 };
 
-// Rigid particle on the device (all FP64).  Index 0 of the history arrays
-// is the latest level, index 1 the level before it.
-struct DParticle {
-    double X[2][2], th[2], U[2][2], W[2];
-    double cs[2][2];          // (cos, sin) of th[0] and th[1]
-    double F[2], M;
-    double mass, inertia, area, rho_s, inv_mass, inv_inertia;
+// Rigid particle on the device, real type R (FP64, or FP64 with tangents).
+// Index 0 of the history arrays is the latest level, index 1 the level
+// before it.
+template <class R>
+struct DParticleT {
+    R X[2][2], th[2], U[2][2], W[2];
+    R cs[2][2];               // (cos, sin) of th[0] and th[1]
+    R F[2], M;
+    R wsum;                   // sum of the angular velocity over the updates done
+    R mass, inertia, area, rho_s, inv_mass, inv_inertia;
     int m0, nm;               // first marker, marker count
     int b0, nblk;             // first marker block, marker blocks (MB markers each)
     int inst, pad_;           // lattice the particle lives in
     long long nupd;           // rigid-body updates done
 };
+using DParticle = DParticleT<double>;
 
 constexpr int MB = 8;         // markers per block of the marker kernels (one warp, 4 lanes each)
 
@@ -64,17 +83,18 @@ enum : unsigned { ERR_DOMAIN = 1u, ERR_NONFINITE = 2u, ERR_TIMEOUT = 4u };
 // The particle state is double-buffered with the populations: a step that
 // reads populations buffer c reads particles pin = state[c] and writes the
 // updated bodies to pout = state[c ^ 1].
+// Arrays of the real type R are passed untyped (the kernel's R decides).
 struct ParticleArgs {
     const void* f;            // post-collision populations buffer (storage type)
     const Inst* insts;
-    const DParticle* pin;     // bodies at the start of the step
-    DParticle* pout;          // bodies after the rigid-body update
+    const void* pin;          // DParticleT<R>: bodies at the start of the step
+    void* pout;               // DParticleT<R>: bodies after the rigid-body update
     const int4* blk;          // per marker block: (particle, first marker, markers, 0)
-    double* partial;          // per marker block: F_x, F_y, M partial sums
+    void* partial;            // R per marker block: F_x, F_y, M partial sums
     unsigned* count;          // per particle: probe blocks done (the last one resets it)
-    const double2* rb;        // body-frame marker positions
-    const double2* nb;        // body-frame normals
-    const double* S;          // marker arc lengths
+    const void* rb;           // Vec2<R>: body-frame marker positions
+    const void* nb;           // Vec2<R>: body-frame normals
+    const void* S;            // R: marker arc lengths
     void* recs;               // Rec<C>[max_markers]
     int4* boxes;              // per particle: support box (x0, y0, x1, y1)
     unsigned* err;
@@ -83,7 +103,7 @@ struct ParticleArgs {
 
 struct SpreadArgs {
     const Inst* insts;
-    const DParticle* parts;   // either state buffer (marker ranges, instance)
+    const void* parts;        // either state buffer (marker ranges, instance)
     const void* recs;
     const int4* boxes;
     void* flb;                // force buffer (2 planes of compute type per instance)
@@ -116,6 +136,7 @@ struct FieldArgs {
     Inst I;
     int y0, rows;
     double *rho, *ux, *uy;    // [rows][nx]
+    double* tan;              // tangent mode, optional: [3][KT][rows][nx] (rho, ux, uy)
 };
 
 // kernel launchers (fluid.cu / particles.cu); prec is an lbm_precision
@@ -132,12 +153,21 @@ cudaError_t launch_spread(int prec, const SpreadArgs& a, int np, int tiles, cuda
 size_t storage_bytes(int prec);
 size_t compute_bytes(int prec);
 size_t rec_bytes(int prec);
+size_t real_bytes(int prec);      // the particle real type R
+size_t particle_bytes(int prec);  // sizeof(DParticleT<R>)
 
-// shapes.cpp: body-frame markers and rigid-body properties of a shape
-struct ShapeOut {
-    double area, inertia_per_mass, rcirc;
+// shapes.cpp: body-frame markers and rigid-body properties of a shape, in
+// double or, with derivatives of the dimensions, in TD
+template <class T>
+struct ShapeOutT {
+    T area, inertia_per_mass;
+    double rcirc;
     int n;
 };
+using ShapeOut = ShapeOutT<double>;
+template <class T>
+int make_shape_t(const lbm_particle_desc& d, const T dim[2], double spacing, T* rb, T* nb, T* S,
+                 int cap, ShapeOutT<T>* out);
 int make_shape(const lbm_particle_desc& d, double spacing, double* rb, double* nb, double* S,
                int cap, ShapeOut* out);
 

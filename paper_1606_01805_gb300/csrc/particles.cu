@@ -18,6 +18,11 @@
 //   then adds the particle's sum into f_lb (the only atomic: one add per
 //   cell and particle, contended only where particles overlap) and flags the
 //   32-cell row segments the fluid kernel must read.
+// Each kernel is a template on the population storage type S, the compute
+// type C and the particle real type R: (double, double, double) in FP64,
+// (float or half, float, double) in FP32 / FP16, and in the tangent mode
+// (TF, TF, TD), where every value carries its derivatives along K input
+// directions and the same code propagates them.
 #include <climits>
 
 #include "lbib_device.cuh"
@@ -30,11 +35,6 @@ constexpr int TX = 32, TY = 16;  // spreading tile (cells); one thread per cell
 constexpr double CS2 = 1.0 / 3.0;
 constexpr double PROBE = 1.2;
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
 __device__ __forceinline__ int warp_min(int v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_down_sync(0xffffffffu, v, o));
@@ -44,6 +44,16 @@ __device__ __forceinline__ int warp_max(int v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
     return v;
+}
+
+// load through L2 of a value another block of the running kernel wrote
+__device__ __forceinline__ double ldcg_r(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ TD ldcg_r(const TD* p) {
+    TD r;
+    r.v = __ldcg(&p->v);
+#pragma unroll
+    for (int k = 0; k < KT; ++k) r.d[k] = __ldcg(&p->d[k]);
+    return r;
 }
 
 constexpr int LPM = 4;  // lanes per marker: lane q gathers support nodes q, q + 4, q + 8
@@ -59,27 +69,28 @@ __device__ __forceinline__ T quad_sum(T v) {  // sum over the 4 lanes of a marke
 // holds support nodes k = q, q + 4, q + 8 (k < 9) of the 3x3 block around
 // the nearest node of (px, py).  Weights and the moment matrix
 // A = sum W p p^T in precision C (reduced across the lanes); A is inverted
-// (adjugate) in FP64.  On return the lane has, for its nodes, W (in w[]), the offsets,
-// and the first (phi) and, if D, second/third rows of A^-1 [W p].
-template <bool D, class C>
+// (adjugate) in the particle type R.  On return the lane has, for its
+// nodes, the first (phi) and, if D, second/third rows of A^-1 [W p].
+template <bool D, class C, class R>
 struct QuadMLS {
     int i0, j0;      // lower-left node of the support
     int nk;          // nodes held by this lane (3 or 2)
     int kk[3];
     C phi[3], dpx[3], dpy[3];
 
-    // support of (px, py) and the nodes of lane q
-    __device__ __forceinline__ void support(double px, double py, int q) {
-        i0 = (int)floor(px + 0.5) - 1;
-        j0 = (int)floor(py + 0.5) - 1;
+    // support of (px, py) and the nodes of lane q; the choice of support is
+    // piecewise constant in the position and carries no derivative
+    __device__ __forceinline__ void support(const R& px, const R& py, int q) {
+        i0 = (int)floor_value(px + 0.5) - 1;
+        j0 = (int)floor_value(py + 0.5) - 1;
         nk = q == 0 ? 3 : 2;
 #pragma unroll
         for (int j = 0; j < 3; ++j) kk[j] = q + 4 * j;
     }
 
-    // weights and moment matrix in precision C, the 3x3 solve in FP64
+    // weights and moment matrix in precision C, the 3x3 solve in R
     // (after support())
-    __device__ __forceinline__ void build(int kind, double px, double py, int q, bool active) {
+    __device__ __forceinline__ void build(int kind, const R& px, const R& py, bool active) {
         C W[3], DX[3], DY[3];
         C b00 = C(0), b01 = C(0), b02 = C(0), b11 = C(0), b12 = C(0), b22 = C(0);
 #pragma unroll
@@ -89,7 +100,7 @@ struct QuadMLS {
             DX[j] = C(0);
             DY[j] = C(0);
             if (j < nk && active) {
-                const C dxw = (C)((double)(i0 + k % 3) - px), dyw = (C)((double)(j0 + k / 3) - py);
+                const C dxw = (C)(R((double)(i0 + k % 3)) - px), dyw = (C)(R((double)(j0 + k / 3)) - py);
                 W[j] = mls_weight<C>(kind, sqrt(dxw * dxw + dyw * dyw) * C(1.0 / 2.6));
                 DX[j] = dxw;
                 DY[j] = dyw;
@@ -102,11 +113,11 @@ struct QuadMLS {
                 b22 += wy * dyw;
             }
         }
-        double a00 = (double)quad_sum(b00), a01 = (double)quad_sum(b01), a02 = (double)quad_sum(b02);
-        double a11 = (double)quad_sum(b11), a12 = (double)quad_sum(b12), a22 = (double)quad_sum(b22);
-        if (!active) a00 = a11 = a22 = 1.0;  // keep idle lanes finite
-        const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
-        const double id = 1.0 / (a00 * c00 + a01 * c01 + a02 * c02);
+        R a00 = (R)quad_sum(b00), a01 = (R)quad_sum(b01), a02 = (R)quad_sum(b02);
+        R a11 = (R)quad_sum(b11), a12 = (R)quad_sum(b12), a22 = (R)quad_sum(b22);
+        if (!active) a00 = a11 = a22 = R(1.0);  // keep idle lanes finite
+        const R c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+        const R id = R(1.0) / (a00 * c00 + a01 * c01 + a02 * c02);
         const C i00 = (C)(c00 * id), i01 = (C)(c01 * id), i02 = (C)(c02 * id);
         C i11 = C(0), i12 = C(0), i22 = C(0);
         if (D) {
@@ -127,16 +138,18 @@ struct QuadMLS {
 
 // Sum of the block force/torque sums of particle P and its rigid-body update
 // (Eqs. 15-16), computed identically by every lane.
+template <class R>
 struct Body {
-    double X, Y, T, U, V, W, c, s, F0, F1, M;
+    R X, Y, T, U, V, W, c, s, F0, F1, M;
 };
-__device__ __forceinline__ Body update_body(const DParticle* P, const double* partial,
-                                            const double gravity[2], int lane) {
-    double F0 = 0, F1 = 0, Mt = 0;
+template <class R>
+__device__ __forceinline__ Body<R> update_body(const DParticleT<R>* P, const R* partial,
+                                               const double gravity[2], int lane) {
+    R F0 = R(0.0), F1 = R(0.0), Mt = R(0.0);
     for (int b = P->b0 + lane; b < P->b0 + P->nblk; b += 32) {  // L2: other blocks wrote them
-        F0 += __ldcg(partial + 3 * (long long)b);
-        F1 += __ldcg(partial + 3 * (long long)b + 1);
-        Mt += __ldcg(partial + 3 * (long long)b + 2);
+        F0 += ldcg_r(partial + 3 * (long long)b);
+        F1 += ldcg_r(partial + 3 * (long long)b + 1);
+        Mt += ldcg_r(partial + 3 * (long long)b + 2);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {  // butterfly: every lane ends with the total
@@ -144,13 +157,13 @@ __device__ __forceinline__ Body update_body(const DParticle* P, const double* pa
         F1 += __shfl_xor_sync(0xffffffffu, F1, o);
         Mt += __shfl_xor_sync(0xffffffffu, Mt, o);
     }
-    const double X0 = P->X[0][0], Y0 = P->X[0][1], th0 = P->th[0];
-    const double U0 = P->U[0][0], V0 = P->U[0][1], W0 = P->W[0];
-    const double buoy = (P->rho_s - 1.0) * P->area;
-    const double ax = (F0 + buoy * gravity[0]) * P->inv_mass;
-    const double ay = (F1 + buoy * gravity[1]) * P->inv_mass;
-    const double al = Mt * P->inv_inertia;
-    Body B;
+    const R X0 = P->X[0][0], Y0 = P->X[0][1], th0 = P->th[0];
+    const R U0 = P->U[0][0], V0 = P->U[0][1], W0 = P->W[0];
+    const R buoy = (P->rho_s - 1.0) * P->area;
+    const R ax = (F0 + buoy * gravity[0]) * P->inv_mass;
+    const R ay = (F1 + buoy * gravity[1]) * P->inv_mass;
+    const R al = Mt * P->inv_inertia;
+    Body<R> B;
     if (P->nupd == 0) {  // one stored level: u1 = u0 + a, x1 = x0 + u1
         B.U = U0 + ax;
         B.V = V0 + ay;
@@ -174,13 +187,14 @@ __device__ __forceinline__ Body update_body(const DParticle* P, const double* pa
     return B;
 }
 
-template <class S, class C>
+template <class S, class C, class R>
 __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     const int4 bk = a.blk[blockIdx.x];
-    const DParticle* P = a.pin + bk.x;
+    const DParticleT<R>* P = static_cast<const DParticleT<R>*>(a.pin) + bk.x;
     const Inst& I = a.insts[P->inst];
     const Geo& G = I.G;
     const S* __restrict__ f = static_cast<const S*>(a.f) + I.f_off;
+    R* partial = static_cast<R*>(a.partial);
     const int lane = threadIdx.x, q = lane & (LPM - 1);
     const int ml = lane / LPM, m = bk.y + ml;  // marker (absolute index)
     const bool active = ml < bk.z;
@@ -188,16 +202,16 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     if (lane == 0 && bk.y == P->m0)  // the particle's first block resets its box
         a.boxes[bk.x] = make_int4(INT_MAX, INT_MAX, INT_MIN, INT_MIN);
     // body at its latest level
-    const double c0 = P->cs[0][0], s0 = P->cs[0][1];
-    double2 rb = make_double2(0, 0), nb = make_double2(1, 0);
+    const R c0 = P->cs[0][0], s0 = P->cs[0][1];
+    Vec2<R> rb{R(0.0), R(0.0)}, nb{R(1.0), R(0.0)};
     if (active) {
-        rb = a.rb[m];
-        nb = a.nb[m];
+        rb = static_cast<const Vec2<R>*>(a.rb)[m];
+        nb = static_cast<const Vec2<R>*>(a.nb)[m];
     }
-    const double rx = c0 * rb.x - s0 * rb.y, ry = s0 * rb.x + c0 * rb.y;  // x_l - X_c
-    const double nx = c0 * nb.x - s0 * nb.y, ny = s0 * nb.x + c0 * nb.y;
-    const double px = P->X[0][0] + rx + PROBE * nx, py = P->X[0][1] + ry + PROBE * ny;
-    QuadMLS<true, C> M;
+    const R rx = c0 * rb.x - s0 * rb.y, ry = s0 * rb.x + c0 * rb.y;  // x_l - X_c
+    const R nx = c0 * nb.x - s0 * nb.y, ny = s0 * nb.x + c0 * nb.y;
+    const R px = P->X[0][0] + rx + PROBE * nx, py = P->X[0][1] + ry + PROBE * ny;
+    QuadMLS<true, C, R> M;
     M.support(px, py, q);
     // node fields first (their loads overlap the FP64 work of the solve)
     C rk[3], uk[3], vk[3];
@@ -212,7 +226,7 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
             }
         }
     }
-    M.build(a.weight, px, py, q, active);
+    M.build(a.weight, px, py, active);
     // MLS fit of rho and grad u at the probe (Section 2.3)
     C r = C(0), uxx = C(0), uxy = C(0), uyx = C(0), uyy = C(0);
 #pragma unroll
@@ -226,20 +240,20 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
         }
     }
     r = quad_sum(r); uxx = quad_sum(uxx); uxy = quad_sum(uxy); uyx = quad_sum(uyx); uyy = quad_sum(uyy);
-    double Fx = 0, Fy = 0, Mz = 0;
+    R Fx = R(0.0), Fy = R(0.0), Mz = R(0.0);
     if (active && q == 0) {
         // change of the marker's rigid velocity between the two stored levels
-        const double c1 = P->cs[1][0], s1 = P->cs[1][1];
-        const double r1x = c1 * rb.x - s1 * rb.y, r1y = s1 * rb.x + c1 * rb.y;
+        const R c1 = P->cs[1][0], s1 = P->cs[1][1];
+        const R r1x = c1 * rb.x - s1 * rb.y, r1y = s1 * rb.x + c1 * rb.y;
         const C dvx = (C)((P->U[0][0] - P->W[0] * ry) - (P->U[1][0] - P->W[1] * r1y));
         const C dvy = (C)((P->U[0][1] + P->W[0] * rx) - (P->U[1][1] + P->W[1] * r1x));
         const C cnx = (C)nx, cny = (C)ny;
         const C p = C(CS2) * (r - C(1)) + r * C(PROBE) * (dvx * cnx + dvy * cny);
-        const C mu = r * (C)(CS2 * (G.tau - 0.5));
+        const C mu = r * C(CS2 * (G.tau - 0.5));
         const C txx = C(2) * mu * uxx, tyy = C(2) * mu * uyy, txy = mu * (uxy + uyx);
-        const double tx = (double)(txx * cnx + txy * cny - p * cnx);
-        const double ty = (double)(txy * cnx + tyy * cny - p * cny);
-        const double Sl = a.S[m];
+        const R tx = (R)(txx * cnx + txy * cny - p * cnx);
+        const R ty = (R)(txy * cnx + tyy * cny - p * cny);
+        const R Sl = static_cast<const R*>(a.S)[m];
         Fx = tx * Sl;
         Fy = ty * Sl;
         Mz = (rx * ty - ry * tx) * Sl;
@@ -254,7 +268,7 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     if (err) atomicOr(a.err, err);
     unsigned done = 0;
     if (lane == 0) {
-        double* part = a.partial + 3 * (long long)blockIdx.x;
+        R* part = partial + 3 * (long long)blockIdx.x;
         part[0] = Fx;
         part[1] = Fy;
         part[2] = Mz;
@@ -264,9 +278,9 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     done = __shfl_sync(0xffffffffu, done, 0);
     if (done != (unsigned)P->nblk - 1) return;  // not the last block (whole warp)
     __threadfence();
-    const Body B = update_body(P, a.partial, G.grav, lane);
+    const Body<R> B = update_body<R>(P, partial, G.grav, lane);
     if (lane == 0) {
-        DParticle* Q = a.pout + bk.x;
+        DParticleT<R>* Q = static_cast<DParticleT<R>*>(a.pout) + bk.x;
         *Q = *P;
         Q->X[1][0] = P->X[0][0]; Q->X[1][1] = P->X[0][1]; Q->th[1] = P->th[0];
         Q->U[1][0] = P->U[0][0]; Q->U[1][1] = P->U[0][1]; Q->W[1] = P->W[0];
@@ -275,6 +289,7 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
         Q->U[0][0] = B.U; Q->U[0][1] = B.V; Q->W[0] = B.W;
         Q->cs[0][0] = B.c; Q->cs[0][1] = B.s;
         Q->F[0] = B.F0; Q->F[1] = B.F1; Q->M = B.M;
+        Q->wsum = P->wsum + B.W;
         Q->nupd = P->nupd + 1;
         if (!isfinite(B.X) || !isfinite(B.Y) || !isfinite(B.T) || !isfinite(B.U) || !isfinite(B.W))
             atomicOr(a.err, ERR_NONFINITE);
@@ -282,11 +297,11 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     }
 }
 
-template <class S, class C>
+template <class S, class C, class R>
 __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
     const int4 bk = a.blk[blockIdx.x];
-    const DParticle* P = a.pin + bk.x;
-    const Inst& I = a.insts[P->inst];
+    const DParticleT<R>* Q = static_cast<const DParticleT<R>*>(a.pout) + bk.x;  // after the update
+    const Inst& I = a.insts[Q->inst];
     const Geo& G = I.G;
     const S* __restrict__ f = static_cast<const S*>(a.f) + I.f_off;
     Rec<C>* recs = static_cast<Rec<C>*>(a.recs);
@@ -294,13 +309,14 @@ __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
     const int ml = lane / LPM, m = bk.y + ml;  // marker (absolute index)
     const bool active = ml < bk.z;
     unsigned err = 0;
-    const double2 rb = active ? a.rb[m] : make_double2(0, 0);
-    const DParticle* Q = a.pout + bk.x;  // the body after this step's update
-    const double X = Q->X[0][0], Y = Q->X[0][1], cn = Q->cs[0][0], sn = Q->cs[0][1];
-    const double BU = Q->U[0][0], BV = Q->U[0][1], BW = Q->W[0];
-    const double rx = cn * rb.x - sn * rb.y, ry = sn * rb.x + cn * rb.y;
-    QuadMLS<false, C> M;
-    M.support(X + rx, Y + ry, q);
+    Vec2<R> rb{R(0.0), R(0.0)};
+    if (active) rb = static_cast<const Vec2<R>*>(a.rb)[m];
+    const R X = Q->X[0][0], Y = Q->X[0][1], cn = Q->cs[0][0], sn = Q->cs[0][1];
+    const R BU = Q->U[0][0], BV = Q->U[0][1], BW = Q->W[0];
+    const R rx = cn * rb.x - sn * rb.y, ry = sn * rb.x + cn * rb.y;
+    const R mx = X + rx, my = Y + ry;
+    QuadMLS<false, C, R> M;
+    M.support(mx, my, q);
     C uk[3], vk[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -314,7 +330,7 @@ __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
             }
         }
     }
-    M.build(a.weight, X + rx, Y + ry, q, active);
+    M.build(a.weight, mx, my, active);
     C ux = C(0), uy = C(0);
 #pragma unroll
     for (int j = 0; j < 3; ++j)
@@ -327,9 +343,9 @@ __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
     int bx0 = INT_MAX, by0 = INT_MAX, bx1 = INT_MIN, by1 = INT_MIN;
     if (active) {
         // Eq. 11 with dt = 1, times the arc length c_l = S_l of Eq. 12
-        const double Sl = a.S[m];
-        const C sx = (C)(Sl * ((BU - BW * ry) - (double)ux));
-        const C sy = (C)(Sl * ((BV + BW * rx) - (double)uy));
+        const R Sl = static_cast<const R*>(a.S)[m];
+        const C sx = (C)(Sl * ((BU - BW * ry) - (R)ux));
+        const C sy = (C)(Sl * ((BV + BW * rx) - (R)uy));
         Rec<C>* rc = recs + m;
 #pragma unroll
         for (int j = 0; j < 3; ++j)
@@ -360,11 +376,18 @@ __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
     }
 }
 
+// records examined per round of k_spread: as many as fit a 48 KB static list
 template <class C>
+constexpr int spread_cap() {
+    int c = TX * TY;
+    while (c > 32 && sizeof(Rec<C>) * (size_t)c > 48 * 1024) c /= 2;
+    return c;
+}
+
+template <class C, class R>
 __global__ void __launch_bounds__(TX * TY) k_spread(SpreadArgs a) {
-    // records examined per round: as many as fit the static shared list
-    constexpr int CAP = sizeof(Rec<C>) * TX * TY <= 48 * 1024 ? TX * TY : TX * TY / 2;
-    const DParticle* P = a.parts + blockIdx.y;
+    constexpr int CAP = spread_cap<C>();
+    const DParticleT<R>* P = static_cast<const DParticleT<R>*>(a.parts) + blockIdx.y;
     const Inst& I = a.insts[P->inst];
     const Geo& G = I.G;
     const Rec<C>* recs = static_cast<const Rec<C>*>(a.recs);
@@ -430,29 +453,40 @@ __global__ void __launch_bounds__(TX * TY) k_spread(SpreadArgs a) {
 
 }  // namespace
 
-size_t rec_bytes(int prec) { return prec == LBM_FP64 ? sizeof(Rec<double>) : sizeof(Rec<float>); }
+size_t rec_bytes(int prec) {
+    if (prec == LBM_FP64) return sizeof(Rec<double>);
+    if (prec == LBM_FP32_TANGENT) return sizeof(Rec<TF>);
+    return sizeof(Rec<float>);
+}
+size_t real_bytes(int prec) { return prec == LBM_FP32_TANGENT ? sizeof(TD) : sizeof(double); }
+size_t particle_bytes(int prec) {
+    return prec == LBM_FP32_TANGENT ? sizeof(DParticleT<TD>) : sizeof(DParticleT<double>);
+}
 
 cudaError_t launch_probes(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
-    if (prec == LBM_FP64) k_probes<double, double><<<nblocks, 32, 0, s>>>(a);
-    else if (prec == LBM_FP32) k_probes<float, float><<<nblocks, 32, 0, s>>>(a);
-    else k_probes<__half, float><<<nblocks, 32, 0, s>>>(a);
+    if (prec == LBM_FP64) k_probes<double, double, double><<<nblocks, 32, 0, s>>>(a);
+    else if (prec == LBM_FP32) k_probes<float, float, double><<<nblocks, 32, 0, s>>>(a);
+    else if (prec == LBM_FP16_SHIFTED) k_probes<__half, float, double><<<nblocks, 32, 0, s>>>(a);
+    else k_probes<TF, TF, TD><<<nblocks, 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_markers(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
-    if (prec == LBM_FP64) k_markers<double, double><<<nblocks, 32, 0, s>>>(a);
-    else if (prec == LBM_FP32) k_markers<float, float><<<nblocks, 32, 0, s>>>(a);
-    else k_markers<__half, float><<<nblocks, 32, 0, s>>>(a);
+    if (prec == LBM_FP64) k_markers<double, double, double><<<nblocks, 32, 0, s>>>(a);
+    else if (prec == LBM_FP32) k_markers<float, float, double><<<nblocks, 32, 0, s>>>(a);
+    else if (prec == LBM_FP16_SHIFTED) k_markers<__half, float, double><<<nblocks, 32, 0, s>>>(a);
+    else k_markers<TF, TF, TD><<<nblocks, 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_spread(int prec, const SpreadArgs& a, int np, int tiles, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     const dim3 g(tiles, np);
-    if (prec == LBM_FP64) k_spread<double><<<g, TX * TY, 0, s>>>(a);
-    else k_spread<float><<<g, TX * TY, 0, s>>>(a);
+    if (prec == LBM_FP64) k_spread<double, double><<<g, TX * TY, 0, s>>>(a);
+    else if (prec == LBM_FP32_TANGENT) k_spread<TF, TD><<<g, TX * TY, 0, s>>>(a);
+    else k_spread<float, double><<<g, TX * TY, 0, s>>>(a);
     return cudaGetLastError();
 }
 

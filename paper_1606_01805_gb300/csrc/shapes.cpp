@@ -6,6 +6,7 @@
 // and carry the piece length S_l; the normal is the analytic outward normal
 // (circle, ellipse) or the face normal (polygons, each face cut into its own
 // equal pieces so that no marker straddles a corner).
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -41,16 +42,20 @@ struct GaussLegendre {
 };
 
 // arc length of (a cos t, b sin t) over [0, t]: composite 20-point Gauss-Legendre
-double ellipse_arc(double a, double b, double t) {
+template <class T>
+T ellipse_arc(const T& a, const T& b, const T& t) {
+    using std::cos;
+    using std::hypot;
+    using std::sin;
     static const GaussLegendre gl(20);
     const int panels = 64;
-    const double h = t / panels;
-    double acc = 0;
+    const T h = t / (double)panels;
+    T acc = T(0.0);
     for (int p = 0; p < panels; ++p) {
-        const double mid = (p + 0.5) * h;
+        const T mid = (p + 0.5) * h;
         for (size_t i = 0; i < gl.x.size(); ++i) {
-            const double s = mid + 0.5 * h * gl.x[i];
-            acc += gl.w[i] * std::hypot(a * std::sin(s), b * std::cos(s));
+            const T s = mid + (0.5 * gl.x[i]) * h;
+            acc += gl.w[i] * hypot(a * sin(s), b * cos(s));
         }
     }
     return 0.5 * h * acc;
@@ -58,79 +63,94 @@ double ellipse_arc(double a, double b, double t) {
 
 }  // namespace
 
-int make_shape(const lbm_particle_desc& d, double spacing, double* rb, double* nb, double* S,
-               int cap, ShapeOut* out) {
+// T = double, or TD: the dimensions then carry derivatives, and so do the
+// markers, normals, arc lengths, area and inertia (the marker count and the
+// split of the polygon faces follow the values only)
+template <class T>
+int make_shape_t(const lbm_particle_desc& d, const T dim[2], double spacing, T* rb, T* nb, T* S,
+                 int cap, ShapeOutT<T>* out) {
+    using std::cos;
+    using std::hypot;
+    using std::sin;
+    using std::sqrt;
     const double h0 = spacing > 0 ? spacing : 0.3;
-    const double D0 = d.dim[0], D1 = d.dim[1];
+    const T D0 = dim[0], D1 = dim[1];
     int n = 0;
     switch (d.shape) {
         case LBM_SHAPE_CIRCLE:
         case LBM_SHAPE_ELLIPSE: {
-            const double a = 0.5 * D0, b = d.shape == LBM_SHAPE_CIRCLE ? 0.5 * D0 : 0.5 * D1;
-            const double P = d.shape == LBM_SHAPE_CIRCLE ? M_PI * D0 : ellipse_arc(a, b, 2.0 * M_PI);
-            n = d.n_markers > 0 ? d.n_markers : (int)std::lround(P / h0);
+            const T a = 0.5 * D0, b = d.shape == LBM_SHAPE_CIRCLE ? 0.5 * D0 : 0.5 * D1;
+            const T P = d.shape == LBM_SHAPE_CIRCLE ? M_PI * D0 : ellipse_arc<T>(a, b, T(2.0 * M_PI));
+            n = d.n_markers > 0 ? d.n_markers : (int)std::lround(value_of(P) / h0);
             if (n < 8) n = 8;
             if (n > cap) return -1;
             for (int l = 0; l < n; ++l) {
-                double t = 2.0 * M_PI * (l + 0.5) / n;
+                T t = T(2.0 * M_PI * (l + 0.5) / n);
                 if (d.shape == LBM_SHAPE_ELLIPSE) {  // invert the arc length by Newton
-                    const double target = (l + 0.5) * P / n;
+                    const T target = ((l + 0.5) / n) * P;
                     for (int it = 0; it < 60; ++it) {
-                        const double g = ellipse_arc(a, b, t) - target;
-                        const double dt = g / std::hypot(a * std::sin(t), b * std::cos(t));
+                        const T g = ellipse_arc<T>(a, b, t) - target;
+                        const T dt = g / hypot(a * sin(t), b * cos(t));
                         t -= dt;
-                        if (std::fabs(dt) < 1e-15) break;
+                        // one more pass after the value has converged lets the
+                        // derivatives converge too (Newton on the dual part)
+                        if (std::fabs(value_of(dt)) < 1e-15) {
+                            const T g2 = ellipse_arc<T>(a, b, t) - target;
+                            t -= g2 / hypot(a * sin(t), b * cos(t));
+                            break;
+                        }
                     }
                 }
-                const double ct = std::cos(t), stt = std::sin(t);
-                const double mx = b * ct, my = a * stt, mn = std::hypot(mx, my);
+                const T ct = cos(t), stt = sin(t);
+                const T mx = b * ct, my = a * stt, mn = hypot(mx, my);
                 rb[2 * l] = a * ct;
                 rb[2 * l + 1] = b * stt;
                 nb[2 * l] = mx / mn;
                 nb[2 * l + 1] = my / mn;
-                S[l] = P / n;
+                S[l] = P / (double)n;
             }
             if (d.shape == LBM_SHAPE_CIRCLE) {
                 out->area = M_PI * a * a;
                 out->inertia_per_mass = 0.5 * a * a;
-                out->rcirc = a;
+                out->rcirc = value_of(a);
             } else {
                 out->area = M_PI * a * b;
                 out->inertia_per_mass = 0.25 * (a * a + b * b);
-                out->rcirc = a > b ? a : b;
+                out->rcirc = std::max(value_of(a), value_of(b));
             }
             break;
         }
         default: {
-            std::vector<double> vx, vy;
+            std::vector<T> vx, vy;
             if (d.shape == LBM_SHAPE_TRIANGLE) {
-                const double R = D0 / std::sqrt(3.0);
+                const T R = D0 / std::sqrt(3.0);
                 for (int j = 0; j < 3; ++j) {
                     const double ang = M_PI / 2 + 2.0 * M_PI * j / 3.0;
                     vx.push_back(R * std::cos(ang));
                     vy.push_back(R * std::sin(ang));
                 }
-                out->area = std::sqrt(3.0) / 4.0 * D0 * D0;
+                out->area = (std::sqrt(3.0) / 4.0) * D0 * D0;
                 out->inertia_per_mass = D0 * D0 / 12.0;
-                out->rcirc = R;
+                out->rcirc = value_of(R);
             } else {
-                const double w = D0, hh = d.shape == LBM_SHAPE_SQUARE ? D0 : D1;
-                const double px[4] = {-w / 2, w / 2, w / 2, -w / 2};
-                const double py[4] = {-hh / 2, -hh / 2, hh / 2, hh / 2};
+                const T w = D0, hh = d.shape == LBM_SHAPE_SQUARE ? D0 : D1;
+                const T px[4] = {-0.5 * w, 0.5 * w, 0.5 * w, -0.5 * w};
+                const T py[4] = {-0.5 * hh, -0.5 * hh, 0.5 * hh, 0.5 * hh};
                 vx.assign(px, px + 4);
                 vy.assign(py, py + 4);
                 out->area = w * hh;
                 out->inertia_per_mass = (w * w + hh * hh) / 12.0;
-                out->rcirc = 0.5 * std::hypot(w, hh);
+                out->rcirc = 0.5 * std::hypot(value_of(w), value_of(hh));
             }
             const int nv = (int)vx.size();
             double P = 0;
-            for (int j = 0; j < nv; ++j) P += std::hypot(vx[(j + 1) % nv] - vx[j], vy[(j + 1) % nv] - vy[j]);
+            for (int j = 0; j < nv; ++j)
+                P += std::hypot(value_of(vx[(j + 1) % nv] - vx[j]), value_of(vy[(j + 1) % nv] - vy[j]));
             const double h = d.n_markers > 0 ? P / d.n_markers : h0;
             for (int j = 0; j < nv; ++j) {
-                const double ex = vx[(j + 1) % nv] - vx[j], ey = vy[(j + 1) % nv] - vy[j];
-                const double L = std::hypot(ex, ey);
-                int cnt = (int)std::lround(L / h);
+                const T ex = vx[(j + 1) % nv] - vx[j], ey = vy[(j + 1) % nv] - vy[j];
+                const T L = hypot(ex, ey);
+                int cnt = (int)std::lround(value_of(L) / h);
                 if (cnt < 1) cnt = 1;
                 if (n + cnt > cap) return -1;
                 for (int m = 0; m < cnt; ++m, ++n) {
@@ -139,7 +159,7 @@ int make_shape(const lbm_particle_desc& d, double spacing, double* rb, double* n
                     rb[2 * n + 1] = vy[j] + s * ey;
                     nb[2 * n] = ey / L;  // vertices counter-clockwise: outward = (ey, -ex)/L
                     nb[2 * n + 1] = -ex / L;
-                    S[n] = L / cnt;
+                    S[n] = L / (double)cnt;
                 }
             }
             break;
@@ -147,6 +167,16 @@ int make_shape(const lbm_particle_desc& d, double spacing, double* rb, double* n
     }
     out->n = n;
     return n;
+}
+
+template int make_shape_t<double>(const lbm_particle_desc&, const double*, double, double*, double*,
+                                  double*, int, ShapeOutT<double>*);
+template int make_shape_t<TD>(const lbm_particle_desc&, const TD*, double, TD*, TD*, TD*, int,
+                              ShapeOutT<TD>*);
+
+int make_shape(const lbm_particle_desc& d, double spacing, double* rb, double* nb, double* S,
+               int cap, ShapeOut* out) {
+    return make_shape_t<double>(d, d.dim, spacing, rb, nb, S, cap, out);
 }
 
 }  // namespace lbib

@@ -21,7 +21,11 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_ENONFINITE, LBM_EIN
 STATUS_NAMES = ["LBM_OK", "LBM_EINVAL", "LBM_ENOMEM", "LBM_ECUDA", "LBM_ETIMEOUT",
                 "LBM_ENONFINITE", "LBM_EINTERNAL", "LBM_EDOMAIN"]
 LBM_BC_PERIODIC, LBM_BC_VELOCITY = 0, 1
-LBM_FP64, LBM_FP32, LBM_FP16_SHIFTED = 0, 1, 2
+LBM_FP64, LBM_FP32, LBM_FP16_SHIFTED, LBM_FP32_TANGENT = 0, 1, 2, 3
+LBM_TANGENTS = 3            # derivative directions of the tangent mode
+LBM_TANGENT_FIELDS = 10     # xc, yc, theta, u[0], u[1], omega, F[0], F[1], M, omega_sum
+TANGENT_FIELDS = ("xc", "yc", "theta", "ux", "uy", "omega", "Fx", "Fy", "M", "omega_sum")
+SEED_FIELDS = ("dim0", "dim1", "xc", "yc", "theta", "rho_s")
 LBM_INIT_REST, LBM_INIT_COUETTE, LBM_INIT_TAYLOR_GREEN = 0, 1, 2
 LBM_SHAPE_CIRCLE, LBM_SHAPE_ELLIPSE, LBM_SHAPE_RECT, LBM_SHAPE_SQUARE, LBM_SHAPE_TRIANGLE = range(5)
 LBM_W_EXP, LBM_W_CUBIC, LBM_W_QUARTIC, LBM_W_COSINE, LBM_W_POLY = range(5)
@@ -32,7 +36,9 @@ EXPORTS = ["lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "l
            "lbm_get_particles", "lbm_steps_done", "lbm_last_error", "lbm_destroy",
            "lbm_step_static", "lbm_batch_workspace_bytes", "lbm_init_batch", "lbm_instances",
            "lbm_add_particle_to", "lbm_get_instance_fields", "lbm_get_instance_populations",
-           "lbm_set_instance_populations", "lbm_get_tile", "lbm_set_tile"]
+           "lbm_set_instance_populations", "lbm_get_tile", "lbm_set_tile",
+           "lbm_set_wall_tangents", "lbm_add_particle_tangent", "lbm_get_particle_tangents",
+           "lbm_get_field_tangents"]
 LBM_STATIC_MAX_PARTICLES, LBM_STATIC_MAX_MARKERS = 1024, 16384
 
 
@@ -60,6 +66,7 @@ class lbm_particle_state(C.Structure):
     _fields_ = [
         ("xc", C.c_double), ("yc", C.c_double), ("theta", C.c_double), ("u", C.c_double * 2),
         ("omega", C.c_double), ("F", C.c_double * 2), ("M", C.c_double),
+        ("omega_sum", C.c_double),
     ]
 
 
@@ -111,12 +118,18 @@ def load(path: os.PathLike | str | None = None):
     L.lbm_set_instance_populations.argtypes = [C.c_void_p, C.c_int32, _dp]
     L.lbm_get_tile.argtypes = [C.c_void_p] + [C.POINTER(C.c_int32)] * 3
     L.lbm_set_tile.argtypes = [C.c_void_p, C.c_int32]
+    L.lbm_set_wall_tangents.argtypes = [C.c_void_p, C.c_int32, _dp]
+    L.lbm_add_particle_tangent.argtypes = [C.c_void_p, C.c_int32, C.POINTER(lbm_particle_desc), _dp,
+                                           C.POINTER(C.c_int32)]
+    L.lbm_get_particle_tangents.argtypes = [C.c_void_p, _dp, C.c_int32, C.POINTER(C.c_int32)]
+    L.lbm_get_field_tangents.argtypes = [C.c_void_p, C.c_int32, _dp, _dp, _dp]
     for fn in ("lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "lbm_step_timed",
                "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
                "lbm_get_particles", "lbm_step_static", "lbm_batch_workspace_bytes",
                "lbm_init_batch", "lbm_add_particle_to", "lbm_get_instance_fields",
                "lbm_get_instance_populations", "lbm_set_instance_populations", "lbm_get_tile",
-               "lbm_set_tile"):
+               "lbm_set_tile", "lbm_set_wall_tangents", "lbm_add_particle_tangent",
+               "lbm_get_particle_tangents", "lbm_get_field_tangents"):
         getattr(L, fn).restype = C.c_int
     _lib = L
     return L
@@ -185,18 +198,10 @@ class Simulation:
             pass
 
     def add_particle(self, shape, dim, xc, yc, theta=0.0, rho_s=1.0, u0=(0.0, 0.0), omega0=0.0,
-                     n_markers=0):
-        d = lbm_particle_desc()
-        d.shape = shape
-        d.dim[0] = dim[0]
-        d.dim[1] = dim[1] if len(dim) > 1 else 0.0
-        d.xc, d.yc, d.theta, d.rho_s = xc, yc, theta, rho_s
-        d.u0[0], d.u0[1] = u0
-        d.omega0, d.n_markers = omega0, n_markers
-        pid = C.c_int32()
-        self._check(load().lbm_add_particle(self._h, C.byref(d), C.byref(pid)), "lbm_add_particle")
-        self.np += 1
-        return pid.value
+                     n_markers=0, tangent=None):
+        """Add a particle; `tangent` (tangent mode only) is an array
+        [LBM_TANGENTS][6] of d(dim0, dim1, xc, yc, theta, rho_s)/dp_k."""
+        return _add(self, 0, shape, dim, xc, yc, theta, rho_s, u0, omega0, n_markers, tangent)
 
     def step(self, n=1):
         self._check(load().lbm_step(self._h, n), "lbm_step")
@@ -237,7 +242,33 @@ class Simulation:
         cnt = C.c_int32()
         self._check(load().lbm_get_particles(self._h, arr, n, C.byref(cnt)), "lbm_get_particles")
         return [dict(xc=p.xc, yc=p.yc, theta=p.theta, u=(p.u[0], p.u[1]), omega=p.omega,
-                     F=(p.F[0], p.F[1]), M=p.M) for p in arr[: cnt.value]]
+                     F=(p.F[0], p.F[1]), M=p.M, omega_sum=p.omega_sum) for p in arr[: cnt.value]]
+
+    def particle_tangents(self):
+        """Tangent mode: [particles][LBM_TANGENTS][LBM_TANGENT_FIELDS] array of
+        d(state)/dp_k, fields in TANGENT_FIELDS order."""
+        n = max(self.np, 1)
+        out = np.zeros((n, LBM_TANGENTS, LBM_TANGENT_FIELDS))
+        cnt = C.c_int32()
+        self._check(load().lbm_get_particle_tangents(self._h, _ptr(out), n, C.byref(cnt)),
+                    "lbm_get_particle_tangents")
+        return out[: cnt.value]
+
+    def set_wall_tangents(self, dwall, instance=0):
+        """Tangent mode: dwall[side][c][k] = d(wall_u[side][c])/dp_k."""
+        dw = np.ascontiguousarray(dwall, np.float64).reshape(4, 2, LBM_TANGENTS)
+        self._check(load().lbm_set_wall_tangents(self._h, instance, _ptr(dw)), "lbm_set_wall_tangents")
+
+    def field_tangents(self, instance=0):
+        """Tangent mode: d(rho, ux, uy)/dp_k as three [LBM_TANGENTS][ny][nx] arrays."""
+        ny, nx = self._shape(instance)
+        out = [np.empty((LBM_TANGENTS, ny, nx)) for _ in range(3)]
+        self._check(load().lbm_get_field_tangents(self._h, instance, *(_ptr(a) for a in out)),
+                    "lbm_get_field_tangents")
+        return tuple(out)
+
+    def _shape(self, instance):
+        return (self.ny, self.nx)
 
 
 class Batch:
@@ -293,20 +324,16 @@ class Batch:
     def __len__(self):
         return load().lbm_instances(self._h)
 
+    particle_tangents = Simulation.particle_tangents
+    set_wall_tangents = Simulation.set_wall_tangents
+    field_tangents = Simulation.field_tangents
+
+    def _shape(self, instance):
+        return self.shapes[instance]
+
     def add_particle(self, instance, shape, dim, xc, yc, theta=0.0, rho_s=1.0, u0=(0.0, 0.0),
-                     omega0=0.0, n_markers=0):
-        d = lbm_particle_desc()
-        d.shape = shape
-        d.dim[0] = dim[0]
-        d.dim[1] = dim[1] if len(dim) > 1 else 0.0
-        d.xc, d.yc, d.theta, d.rho_s = xc, yc, theta, rho_s
-        d.u0[0], d.u0[1] = u0
-        d.omega0, d.n_markers = omega0, n_markers
-        pid = C.c_int32()
-        self._check(load().lbm_add_particle_to(self._h, instance, C.byref(d), C.byref(pid)),
-                    "lbm_add_particle_to")
-        self.np += 1
-        return pid.value
+                     omega0=0.0, n_markers=0, tangent=None):
+        return _add(self, instance, shape, dim, xc, yc, theta, rho_s, u0, omega0, n_markers, tangent)
 
     def fields(self, instance):
         ny, nx = self.shapes[instance]
@@ -333,6 +360,26 @@ class Batch:
 
     tile = None  # set below
     set_tile = None
+
+
+def _add(obj, instance, shape, dim, xc, yc, theta, rho_s, u0, omega0, n_markers, tangent):
+    d = lbm_particle_desc()
+    d.shape = shape
+    d.dim[0] = dim[0]
+    d.dim[1] = dim[1] if len(dim) > 1 else 0.0
+    d.xc, d.yc, d.theta, d.rho_s = xc, yc, theta, rho_s
+    d.u0[0], d.u0[1] = u0
+    d.omega0, d.n_markers = omega0, n_markers
+    pid = C.c_int32()
+    L = load()
+    if tangent is not None:
+        seed = np.ascontiguousarray(tangent, np.float64).reshape(LBM_TANGENTS, len(SEED_FIELDS))
+        rc = L.lbm_add_particle_tangent(obj._h, instance, C.byref(d), _ptr(seed), C.byref(pid))
+    else:
+        rc = L.lbm_add_particle_to(obj._h, instance, C.byref(d), C.byref(pid))
+    obj._check(rc, "lbm_add_particle")
+    obj.np += 1
+    return pid.value
 
 
 def _tile(self):

@@ -30,6 +30,9 @@ Workloads (lattice units, dx = dt = 1, fluid reference density 1):
 * ``large_couette``: 16384 x 4096 antisymmetric Couette channel (cfg of the
   first workload scaled up) with 64 circles D = 20 on a seeded jittered
   grid: a lattice well beyond the 129 MB L2 for the bandwidth roofline.
+* ``sensitivity_ellipse`` / ``sensitivity_batch``: the first workload with
+  an ellipse of the circle's area, parameterised by aspect ratio, initial
+  height and wall speed; 64 seeded parameter triples (seed 4).
 """
 from __future__ import annotations
 
@@ -181,6 +184,35 @@ def batched_screening(n=512, seed=3, nx_range=(256, 1024), ny_range=(128, 256), 
                             particles=[Particle(shape, shape_for(shape, rc, ar), nx / 2, y0,
                                                 theta=th)]))
     return out
+
+
+SENS_MARKERS = 72  # fixed marker count of the sensitivity ellipses (spacing <= 1.05 up to AR 3)
+
+
+def sensitivity_ellipse(ar, y0, U, steps=2000, theta=0.0, nx=400, ny=100, tau=0.8):
+    """The plain method's channel (``couette_circle``) with the circle
+    replaced by an ellipse of aspect ratio `ar` and the area of the D = 20
+    circle (semi-axes 10 sqrt(ar) and 10 / sqrt(ar)), released at y0 with
+    angle theta; walls at -U and +U.  The three parameters (ar, y0, U) are
+    the inputs of the sensitivity study; the marker count is fixed."""
+    a, b = 10.0 * math.sqrt(ar), 10.0 / math.sqrt(ar)
+    return Workload(f"sens_ellipse_ar{ar:.4f}_{nx}x{ny}", nx, ny, tau,
+                    wall_u=((0, 0), (0, 0), (-U, 0.0), (U, 0.0)), init=COUETTE, steps=steps,
+                    particles=[Particle(ELLIPSE, (2 * a, 2 * b), nx / 2, y0, theta=theta,
+                                        n_markers=SENS_MARKERS)])
+
+
+def sensitivity_batch(n=64, seed=4, steps=2000):
+    """n seeded parameter triples (ar ~ U[1.5, 3], y0 ~ U[0.25 H, 0.4 H],
+    U ~ U0 * U[0.8, 1.2] with U0 the wall speed of Re = 20) and angles
+    ~ U[0, pi), as an [n][3] array and the angles."""
+    tau, H = 0.8, 99.0
+    U0 = 20.0 * (tau - 0.5) / 3.0 / H / 2.0
+    rng = np.random.default_rng(seed)
+    P = np.stack([rng.uniform(1.5, 3.0, n), rng.uniform(0.25 * H, 0.4 * H, n),
+                  U0 * rng.uniform(0.8, 1.2, n)], axis=1)
+    th = rng.uniform(0.0, math.pi, n)
+    return P, th
 
 
 def batch_config(wl: Workload):
