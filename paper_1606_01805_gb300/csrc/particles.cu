@@ -56,6 +56,10 @@ __device__ __forceinline__ TD ldcg_r(const TD* p) {
     return r;
 }
 
+// 1 / x, correctly rounded (with its derivatives for a dual)
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ TD recip(const TD& x) { return TD(1.0) / x; }
+
 constexpr int LPM = 4;  // lanes per marker: lane q gathers support nodes q, q + 4, q + 8
 
 template <class T>
@@ -93,6 +97,9 @@ struct QuadMLS {
     __device__ __forceinline__ void build(int kind, const R& px, const R& py, bool active) {
         C W[3], DX[3], DY[3];
         C b00 = C(0), b01 = C(0), b02 = C(0), b11 = C(0), b12 = C(0), b22 = C(0);
+        // offset from the support's lower-left node in R (one conversion),
+        // the steps to the other nodes added in C
+        const C ox = (C)(R((double)i0) - px), oy = (C)(R((double)j0) - py);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int k = kk[j];
@@ -100,7 +107,7 @@ struct QuadMLS {
             DX[j] = C(0);
             DY[j] = C(0);
             if (j < nk && active) {
-                const C dxw = (C)(R((double)(i0 + k % 3)) - px), dyw = (C)(R((double)(j0 + k / 3)) - py);
+                const C dxw = ox + C(k % 3), dyw = oy + C(k / 3);
                 W[j] = mls_weight<C>(kind, sqrt(dxw * dxw + dyw * dyw) * C(1.0 / 2.6));
                 DX[j] = dxw;
                 DY[j] = dyw;
@@ -117,7 +124,7 @@ struct QuadMLS {
         R a11 = (R)quad_sum(b11), a12 = (R)quad_sum(b12), a22 = (R)quad_sum(b22);
         if (!active) a00 = a11 = a22 = R(1.0);  // keep idle lanes finite
         const R c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
-        const R id = R(1.0) / (a00 * c00 + a01 * c01 + a02 * c02);
+        const R id = recip(a00 * c00 + a01 * c01 + a02 * c02);
         const C i00 = (C)(c00 * id), i01 = (C)(c01 * id), i02 = (C)(c02 * id);
         C i11 = C(0), i12 = C(0), i22 = C(0);
         if (D) {
@@ -425,12 +432,26 @@ __global__ void __launch_bounds__(TX * TY) k_spread(SpreadArgs a) {
         }
         if (rel) list[off + __popc(bal & ((1u << lane) - 1u))] = r;
         __syncthreads();
-        for (int m = 0; m < total; ++m) {
-            const int da = cxl - list[m].i0, db = cyl - list[m].j0;
-            if (da >= 0 && da < 3 && db >= 0 && db < 3) {
-                ax += list[m].cx[db * 3 + da];
-                ay += list[m].cy[db * 3 + da];
-                touched = true;
+        // warp wid holds tile row cyl: it picks, 32 at a time, the records
+        // whose support has that row (one ballot), then every lane adds
+        // those that cover its cell, in list (marker) order
+        for (int b0 = 0; b0 < total; b0 += 32) {
+            const int m = b0 + lane;
+            bool row = false;
+            if (m < total) {
+                const int db = cyl - list[m].j0;
+                row = db >= 0 && db < 3;
+            }
+            unsigned bits = __ballot_sync(0xffffffffu, row);
+            while (bits) {
+                const Rec<C>& rc = list[b0 + __ffs(bits) - 1];
+                bits &= bits - 1u;
+                const int da = cxl - rc.i0, db = cyl - rc.j0;
+                if (da >= 0 && da < 3) {
+                    ax += rc.cx[db * 3 + da];
+                    ay += rc.cy[db * 3 + da];
+                    touched = true;
+                }
             }
         }
         __syncthreads();
