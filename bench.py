@@ -34,11 +34,14 @@ FALLBACK_HBM_GBS = 6800.0
 BYTES_PER_CELL = {0: 144, 1: 72, 2: 36, 3: 288}
 PREC_NAMES = {0: "f64", 1: "f32", 2: "f16-storage/f32", 3: "f32+3 tangents"}
 
-# dram__bytes_read.sum + dram__bytes_write.sum per fluid-kernel launch from one
-# ncu capture, keyed by the hash of the kernel sources it was taken on
+# dram__bytes_read.sum + dram__bytes_write.sum per fluid-kernel launch (median
+# over the launches of one ncu capture of the bench command), keyed by the
+# hash of the kernel sources it was taken on, the workload, the precision
+# and the tile shape (profiles/k_fluid_sedimentation_400x1200.md)
 NCU_TRAFFIC = {
-    # k_fluid<float,float>, sedimentation 400 x 1200 (profiles/k_fluid_sedimentation_400x1200.md)
-    ("6cb43485324753bc", "sedimentation_circle_400x1200", 1): 18064640 + 14336,
+    ("026f9be10680c620", "sedimentation_circle_400x1200", 1, 0): 18220672 + 148480,
+    ("026f9be10680c620", "sedimentation_circle_400x1200", 1, 1): 18216960 + 147968,
+    ("026f9be10680c620", "sedimentation_circle_400x1200", 1, 2): 18037248 + 0,
 }
 
 
@@ -400,7 +403,7 @@ def main():
     peak, peak_kind = hbm_peak()
     algo_bytes = BYTES_PER_CELL[prec] * cells
     achieved = algo_bytes / (ms_fluid * 1e-3 / args.steps) / 1e9
-    traffic = NCU_TRAFFIC.get((kernel_hash(), wl.name, prec))
+    traffic = NCU_TRAFFIC.get((kernel_hash(), wl.name, prec, tile[0]))
     out = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step / args.steps, "higher_is_better": True,
