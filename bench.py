@@ -164,7 +164,9 @@ def time_device(wl, prec, steps, warmup, flush, pick_tile=False):
 
     if pick_tile:
         best = None
-        for v in range(3):
+        from paper_1606_01805_gb300 import lbib
+
+        for v in range(lbib.LBM_TILE_VARIANTS):
             sim.set_tile(v)
             for _ in range(3):
                 do_flush()

@@ -263,8 +263,11 @@ lbm_status lbm_set_instance_populations(lbm_ctx* ctx, int32_t instance, const do
  * shape on the context's own lattices and keep the fastest (all shapes give
  * bit-identical results); lbm_get_tile reports the choice (index, cells per
  * thread, rows per block) and lbm_set_tile forces shape `variant`
- * (0 .. 2; LBM_EINVAL otherwise).  The tangent mode has shape 2 only.
+ * (0 .. LBM_TILE_VARIANTS - 1; LBM_EINVAL otherwise).  The shapes: 4 cells
+ * per thread in blocks of 8 or 4 rows, and 1 cell per thread in blocks of
+ * 8 rows.  The tangent mode has shape 2 only.
  */
+#define LBM_TILE_VARIANTS 3
 lbm_status lbm_get_tile(const lbm_ctx* ctx, int32_t* variant, int32_t* cells_per_thread,
                         int32_t* rows_per_block);
 lbm_status lbm_set_tile(lbm_ctx* ctx, int32_t variant);

@@ -240,6 +240,8 @@ ParticleArgs particle_args(lbm_ctx* ctx, int cur) {
     pa.boxes = ctx->boxes;
     pa.err = ctx->err;
     pa.weight = ctx->cfg.weight;
+    pa.single = ctx->ninst == 1;
+    pa.one = ctx->hinst[0];
     return pa;
 }
 
@@ -252,6 +254,8 @@ SpreadArgs spread_args(lbm_ctx* ctx, const ParticleArgs& pa) {
     sa.flb = ctx->flb;
     sa.flags = ctx->flags;
     sa.err = ctx->err;
+    sa.single = ctx->ninst == 1;
+    sa.one = ctx->hinst[0];
     return sa;
 }
 
@@ -551,7 +555,7 @@ lbm_status add_particle_t(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, co
     if (P.b0 + P.nblk > cap_blocks(ctx->cfg)) return fail(ctx, LBM_EINVAL, "marker capacity exceeded");
     std::vector<int4> blocks(P.nblk);
     for (int k = 0; k < P.nblk; ++k)
-        blocks[k] = make_int4(ctx->np, P.m0 + k * MB, std::min(MB, n - k * MB), 0);
+        blocks[k] = make_int4(ctx->np, P.m0 + k * MB, std::min(MB, n - k * MB), inst);
     const size_t v2 = sizeof(Vec2<R>);
     static_assert(sizeof(Vec2<R>) == 2 * sizeof(R), "marker arrays are packed pairs");
     CK(cudaMemcpyAsync(static_cast<char*>(ctx->rb) + P.m0 * v2, rb.data(), n * v2, cudaMemcpyHostToDevice,

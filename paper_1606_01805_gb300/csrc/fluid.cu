@@ -302,7 +302,7 @@ __global__ void k_fields(FieldArgs a) {
     const int x = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * BY + threadIdx.y;
     if (x >= a.I.G.nx || r >= a.rows) return;
     C rho, ux, uy;
-    node_fields<S, C>(static_cast<const S*>(a.f) + a.I.f_off, a.I.G, x, a.y0 + r, rho, ux, uy);
+    node_fields<S, C>(static_cast<const S*>(a.f) + a.I.f_off, a.I.G, &a.I.G, x, a.y0 + r, rho, ux, uy);
     const long long k = (long long)r * a.I.G.nx + x;
     a.rho[k] = (double)value_of(rho);
     a.ux[k] = (double)value_of(ux);

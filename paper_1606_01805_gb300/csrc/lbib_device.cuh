@@ -223,10 +223,12 @@ __device__ __noinline__ bool node_fields_general(const S* __restrict__ f, const 
     return true;
 }
 
-// rho, u* at the unwrapped node (ix, iy); false if it lies across a wall
+// rho, u* at the unwrapped node (ix, iy); false if it lies across a wall.
+// Gg is the same geometry in global memory, for the out-of-line wrap / wall
+// path (G itself may live in the kernel's parameters).
 template <class S, class C>
-__device__ __forceinline__ bool node_fields(const S* __restrict__ f, const Geo& G, int ix, int iy,
-                                            C& rho, C& ux, C& uy) {
+__device__ __forceinline__ bool node_fields(const S* __restrict__ f, const Geo& G, const Geo* Gg, int ix,
+                                            int iy, C& rho, C& ux, C& uy) {
     if (ix > 0 && ix < G.nx - 1 && iy > 0 && iy < G.ny - 1) {
         C v[9];
         const long long c = (long long)iy * G.pitch + ix;
@@ -236,7 +238,7 @@ __device__ __forceinline__ bool node_fields(const S* __restrict__ f, const Geo& 
         fields_of<C>(v, G, rho, ux, uy);
         return true;
     }
-    return node_fields_general<S, C>(f, G, ix, iy, rho, ux, uy);
+    return node_fields_general<S, C>(f, *Gg, ix, iy, rho, ux, uy);
 }
 
 // --------------------------------------------------------------- MLS ----

@@ -89,7 +89,7 @@ struct ParticleArgs {
     const Inst* insts;
     const void* pin;          // DParticleT<R>: bodies at the start of the step
     void* pout;               // DParticleT<R>: bodies after the rigid-body update
-    const int4* blk;          // per marker block: (particle, first marker, markers, 0)
+    const int4* blk;          // per marker block: (particle, first marker, markers, instance)
     void* partial;            // R per marker block: F_x, F_y, M partial sums
     unsigned* count;          // per particle: probe blocks done (the last one resets it)
     const void* rb;           // Vec2<R>: body-frame marker positions
@@ -99,6 +99,8 @@ struct ParticleArgs {
     int4* boxes;              // per particle: support box (x0, y0, x1, y1)
     unsigned* err;
     int weight;
+    int single;               // the context holds one lattice: `one` is its descriptor
+    Inst one;
 };
 
 struct SpreadArgs {
@@ -109,10 +111,12 @@ struct SpreadArgs {
     void* flb;                // force buffer (2 planes of compute type per instance)
     uint8_t* flags;           // flags buffer ([ny][nseg] bytes per instance)
     unsigned* err;
+    int single;               // as in ParticleArgs
+    Inst one;
 };
 
 // Fluid step over a list of tiles: task t = (instance, tile x, tile y, 0),
-// a tile being 32 * CPT cells of BY rows.  One launch covers every tile of
+// a tile being 32 * cpt cells of by rows.  One launch covers every tile of
 // every instance; a CTA takes tasks blockIdx.x, blockIdx.x + gridDim.x, ...
 struct FluidArgs {
     const void* fin;
@@ -125,7 +129,7 @@ struct FluidArgs {
 };
 
 // fluid tile shapes: (cells per thread, rows per block); the autotuner picks one
-constexpr int N_FLUID_VARIANTS = 3;
+constexpr int N_FLUID_VARIANTS = LBM_TILE_VARIANTS;
 struct FluidVariant {
     int cpt, by;
 };

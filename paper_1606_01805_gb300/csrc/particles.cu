@@ -194,12 +194,21 @@ __device__ __forceinline__ Body<R> update_body(const DParticleT<R>* P, const R* 
     return B;
 }
 
-template <class S, class C, class R>
+// The lattice of a marker block or particle: for a context of one lattice
+// its descriptor travels in the kernel parameters (ONE), else it is loaded.
+template <bool ONE, class A>
+__device__ __forceinline__ const Inst& inst_of(const A& a, int w) {
+    if (ONE) return a.one;
+    return a.insts[w];
+}
+
+template <class S, class C, class R, bool ONE>
 __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     const int4 bk = a.blk[blockIdx.x];
     const DParticleT<R>* P = static_cast<const DParticleT<R>*>(a.pin) + bk.x;
-    const Inst& I = a.insts[P->inst];
+    const Inst& I = inst_of<ONE>(a, bk.w);
     const Geo& G = I.G;
+    const Geo* Gg = &a.insts[ONE ? 0 : bk.w].G;
     const S* __restrict__ f = static_cast<const S*>(a.f) + I.f_off;
     R* partial = static_cast<R*>(a.partial);
     const int lane = threadIdx.x, q = lane & (LPM - 1);
@@ -227,7 +236,7 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
         rk[j] = C(1); uk[j] = C(0); vk[j] = C(0);
         if (j < M.nk && active) {
             const int k = M.kk[j];
-            if (!node_fields<S, C>(f, G, M.i0 + k % 3, M.j0 + k / 3, rk[j], uk[j], vk[j])) {
+            if (!node_fields<S, C>(f, G, Gg, M.i0 + k % 3, M.j0 + k / 3, rk[j], uk[j], vk[j])) {
                 err |= ERR_DOMAIN;
                 rk[j] = C(1); uk[j] = C(0); vk[j] = C(0);
             }
@@ -304,12 +313,13 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     }
 }
 
-template <class S, class C, class R>
+template <class S, class C, class R, bool ONE>
 __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
     const int4 bk = a.blk[blockIdx.x];
     const DParticleT<R>* Q = static_cast<const DParticleT<R>*>(a.pout) + bk.x;  // after the update
-    const Inst& I = a.insts[Q->inst];
+    const Inst& I = inst_of<ONE>(a, bk.w);
     const Geo& G = I.G;
+    const Geo* Gg = &a.insts[ONE ? 0 : bk.w].G;
     const S* __restrict__ f = static_cast<const S*>(a.f) + I.f_off;
     Rec<C>* recs = static_cast<Rec<C>*>(a.recs);
     const int lane = threadIdx.x, q = lane & (LPM - 1);
@@ -331,7 +341,7 @@ __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
         if (j < M.nk && active) {
             const int k = M.kk[j];
             C rk;
-            if (!node_fields<S, C>(f, G, M.i0 + k % 3, M.j0 + k / 3, rk, uk[j], vk[j])) {
+            if (!node_fields<S, C>(f, G, Gg, M.i0 + k % 3, M.j0 + k / 3, rk, uk[j], vk[j])) {
                 err |= ERR_DOMAIN;
                 uk[j] = C(0); vk[j] = C(0);
             }
@@ -391,11 +401,11 @@ constexpr int spread_cap() {
     return c;
 }
 
-template <class C, class R>
+template <class C, class R, bool ONE>
 __global__ void __launch_bounds__(TX * TY) k_spread(SpreadArgs a) {
     constexpr int CAP = spread_cap<C>();
     const DParticleT<R>* P = static_cast<const DParticleT<R>*>(a.parts) + blockIdx.y;
-    const Inst& I = a.insts[P->inst];
+    const Inst& I = inst_of<ONE>(a, ONE ? 0 : P->inst);
     const Geo& G = I.G;
     const Rec<C>* recs = static_cast<const Rec<C>*>(a.recs);
     C* flb = static_cast<C*>(a.flb) + I.flb_off;
@@ -484,30 +494,48 @@ size_t particle_bytes(int prec) {
     return prec == LBM_FP32_TANGENT ? sizeof(DParticleT<TD>) : sizeof(DParticleT<double>);
 }
 
+template <bool ONE>
+void probes_t(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s) {
+    if (prec == LBM_FP64) k_probes<double, double, double, ONE><<<nblocks, 32, 0, s>>>(a);
+    else if (prec == LBM_FP32) k_probes<float, float, double, ONE><<<nblocks, 32, 0, s>>>(a);
+    else if (prec == LBM_FP16_SHIFTED) k_probes<__half, float, double, ONE><<<nblocks, 32, 0, s>>>(a);
+    else k_probes<TF, TF, TD, ONE><<<nblocks, 32, 0, s>>>(a);
+}
+
+template <bool ONE>
+void markers_t(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s) {
+    if (prec == LBM_FP64) k_markers<double, double, double, ONE><<<nblocks, 32, 0, s>>>(a);
+    else if (prec == LBM_FP32) k_markers<float, float, double, ONE><<<nblocks, 32, 0, s>>>(a);
+    else if (prec == LBM_FP16_SHIFTED) k_markers<__half, float, double, ONE><<<nblocks, 32, 0, s>>>(a);
+    else k_markers<TF, TF, TD, ONE><<<nblocks, 32, 0, s>>>(a);
+}
+
+template <bool ONE>
+void spread_t(int prec, const SpreadArgs& a, dim3 g, cudaStream_t s) {
+    if (prec == LBM_FP64) k_spread<double, double, ONE><<<g, TX * TY, 0, s>>>(a);
+    else if (prec == LBM_FP32_TANGENT) k_spread<TF, TD, ONE><<<g, TX * TY, 0, s>>>(a);
+    else k_spread<float, double, ONE><<<g, TX * TY, 0, s>>>(a);
+}
+
 cudaError_t launch_probes(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
-    if (prec == LBM_FP64) k_probes<double, double, double><<<nblocks, 32, 0, s>>>(a);
-    else if (prec == LBM_FP32) k_probes<float, float, double><<<nblocks, 32, 0, s>>>(a);
-    else if (prec == LBM_FP16_SHIFTED) k_probes<__half, float, double><<<nblocks, 32, 0, s>>>(a);
-    else k_probes<TF, TF, TD><<<nblocks, 32, 0, s>>>(a);
+    if (a.single) probes_t<true>(prec, a, nblocks, s);
+    else probes_t<false>(prec, a, nblocks, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_markers(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
-    if (prec == LBM_FP64) k_markers<double, double, double><<<nblocks, 32, 0, s>>>(a);
-    else if (prec == LBM_FP32) k_markers<float, float, double><<<nblocks, 32, 0, s>>>(a);
-    else if (prec == LBM_FP16_SHIFTED) k_markers<__half, float, double><<<nblocks, 32, 0, s>>>(a);
-    else k_markers<TF, TF, TD><<<nblocks, 32, 0, s>>>(a);
+    if (a.single) markers_t<true>(prec, a, nblocks, s);
+    else markers_t<false>(prec, a, nblocks, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_spread(int prec, const SpreadArgs& a, int np, int tiles, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     const dim3 g(tiles, np);
-    if (prec == LBM_FP64) k_spread<double, double><<<g, TX * TY, 0, s>>>(a);
-    else if (prec == LBM_FP32_TANGENT) k_spread<TF, TD><<<g, TX * TY, 0, s>>>(a);
-    else k_spread<float, double><<<g, TX * TY, 0, s>>>(a);
+    if (a.single) spread_t<true>(prec, a, g, s);
+    else spread_t<false>(prec, a, g, s);
     return cudaGetLastError();
 }
 

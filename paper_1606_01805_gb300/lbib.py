@@ -23,6 +23,7 @@ STATUS_NAMES = ["LBM_OK", "LBM_EINVAL", "LBM_ENOMEM", "LBM_ECUDA", "LBM_ETIMEOUT
 LBM_BC_PERIODIC, LBM_BC_VELOCITY = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16_SHIFTED, LBM_FP32_TANGENT = 0, 1, 2, 3
 LBM_TANGENTS = 3            # derivative directions of the tangent mode
+LBM_TILE_VARIANTS = 3       # fluid tile shapes (lbm_get_tile / lbm_set_tile)
 LBM_TANGENT_FIELDS = 10     # xc, yc, theta, u[0], u[1], omega, F[0], F[1], M, omega_sum
 TANGENT_FIELDS = ("xc", "yc", "theta", "ux", "uy", "omega", "Fx", "Fy", "M", "omega_sum")
 SEED_FIELDS = ("dim0", "dim1", "xc", "yc", "theta", "rho_s")

@@ -67,7 +67,7 @@ def test_batch_instances_match_oracle_fp32():
 def test_every_tile_shape_gives_the_same_bits(prec):
     wls = small_batch(n=3, seed=5)
     results = []
-    for v in range(3):
+    for v in range(lbib.LBM_TILE_VARIANTS):
         b = make_batch(wls, prec)
         b.set_tile(v)
         assert b.tile()[0] == v
@@ -82,9 +82,9 @@ def test_every_tile_shape_gives_the_same_bits(prec):
 def test_autotuner_reports_a_valid_shape():
     b = make_batch(small_batch(n=2), FP32)
     v, cpt, by = b.tile()
-    assert 0 <= v < 3 and cpt in (1, 4) and by in (4, 8)
+    assert 0 <= v < lbib.LBM_TILE_VARIANTS and cpt in (1, 4) and by in (4, 8)
     with pytest.raises(lbib.LbmError):
-        b.set_tile(3)
+        b.set_tile(lbib.LBM_TILE_VARIANTS)
 
 
 def test_full_screening_batch_runs():
