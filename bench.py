@@ -39,9 +39,9 @@ PREC_NAMES = {0: "f64", 1: "f32", 2: "f16-storage/f32", 3: "f32+3 tangents"}
 # hash of the kernel sources it was taken on, the workload, the precision
 # and the tile shape (profiles/k_fluid_sedimentation_400x1200.md)
 NCU_TRAFFIC = {
-    ("026f9be10680c620", "sedimentation_circle_400x1200", 1, 0): 18220672 + 148480,
-    ("026f9be10680c620", "sedimentation_circle_400x1200", 1, 1): 18216960 + 147968,
-    ("026f9be10680c620", "sedimentation_circle_400x1200", 1, 2): 18037248 + 0,
+    ("5c7edde56c8ec884", "sedimentation_circle_400x1200", 1, 0): 18221568 + 150400,
+    ("5c7edde56c8ec884", "sedimentation_circle_400x1200", 1, 1): 18216704 + 147200,
+    ("5c7edde56c8ec884", "sedimentation_circle_400x1200", 1, 2): 18037504 + 0,
 }
 
 
@@ -412,7 +412,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAMES[prec], "data": "synthetic",
         "config": {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "tau": wl.tau,
                    "particles": len(wl.particles), "precision": args.precision +
-                   " populations, fp64 particle work", "l2": "flushed before every timed step",
+                   " populations, fp64 particle work",
+                   "l2": "flushed before every timed step" if flush else "inputs larger than L2",
                    "parallelism": "replicas" if ws > 1 else "single",
                    "fluid_tile": {"variant": tile[0], "cells_per_thread": tile[1], "rows_per_block": tile[2],
                                   "chosen_by": "bench.py, each shape timed over 20 L2-flushed steps"
