@@ -49,6 +49,8 @@ struct lbm_ctx {
     double* scratch;
     int scratch_rows;
     int np = 0, nmark = 0, nblk = 0;
+    std::vector<int4> hblk;         // host copies of the marker-block table and
+    std::vector<int4> hpart;        // of the per-particle (first marker, markers, instance)
     double rc_max = 0;
     int64_t steps = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -242,6 +244,8 @@ ParticleArgs particle_args(lbm_ctx* ctx, int cur) {
     pa.weight = ctx->cfg.weight;
     pa.single = ctx->ninst == 1;
     pa.one = ctx->hinst[0];
+    pa.nblk_inline = ctx->nblk <= INLINE_BLOCKS ? ctx->nblk : 0;
+    for (int k = 0; k < pa.nblk_inline; ++k) pa.blk_inline[k] = ctx->hblk[k];
     return pa;
 }
 
@@ -256,6 +260,8 @@ SpreadArgs spread_args(lbm_ctx* ctx, const ParticleArgs& pa) {
     sa.err = ctx->err;
     sa.single = ctx->ninst == 1;
     sa.one = ctx->hinst[0];
+    sa.np_inline = ctx->np <= INLINE_PARTICLES ? ctx->np : 0;
+    for (int k = 0; k < sa.np_inline; ++k) sa.part_inline[k] = ctx->hpart[k];
     return sa;
 }
 
@@ -572,6 +578,8 @@ lbm_status add_particle_t(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, co
     CK(cudaStreamSynchronize(ctx->stream));
     drop_graphs(ctx);  // captured steps do not know this particle
     ctx->rc_max = std::max(ctx->rc_max, so.rcirc);
+    ctx->hblk.insert(ctx->hblk.end(), blocks.begin(), blocks.end());
+    ctx->hpart.push_back(make_int4(P.m0, n, inst, 0));
     ctx->nmark += n;
     ctx->nblk += P.nblk;
     if (out_id) *out_id = ctx->np;

@@ -68,6 +68,7 @@ struct DParticleT {
 using DParticle = DParticleT<double>;
 
 constexpr int MB = 8;         // markers per block of the marker kernels (one warp, 4 lanes each)
+constexpr int INLINE_BLOCKS = 128, INLINE_PARTICLES = 64;
 
 // Spreading record of one marker: the unwrapped lower-left node (i0, j0) of
 // its 3x3 support and the 9 contributions S_l phi_k F_l (Eq. 12).
@@ -101,6 +102,10 @@ struct ParticleArgs {
     int weight;
     int single;               // the context holds one lattice: `one` is its descriptor
     Inst one;
+    // a context of at most INLINE_BLOCKS marker blocks also passes the block
+    // table in the parameters (no dependent load in front of the block's work)
+    int nblk_inline;          // 0 or the block count
+    int4 blk_inline[INLINE_BLOCKS];
 };
 
 struct SpreadArgs {
@@ -113,6 +118,8 @@ struct SpreadArgs {
     unsigned* err;
     int single;               // as in ParticleArgs
     Inst one;
+    int np_inline;            // 0 or the particle count (at most INLINE_PARTICLES)
+    int4 part_inline[INLINE_PARTICLES];  // per particle: (first marker, markers, instance, 0)
 };
 
 // Fluid step over a list of tiles: task t = (instance, tile x, tile y, 0),

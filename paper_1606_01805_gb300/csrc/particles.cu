@@ -233,7 +233,7 @@ __device__ __forceinline__ const Inst& inst_of(const A& a, int w) {
 
 template <class S, class C, class R, bool ONE>
 __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
-    const int4 bk = a.blk[blockIdx.x];
+    const int4 bk = a.nblk_inline ? a.blk_inline[blockIdx.x] : a.blk[blockIdx.x];
     const DParticleT<R>* P = static_cast<const DParticleT<R>*>(a.pin) + bk.x;
     const Inst& I = inst_of<ONE>(a, bk.w);
     const Geo& G = I.G;
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
 
 template <class S, class C, class R, bool ONE>
 __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
-    const int4 bk = a.blk[blockIdx.x];
+    const int4 bk = a.nblk_inline ? a.blk_inline[blockIdx.x] : a.blk[blockIdx.x];
     const DParticleT<R>* Q = static_cast<const DParticleT<R>*>(a.pout) + bk.x;  // after the update
     const Inst& I = inst_of<ONE>(a, bk.w);
     const Geo& G = I.G;
@@ -434,7 +434,18 @@ template <class C, class R, bool ONE>
 __global__ void __launch_bounds__(TX * TY) k_spread(SpreadArgs a) {
     constexpr int CAP = spread_cap<C>();
     const DParticleT<R>* P = static_cast<const DParticleT<R>*>(a.parts) + blockIdx.y;
-    const Inst& I = inst_of<ONE>(a, ONE ? 0 : P->inst);
+    int m0, nm, pinst;
+    if (a.np_inline) {
+        const int4 pr = a.part_inline[blockIdx.y];
+        m0 = pr.x;
+        nm = pr.y;
+        pinst = pr.z;
+    } else {
+        m0 = P->m0;
+        nm = P->nm;
+        pinst = ONE ? 0 : P->inst;
+    }
+    const Inst& I = inst_of<ONE>(a, pinst);
     const Geo& G = I.G;
     const Rec<C>* recs = static_cast<const Rec<C>*>(a.recs);
     C* flb = static_cast<C*>(a.flb) + I.flb_off;
@@ -449,7 +460,6 @@ __global__ void __launch_bounds__(TX * TY) k_spread(SpreadArgs a) {
     const int x0 = box.x + (blockIdx.x % ntx) * TX, y0 = box.y + (blockIdx.x / ntx) * TY;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int cxl = x0 + t % TX, cyl = y0 + t / TX;  // this thread's (unwrapped) cell
-    const int m0 = P->m0, nm = P->nm;
     C ax = C(0), ay = C(0);
     bool touched = false;
     for (int base = 0; base < nm; base += CAP) {
