@@ -180,14 +180,18 @@ def time_device(wl, prec, steps, warmup, flush, pick_tile=False):
         sim.set_tile(best[1])
     for _ in range(warmup):
         do_flush()
-        sim.step_timed(1)
+        sim.step_timed(1, fluid=False)
     sim.sync()
+    # the steps as lbm_step runs them; then, for the fluid kernel's own time,
+    # the same number of steps with an event in front of it (it then starts
+    # after the spreading kernel instead of overlapping its loads with it)
     ms_step = ms_fluid = 0.0
     for _ in range(steps):
         do_flush()
-        a, b = sim.step_timed(1)
-        ms_step += a
-        ms_fluid += b
+        ms_step += sim.step_timed(1, fluid=False)[0]
+    for _ in range(steps):
+        do_flush()
+        ms_fluid += sim.step_timed(1)[1]
     sim.sync()
     launches = steps * (4 if wl.particles else 1)
     tile = sim.tile()
@@ -214,8 +218,9 @@ def time_batched(prec, steps, warmup, instances=512):
 
     wls = W.batched_screening(steps=0)[:instances]
     b = screening_batch(prec, wls)
-    b.step_timed(warmup)
-    ms_step, ms_fluid = b.step_timed(steps)
+    b.step_timed(warmup, fluid=False)
+    ms_step = b.step_timed(steps, fluid=False)[0]
+    ms_fluid = b.step_timed(steps)[1]
     tile = b.tile()
     b.close()
     cells = sum(w.cells for w in wls)
@@ -241,8 +246,9 @@ def time_sensitivity(prec, steps, warmup, n=64):
         if tangent:
             sim.set_wall_tangents(dwall, b)
         sim.add_particle(b, **w.particles[0].kwargs(), tangent=seed if tangent else None)
-    sim.step_timed(warmup)
-    ms, msf = sim.step_timed(steps)
+    sim.step_timed(warmup, fluid=False)
+    ms = sim.step_timed(steps, fluid=False)[0]
+    msf = sim.step_timed(steps)[1]
     sim.close()
     return sum(w.cells for w in wls), ms / steps, msf / steps
 

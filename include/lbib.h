@@ -162,7 +162,10 @@ lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps);
  * As lbm_step, with CUDA events around each step and around its fused
  * stream-collide launch.  Synchronises; adds the summed device time of
  * the steps (ms) to *ms_step and of the stream-collide launches to
- * *ms_fluid (either may be NULL).
+ * *ms_fluid (either may be NULL).  With ms_fluid NULL no event sits before
+ * the stream-collide launch, which may then start its population loads
+ * while the spreading kernel finishes, as in lbm_step; with ms_fluid it
+ * starts after the spreading kernel, so that its time is its own.
  */
 lbm_status lbm_step_timed(lbm_ctx* ctx, int32_t nsteps, double* ms_step, double* ms_fluid);
 

@@ -57,6 +57,7 @@ struct lbm_ctx {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // GRAPH_STEPS steps from buffer 0 / 1
     bool graphs_ok = true;
     cudaGraphExec_t timed[2] = {nullptr, nullptr};  // one step with its timing events
+    cudaGraphExec_t timed0[2] = {nullptr, nullptr}; // the same without the event before the fluid kernel
     bool timed_ok = true;
     std::string msg;
 };
@@ -271,7 +272,10 @@ int spread_tiles(const lbm_ctx* ctx) {
     return ((int)std::ceil(ext / 32.0) + 1) * ((int)std::ceil(ext / 16.0) + 1);
 }
 
-lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v) {
+// pdl: launch the fluid kernel with programmatic stream serialization (only
+// right after the spreading kernel: its prologue loads the populations the
+// previous step's fluid kernel wrote)
+lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v, bool pdl = false) {
     FluidArgs fa;
     fa.fin = ctx->f[cur];
     fa.fout = ctx->f[cur ^ 1];
@@ -283,7 +287,7 @@ lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v) {
     // one CTA per tile: the block scheduler keeps every SM filled as tiles
     // finish (the kernel's task loop then runs once per CTA)
     const int grid = std::max(1, fa.ntasks);
-    CK(launch_fluid(ctx->prec, v, fa, ctx->ninst == 1 ? &ctx->hinst[0] : nullptr, grid, st));
+    CK(launch_fluid(ctx->prec, v, fa, ctx->ninst == 1 ? &ctx->hinst[0] : nullptr, grid, st, pdl));
     return LBM_OK;
 }
 
@@ -291,8 +295,8 @@ lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v) {
 // boundary kernels (ib = true: probes / rigid update / markers, spreading)
 // or the fused fluid kernel over every instance (ib = false).  Bookkeeping
 // is the caller's.
-lbm_status enqueue_step_part(lbm_ctx* ctx, cudaStream_t st, int cur, bool ib) {
-    if (!ib) return launch_fluid_step(ctx, st, cur, ctx->variant);
+lbm_status enqueue_step_part(lbm_ctx* ctx, cudaStream_t st, int cur, bool ib, bool pdl = false) {
+    if (!ib) return launch_fluid_step(ctx, st, cur, ctx->variant, pdl && ctx->np > 0);
     if (ctx->np == 0) return LBM_OK;
     const ParticleArgs pa = particle_args(ctx, cur);
     CK(launch_probes(ctx->prec, pa, ctx->nblk, st));
@@ -302,12 +306,14 @@ lbm_status enqueue_step_part(lbm_ctx* ctx, cudaStream_t st, int cur, bool ib) {
 }
 
 // one time step from buffer `cur` on stream `st` (mid: optional event
-// between the IB kernels and the fluid kernel).  Bookkeeping is the caller's.
+// between the IB kernels and the fluid kernel, which then starts only after
+// it, so that mid -> end times the fluid kernel alone).  Bookkeeping is the
+// caller's.
 lbm_status enqueue_step(lbm_ctx* ctx, cudaStream_t st, int cur, cudaEvent_t mid) {
     lbm_status s = enqueue_step_part(ctx, st, cur, true);
     if (s != LBM_OK) return s;
     if (mid) CK(cudaEventRecord(mid, st));
-    return enqueue_step_part(ctx, st, cur, false);
+    return enqueue_step_part(ctx, st, cur, false, mid == nullptr);
 }
 
 // Capture GRAPH_STEPS steps starting from buffer `cur` on a private stream
@@ -332,17 +338,19 @@ bool capture_graph(lbm_ctx* ctx, int cur) {
 }
 
 // enqueue_step for capture: the event between the IB kernels and the fluid
-// kernel is an external record, i.e. a real event-record node
-lbm_status enqueue_timed_step(lbm_ctx* ctx, cudaStream_t st, int cur) {
+// kernel (with_mid) is an external record, i.e. a real event-record node
+lbm_status enqueue_timed_step(lbm_ctx* ctx, cudaStream_t st, int cur, bool with_mid) {
     lbm_status s = enqueue_step_part(ctx, st, cur, true);
     if (s != LBM_OK) return s;
-    CK(cudaEventRecordWithFlags(ctx->ev[1], st, cudaEventRecordExternal));
-    return enqueue_step_part(ctx, st, cur, false);
+    if (with_mid) CK(cudaEventRecordWithFlags(ctx->ev[1], st, cudaEventRecordExternal));
+    return enqueue_step_part(ctx, st, cur, false, !with_mid);
 }
 
-// One step from buffer `cur` with the three timing events recorded inside
-// the graph (same launches as enqueue_step, replayed like lbm_step replays).
-bool capture_timed(lbm_ctx* ctx, int cur) {
+// One step from buffer `cur` with the timing events recorded inside the
+// graph (same launches as enqueue_step, replayed like lbm_step replays);
+// with_mid adds the event between the IB kernels and the fluid kernel.
+bool capture_timed(lbm_ctx* ctx, int cur, bool with_mid) {
+    cudaGraphExec_t& ge = with_mid ? ctx->timed[cur] : ctx->timed0[cur];
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return false;
     bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
@@ -350,21 +358,21 @@ bool capture_timed(lbm_ctx* ctx, int cur) {
         // external records: real event-record nodes, not capture-internal
         // dependencies
         ok = cudaEventRecordWithFlags(ctx->ev[0], cs, cudaEventRecordExternal) == cudaSuccess &&
-             enqueue_timed_step(ctx, cs, cur) == LBM_OK &&
+             enqueue_timed_step(ctx, cs, cur, with_mid) == LBM_OK &&
              cudaEventRecordWithFlags(ctx->ev[2], cs, cudaEventRecordExternal) == cudaSuccess;
         cudaGraph_t g = nullptr;
         const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
-        ok = ok && ended && g && cudaGraphInstantiate(&ctx->timed[cur], g, 0) == cudaSuccess;
+        ok = ok && ended && g && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
         if (g) cudaGraphDestroy(g);
     }
     cudaStreamDestroy(cs);
     cudaGetLastError();
-    if (!ok) ctx->timed[cur] = nullptr;
+    if (!ok) ge = nullptr;
     return ok;
 }
 
 void drop_graphs(lbm_ctx* ctx) {
-    for (auto* set : {ctx->graph, ctx->timed})
+    for (auto* set : {ctx->graph, ctx->timed, ctx->timed0})
         for (int k = 0; k < 2; ++k)
             if (set[k]) {
                 cudaGraphExecDestroy(set[k]);
@@ -809,15 +817,19 @@ lbm_status lbm_step_timed(lbm_ctx* ctx, int32_t nsteps, double* ms_step, double*
     for (auto& e : ctx->ev)
         if (!e) CK(cudaEventCreate(&e));
     double tot = 0, flu = 0;
+    // the event before the fluid kernel only when its time is asked for: it
+    // keeps the fluid kernel from starting before the spreading kernel ends
+    const bool mid = ms_fluid != nullptr;
+    cudaGraphExec_t* set = mid ? ctx->timed : ctx->timed0;
     for (int32_t k = 0; k < nsteps; ++k) {
         // each step is a replay of its captured one-step graph (as lbm_step
         // replays steps), with the timing events inside it
-        if (ctx->timed_ok && !ctx->timed[ctx->cur] && !capture_timed(ctx, ctx->cur)) ctx->timed_ok = false;
+        if (ctx->timed_ok && !set[ctx->cur] && !capture_timed(ctx, ctx->cur, mid)) ctx->timed_ok = false;
         if (ctx->timed_ok) {
-            CK(cudaGraphLaunch(ctx->timed[ctx->cur], ctx->stream));
+            CK(cudaGraphLaunch(set[ctx->cur], ctx->stream));
         } else {
             CK(cudaEventRecord(ctx->ev[0], ctx->stream));
-            lbm_status s = enqueue_step(ctx, ctx->stream, ctx->cur, ctx->ev[1]);
+            lbm_status s = enqueue_step(ctx, ctx->stream, ctx->cur, mid ? ctx->ev[1] : nullptr);
             if (s != LBM_OK) return s;
             CK(cudaEventRecord(ctx->ev[2], ctx->stream));
         }
@@ -826,7 +838,7 @@ lbm_status lbm_step_timed(lbm_ctx* ctx, int32_t nsteps, double* ms_step, double*
         CK(cudaEventSynchronize(ctx->ev[2]));
         float a = 0, b = 0;
         CK(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[2]));
-        CK(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]));
+        if (mid) CK(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]));
         tot += a;
         flu += b;
     }
@@ -993,7 +1005,7 @@ extern "C" lbm_status lbm_step_static(lbm_ctx* ctx, int32_t nsteps) {
             CK(launch_markers(ctx->prec, pa, ctx->nblk, ctx->stream));
             CK(launch_spread(ctx->prec, spread_args(ctx, pa), ctx->np, spread_tiles(ctx), ctx->stream));
         }
-        lbm_status s = launch_fluid_step(ctx, ctx->stream, ctx->cur, ctx->variant);
+        lbm_status s = launch_fluid_step(ctx, ctx->stream, ctx->cur, ctx->variant, ctx->np > 0);
         if (s != LBM_OK) return s;
         ctx->cur ^= 1;
         ctx->steps += 1;

@@ -113,9 +113,6 @@ __device__ __forceinline__ void fluid_tile(const Geo& G, const S* __restrict__ f
     // the cell is interior (all 9 sources inside, none of them clamped)
     const bool rows_in = y >= 1 && y <= G.ny - 2;
     const bool any = x0 < G.nx;
-    // force flags of the 32-cell segment of this thread
-    const int seg = y * G.nseg + (x0 >> 5);
-    const bool forced = any && flags[seg] != 0;
 
     C v[9][N];
     // vector loads for every lane (addresses clamped in-bounds), shuffles by all
@@ -161,6 +158,12 @@ __device__ __forceinline__ void fluid_tile(const Geo& G, const S* __restrict__ f
             }
         }
     }
+    // the populations are in; the forces of this step come from the
+    // spreading kernel before this one (flags of this thread's 32-cell segment)
+    pdl_wait();
+    pdl_trigger();
+    const int seg = y * G.nseg + (x0 >> 5);
+    const bool forced = any && flags[seg] != 0;
     if (any) {
         C fxi[N], fyi[N];
 #pragma unroll
@@ -318,23 +321,22 @@ __global__ void k_fields(FieldArgs a) {
 dim3 grid_for(int nx, int rows) { return dim3((nx + 31) / 32, (rows + BY - 1) / BY); }
 
 template <class S, class C, int V>
-cudaError_t launch_fluid_v(const FluidArgs& a, const Inst* one, int grid, cudaStream_t s) {
+cudaError_t launch_fluid_v(const FluidArgs& a, const Inst* one, int grid, cudaStream_t s, bool pdl) {
     constexpr int N = FLUID_VARIANTS[V].cpt, BYt = FLUID_VARIANTS[V].by;
     if (one) {
         const dim3 g((one->G.nx + 32 * N - 1) / (32 * N), (one->G.ny + BYt - 1) / BYt);
-        k_fluid_one<S, C, N, BYt><<<g, dim3(32, BYt), 0, s>>>(a, *one);
-    } else {
-        k_fluid<S, C, N, BYt><<<grid, dim3(32, BYt), 0, s>>>(a);
+        return launch_k(pdl, k_fluid_one<S, C, N, BYt>, g, dim3(32, BYt), s, a, *one);
     }
-    return cudaGetLastError();
+    return launch_k(pdl, k_fluid<S, C, N, BYt>, dim3(grid), dim3(32, BYt), s, a);
 }
 
 template <class S, class C>
-cudaError_t launch_fluid_t(int variant, const FluidArgs& a, const Inst* one, int grid, cudaStream_t s) {
+cudaError_t launch_fluid_t(int variant, const FluidArgs& a, const Inst* one, int grid, cudaStream_t s,
+                           bool pdl) {
     switch (variant) {
-        case 1: return launch_fluid_v<S, C, 1>(a, one, grid, s);
-        case 2: return launch_fluid_v<S, C, 2>(a, one, grid, s);
-        default: return launch_fluid_v<S, C, 0>(a, one, grid, s);
+        case 1: return launch_fluid_v<S, C, 1>(a, one, grid, s, pdl);
+        case 2: return launch_fluid_v<S, C, 2>(a, one, grid, s, pdl);
+        default: return launch_fluid_v<S, C, 0>(a, one, grid, s, pdl);
     }
 }
 
@@ -386,12 +388,12 @@ cudaError_t launch_init(int prec, void* fbuf, const Inst& I, int kind, double in
 // the tangent mode has the one-cell tile only (variant 2): a cell's 9
 // populations with their derivatives already take 36 registers
 cudaError_t launch_fluid(int prec, int variant, const FluidArgs& a, const Inst* one, int grid,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool pdl) {
     if (a.ntasks <= 0) return cudaSuccess;
-    if (prec == LBM_FP64) return launch_fluid_t<double, double>(variant, a, one, grid, s);
-    if (prec == LBM_FP32) return launch_fluid_t<float, float>(variant, a, one, grid, s);
-    if (prec == LBM_FP16_SHIFTED) return launch_fluid_t<__half, float>(variant, a, one, grid, s);
-    return launch_fluid_v<TF, TF, 2>(a, one, grid, s);
+    if (prec == LBM_FP64) return launch_fluid_t<double, double>(variant, a, one, grid, s, pdl);
+    if (prec == LBM_FP32) return launch_fluid_t<float, float>(variant, a, one, grid, s, pdl);
+    if (prec == LBM_FP16_SHIFTED) return launch_fluid_t<__half, float>(variant, a, one, grid, s, pdl);
+    return launch_fluid_v<TF, TF, 2>(a, one, grid, s, pdl);
 }
 
 int fluid_blocks_per_sm(int prec, int variant) {

@@ -9,6 +9,34 @@
 
 namespace lbib {
 
+// ------------------------------------------ programmatic dependent launch ----
+// The four kernels of a step run back to back in one stream.  Each may be
+// launched with programmatic stream serialization: it then starts while its
+// predecessor still runs, does the part of its work that reads nothing the
+// predecessor writes, and calls pdl_wait() before anything else (the
+// predecessor has then completed and its writes are visible).  Each calls
+// pdl_trigger() only after its own pdl_wait(), so when a kernel starts, every
+// kernel before its immediate predecessor has completed.  Launched without
+// the attribute, pdl_wait() returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                     Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ---------------------------------------------------------------- D2Q9 ----
 // Velocities of Eq. 3: e_0 rest, e_1..e_4 axes at angles (i-1) pi/2,
 // e_5..e_8 diagonals at (2i-9) pi/4; weights 4/9, 1/9, 1/36.

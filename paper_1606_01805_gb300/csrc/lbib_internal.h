@@ -154,8 +154,10 @@ struct FieldArgs {
 cudaError_t launch_init(int prec, void* fbuf, const Inst& I, int kind, double init_u, cudaStream_t s);
 // one != nullptr: the context holds that single lattice (2-D tile grid,
 // descriptor by value); otherwise the task list over all instances
+// pdl: launched with programmatic stream serialization (see pdl_wait); only
+// when the kernel before it in the stream is the spreading kernel
 cudaError_t launch_fluid(int prec, int variant, const FluidArgs& a, const Inst* one, int grid,
-                         cudaStream_t s);
+                         cudaStream_t s, bool pdl);
 int fluid_blocks_per_sm(int prec, int variant);
 cudaError_t launch_fields(int prec, const FieldArgs& a, cudaStream_t s);
 cudaError_t launch_probes(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s);

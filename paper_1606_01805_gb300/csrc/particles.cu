@@ -244,9 +244,7 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     const int ml = lane / LPM, m = bk.y + ml;  // marker (absolute index)
     const bool active = ml < bk.z;
     unsigned err = 0;
-    if (lane == 0 && bk.y == P->m0)  // the particle's first block resets its box
-        a.boxes[bk.x] = make_int4(INT_MAX, INT_MAX, INT_MIN, INT_MIN);
-    // body at its latest level
+    // body at its latest level (written by this kernel a step ago)
     const R c0 = P->cs[0][0], s0 = P->cs[0][1];
     Vec2<R> rb{R(0.0), R(0.0)}, nb{R(1.0), R(0.0)};
     if (active) {
@@ -258,6 +256,10 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     const R px = P->X[0][0] + rx + PROBE * nx, py = P->X[0][1] + ry + PROBE * ny;
     QuadMLS<true, C, R> M;
     M.support(px, py, q);
+    pdl_wait();  // the populations come from the fluid kernel before this one
+    pdl_trigger();
+    if (lane == 0 && bk.y == P->m0)  // the particle's first block resets its box
+        a.boxes[bk.x] = make_int4(INT_MAX, INT_MAX, INT_MIN, INT_MIN);
     // node fields first (their loads overlap the FP64 work of the solve)
     C rk[3], uk[3], vk[3];
 #pragma unroll
@@ -357,6 +359,8 @@ __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
     unsigned err = 0;
     Vec2<R> rb{R(0.0), R(0.0)};
     if (active) rb = static_cast<const Vec2<R>*>(a.rb)[m];
+    pdl_wait();  // the updated body comes from the probe kernel
+    pdl_trigger();
     const R X = Q->X[0][0], Y = Q->X[0][1], cn = Q->cs[0][0], sn = Q->cs[0][1];
     const R BU = Q->U[0][0], BV = Q->U[0][1], BW = Q->W[0];
     const R rx = cn * rb.x - sn * rb.y, ry = sn * rb.x + cn * rb.y;
@@ -452,6 +456,8 @@ __global__ void __launch_bounds__(TX * TY) k_spread(SpreadArgs a) {
     uint8_t* flags = a.flags + I.flags_off;
     __shared__ Rec<C> list[CAP];
     __shared__ int wcount[TX * TY / 32];
+    pdl_wait();  // boxes and records come from the marker kernel
+    pdl_trigger();
     const int4 box = a.boxes[blockIdx.y];
     if (box.x > box.z) return;
     const int ntx = (box.z - box.x + TX) / TX, nty = (box.w - box.y + TY) / TY;
@@ -533,49 +539,48 @@ size_t particle_bytes(int prec) {
     return prec == LBM_FP32_TANGENT ? sizeof(DParticleT<TD>) : sizeof(DParticleT<double>);
 }
 
+// every IB kernel is launched with programmatic stream serialization: its
+// prologue reads only what no kernel still running can write (pdl_wait)
 template <bool ONE>
-void probes_t(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s) {
-    if (prec == LBM_FP64) k_probes<double, double, double, ONE><<<nblocks, 32, 0, s>>>(a);
-    else if (prec == LBM_FP32) k_probes<float, float, double, ONE><<<nblocks, 32, 0, s>>>(a);
-    else if (prec == LBM_FP16_SHIFTED) k_probes<__half, float, double, ONE><<<nblocks, 32, 0, s>>>(a);
-    else k_probes<TF, TF, TD, ONE><<<nblocks, 32, 0, s>>>(a);
+cudaError_t probes_t(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s) {
+    const dim3 g(nblocks), b(32);
+    if (prec == LBM_FP64) return launch_k(true, k_probes<double, double, double, ONE>, g, b, s, a);
+    if (prec == LBM_FP32) return launch_k(true, k_probes<float, float, double, ONE>, g, b, s, a);
+    if (prec == LBM_FP16_SHIFTED) return launch_k(true, k_probes<__half, float, double, ONE>, g, b, s, a);
+    return launch_k(true, k_probes<TF, TF, TD, ONE>, g, b, s, a);
 }
 
 template <bool ONE>
-void markers_t(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s) {
-    if (prec == LBM_FP64) k_markers<double, double, double, ONE><<<nblocks, 32, 0, s>>>(a);
-    else if (prec == LBM_FP32) k_markers<float, float, double, ONE><<<nblocks, 32, 0, s>>>(a);
-    else if (prec == LBM_FP16_SHIFTED) k_markers<__half, float, double, ONE><<<nblocks, 32, 0, s>>>(a);
-    else k_markers<TF, TF, TD, ONE><<<nblocks, 32, 0, s>>>(a);
+cudaError_t markers_t(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s) {
+    const dim3 g(nblocks), b(32);
+    if (prec == LBM_FP64) return launch_k(true, k_markers<double, double, double, ONE>, g, b, s, a);
+    if (prec == LBM_FP32) return launch_k(true, k_markers<float, float, double, ONE>, g, b, s, a);
+    if (prec == LBM_FP16_SHIFTED) return launch_k(true, k_markers<__half, float, double, ONE>, g, b, s, a);
+    return launch_k(true, k_markers<TF, TF, TD, ONE>, g, b, s, a);
 }
 
 template <bool ONE>
-void spread_t(int prec, const SpreadArgs& a, dim3 g, cudaStream_t s) {
-    if (prec == LBM_FP64) k_spread<double, double, ONE><<<g, TX * TY, 0, s>>>(a);
-    else if (prec == LBM_FP32_TANGENT) k_spread<TF, TD, ONE><<<g, TX * TY, 0, s>>>(a);
-    else k_spread<float, double, ONE><<<g, TX * TY, 0, s>>>(a);
+cudaError_t spread_t(int prec, const SpreadArgs& a, dim3 g, cudaStream_t s) {
+    const dim3 b(TX * TY);
+    if (prec == LBM_FP64) return launch_k(true, k_spread<double, double, ONE>, g, b, s, a);
+    if (prec == LBM_FP32_TANGENT) return launch_k(true, k_spread<TF, TD, ONE>, g, b, s, a);
+    return launch_k(true, k_spread<float, double, ONE>, g, b, s, a);
 }
 
 cudaError_t launch_probes(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
-    if (a.single) probes_t<true>(prec, a, nblocks, s);
-    else probes_t<false>(prec, a, nblocks, s);
-    return cudaGetLastError();
+    return a.single ? probes_t<true>(prec, a, nblocks, s) : probes_t<false>(prec, a, nblocks, s);
 }
 
 cudaError_t launch_markers(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
-    if (a.single) markers_t<true>(prec, a, nblocks, s);
-    else markers_t<false>(prec, a, nblocks, s);
-    return cudaGetLastError();
+    return a.single ? markers_t<true>(prec, a, nblocks, s) : markers_t<false>(prec, a, nblocks, s);
 }
 
 cudaError_t launch_spread(int prec, const SpreadArgs& a, int np, int tiles, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     const dim3 g(tiles, np);
-    if (a.single) spread_t<true>(prec, a, g, s);
-    else spread_t<false>(prec, a, g, s);
-    return cudaGetLastError();
+    return a.single ? spread_t<true>(prec, a, g, s) : spread_t<false>(prec, a, g, s);
 }
 
 }  // namespace lbib

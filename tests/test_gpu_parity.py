@@ -244,11 +244,14 @@ def test_timed_steps_match_plain_steps():
     wl = _coupled("channel", W.CIRCLE, (12.0,), 30.3, 22.1, n=48).with_(steps=0)
     a = W.run_with(gpu_factory(FP32), wl)
     b = W.run_with(gpu_factory(FP32), wl)
+    c = W.run_with(gpu_factory(FP32), wl)
     ms_step, ms_fluid = a.step_timed(9)
     b.step(9)
-    assert ms_step > ms_fluid > 0
+    ms_c, zero = c.step_timed(9, fluid=False)  # no event in front of the fluid kernel
+    assert ms_step > ms_fluid > 0 and ms_c > 0 and zero == 0
     np.testing.assert_array_equal(a.populations(), b.populations())
-    assert a.particles() == b.particles()
+    np.testing.assert_array_equal(c.populations(), b.populations())
+    assert a.particles() == b.particles() == c.particles()
 
 
 FP16S = lbib.LBM_FP16_SHIFTED
