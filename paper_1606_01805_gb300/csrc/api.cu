@@ -45,6 +45,7 @@ struct lbm_ctx {
     void* S;                        // R[markers]
     void* recs;
     int4* boxes;
+    int4* ptab;                     // device copy of hpart
     unsigned* err;
     double* scratch;
     int scratch_rows;
@@ -140,7 +141,7 @@ std::vector<int4> make_tasks(const std::vector<Inst>& insts, int v) {
 struct Layout {
     std::vector<Inst> insts;
     size_t f0, f1, flb, flags, insts_off, tasks[N_FLUID_VARIANTS], parts, blk, partial, count, rb, nb,
-        S, recs, boxes, err, scratch, total;
+        S, recs, boxes, ptab, err, scratch, total;
     int ntasks[N_FLUID_VARIANTS];
     int scratch_rows;
 };
@@ -189,6 +190,7 @@ Layout layout(const lbm_config* cfgs, int n) {
     L.S = o; o = up(o + M * R);
     L.recs = o; o = up(o + M * rec_bytes(prec));
     L.boxes = o; o = up(o + P * sizeof(int4));
+    L.ptab = o; o = up(o + P * sizeof(int4));
     L.err = o; o = up(o + 16);
     L.scratch = o; o = up(o + fplanes * (size_t)L.scratch_rows * max_nx * sizeof(double));
     L.total = o;
@@ -253,7 +255,7 @@ ParticleArgs particle_args(lbm_ctx* ctx, int cur) {
 SpreadArgs spread_args(lbm_ctx* ctx, const ParticleArgs& pa) {
     SpreadArgs sa;
     sa.insts = ctx->insts;
-    sa.parts = ctx->parts;
+    sa.ptab = ctx->ptab;
     sa.recs = pa.recs;
     sa.boxes = pa.boxes;
     sa.flb = ctx->flb;
@@ -266,11 +268,14 @@ SpreadArgs spread_args(lbm_ctx* ctx, const ParticleArgs& pa) {
     return sa;
 }
 
-// tiles of 32 x 16 cells covering the largest support box
-int spread_tiles(const lbm_ctx* ctx) {
-    const double ext = 2.0 * ctx->rc_max + 4.0;
+// tiles of 32 x 16 cells covering the support box of a particle whose
+// markers lie within rc of its centroid (the box spans at most 2 rc + 4
+// cells per side), and for the largest particle of the context
+int box_tiles(double rc) {
+    const double ext = 2.0 * rc + 4.0;
     return ((int)std::ceil(ext / 32.0) + 1) * ((int)std::ceil(ext / 16.0) + 1);
 }
+int spread_tiles(const lbm_ctx* ctx) { return box_tiles(ctx->rc_max); }
 
 // pdl: launch the fluid kernel with programmatic stream serialization (only
 // right after the spreading kernel: its prologue loads the populations the
@@ -468,6 +473,7 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
     ctx->S = b + L.S;
     ctx->recs = b + L.recs;
     ctx->boxes = reinterpret_cast<int4*>(b + L.boxes);
+    ctx->ptab = reinterpret_cast<int4*>(b + L.ptab);
     ctx->err = reinterpret_cast<unsigned*>(b + L.err);
     ctx->scratch = reinterpret_cast<double*>(b + L.scratch);
     ctx->scratch_rows = L.scratch_rows;
@@ -587,7 +593,10 @@ lbm_status add_particle_t(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, co
     drop_graphs(ctx);  // captured steps do not know this particle
     ctx->rc_max = std::max(ctx->rc_max, so.rcirc);
     ctx->hblk.insert(ctx->hblk.end(), blocks.begin(), blocks.end());
-    ctx->hpart.push_back(make_int4(P.m0, n, inst, 0));
+    ctx->hpart.push_back(make_int4(P.m0, n, inst, box_tiles(so.rcirc)));
+    CK(cudaMemcpyAsync(ctx->ptab + ctx->np, &ctx->hpart.back(), sizeof(int4), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     ctx->nmark += n;
     ctx->nblk += P.nblk;
     if (out_id) *out_id = ctx->np;

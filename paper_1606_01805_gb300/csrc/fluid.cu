@@ -101,7 +101,10 @@ __device__ __forceinline__ void cell_update(C v[9], const Geo& G, C fx_ib, C fy_
 // +-x is a one-lane shuffle of the neighbouring vector, with one extra
 // element load at the warp's two ends.  Cells on a wall or periodic edge
 // take the per-cell general path (emitted once, after the fast cells).
-template <class S, class C, int N>
+// PDL: launched with programmatic stream serialization after the spreading
+// kernel: the population loads come first, the force flags and the forces
+// after pdl_wait().  Otherwise the flags are loaded with the populations.
+template <class S, class C, int N, bool PDL>
 __device__ __forceinline__ void fluid_tile(const Geo& G, const S* __restrict__ fin,
                                            S* __restrict__ fout, C* __restrict__ flb,
                                            uint8_t* __restrict__ flags, int tx, int y) {
@@ -113,6 +116,10 @@ __device__ __forceinline__ void fluid_tile(const Geo& G, const S* __restrict__ f
     // the cell is interior (all 9 sources inside, none of them clamped)
     const bool rows_in = y >= 1 && y <= G.ny - 2;
     const bool any = x0 < G.nx;
+    // force flags of the 32-cell segment of this thread
+    const int seg = y * G.nseg + (x0 >> 5);
+    bool forced = false;
+    if (!PDL) forced = any && flags[seg] != 0;
 
     C v[9][N];
     // vector loads for every lane (addresses clamped in-bounds), shuffles by all
@@ -158,12 +165,13 @@ __device__ __forceinline__ void fluid_tile(const Geo& G, const S* __restrict__ f
             }
         }
     }
-    // the populations are in; the forces of this step come from the
-    // spreading kernel before this one (flags of this thread's 32-cell segment)
-    pdl_wait();
-    pdl_trigger();
-    const int seg = y * G.nseg + (x0 >> 5);
-    const bool forced = any && flags[seg] != 0;
+    if (PDL) {
+        // the populations are on their way; the forces of this step come
+        // from the spreading kernel before this one
+        pdl_wait();
+        pdl_trigger();
+        forced = any && flags[seg] != 0;
+    }
     if (any) {
         C fxi[N], fyi[N];
 #pragma unroll
@@ -250,7 +258,7 @@ __global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value) k_
     for (int t = blockIdx.x; t < a.ntasks; t += gridDim.x) {
         const int4 task = a.tasks[t];
         const Inst& I = a.insts[task.x];
-        fluid_tile<S, C, N>(I.G, fin + I.f_off, fout + I.f_off, flb + I.flb_off,
+        fluid_tile<S, C, N, false>(I.G, fin + I.f_off, fout + I.f_off, flb + I.flb_off,
                             a.flags + I.flags_off, task.y, task.z * BYt + threadIdx.y);
     }
 }
@@ -258,10 +266,10 @@ __global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value) k_
 // the same step for a context holding one lattice: its descriptor arrives
 // by value (constant bank) and the grid is the tile grid itself, so no load
 // stands in front of the population loads
-template <class S, class C, int N, int BYt>
+template <class S, class C, int N, int BYt, bool PDL>
 __global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value)
     k_fluid_one(FluidArgs a, Inst I) {
-    fluid_tile<S, C, N>(I.G, static_cast<const S*>(a.fin) + I.f_off, static_cast<S*>(a.fout) + I.f_off,
+    fluid_tile<S, C, N, PDL>(I.G, static_cast<const S*>(a.fin) + I.f_off, static_cast<S*>(a.fout) + I.f_off,
                         static_cast<C*>(a.flb) + I.flb_off, a.flags + I.flags_off, blockIdx.x,
                         blockIdx.y * BYt + threadIdx.y);
 }
@@ -325,9 +333,12 @@ cudaError_t launch_fluid_v(const FluidArgs& a, const Inst* one, int grid, cudaSt
     constexpr int N = FLUID_VARIANTS[V].cpt, BYt = FLUID_VARIANTS[V].by;
     if (one) {
         const dim3 g((one->G.nx + 32 * N - 1) / (32 * N), (one->G.ny + BYt - 1) / BYt);
-        return launch_k(pdl, k_fluid_one<S, C, N, BYt>, g, dim3(32, BYt), s, a, *one);
+        if (pdl) return launch_k(true, k_fluid_one<S, C, N, BYt, true>, g, dim3(32, BYt), s, a, *one);
+        return launch_k(false, k_fluid_one<S, C, N, BYt, false>, g, dim3(32, BYt), s, a, *one);
     }
-    return launch_k(pdl, k_fluid<S, C, N, BYt>, dim3(grid), dim3(32, BYt), s, a);
+    // the task-list kernel of a batch is launched without PDL: its CTAs are
+    // small and many, and the flags load is best issued with the populations
+    return launch_k(false, k_fluid<S, C, N, BYt>, dim3(grid), dim3(32, BYt), s, a);
 }
 
 template <class S, class C>

@@ -110,7 +110,6 @@ struct ParticleArgs {
 
 struct SpreadArgs {
     const Inst* insts;
-    const void* parts;        // either state buffer (marker ranges, instance)
     const void* recs;
     const int4* boxes;
     void* flb;                // force buffer (2 planes of compute type per instance)
@@ -118,8 +117,9 @@ struct SpreadArgs {
     unsigned* err;
     int single;               // as in ParticleArgs
     Inst one;
+    const int4* ptab;         // per particle: (first marker, markers, instance, tiles of its box)
     int np_inline;            // 0 or the particle count (at most INLINE_PARTICLES)
-    int4 part_inline[INLINE_PARTICLES];  // per particle: (first marker, markers, instance, 0)
+    int4 part_inline[INLINE_PARTICLES];  // the first np_inline entries of ptab
 };
 
 // Fluid step over a list of tiles: task t = (instance, tile x, tile y, 0),

@@ -437,19 +437,11 @@ constexpr int spread_cap() {
 template <class C, class R, bool ONE>
 __global__ void __launch_bounds__(TX * TY) k_spread(SpreadArgs a) {
     constexpr int CAP = spread_cap<C>();
-    const DParticleT<R>* P = static_cast<const DParticleT<R>*>(a.parts) + blockIdx.y;
-    int m0, nm, pinst;
-    if (a.np_inline) {
-        const int4 pr = a.part_inline[blockIdx.y];
-        m0 = pr.x;
-        nm = pr.y;
-        pinst = pr.z;
-    } else {
-        m0 = P->m0;
-        nm = P->nm;
-        pinst = ONE ? 0 : P->inst;
-    }
-    const Inst& I = inst_of<ONE>(a, pinst);
+    // the particle's markers, lattice and tile bound (fixed when it was added)
+    const int4 pr = a.np_inline ? a.part_inline[blockIdx.y] : a.ptab[blockIdx.y];
+    const int m0 = pr.x, nm = pr.y, tiles = pr.w;
+    if ((int)blockIdx.x >= tiles) return;  // beyond this particle's box (whole CTA)
+    const Inst& I = inst_of<ONE>(a, pr.z);
     const Geo& G = I.G;
     const Rec<C>* recs = static_cast<const Rec<C>*>(a.recs);
     C* flb = static_cast<C*>(a.flb) + I.flb_off;
@@ -461,7 +453,7 @@ __global__ void __launch_bounds__(TX * TY) k_spread(SpreadArgs a) {
     const int4 box = a.boxes[blockIdx.y];
     if (box.x > box.z) return;
     const int ntx = (box.z - box.x + TX) / TX, nty = (box.w - box.y + TY) / TY;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && ntx * nty > (int)gridDim.x) atomicOr(a.err, ERR_DOMAIN);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ntx * nty > tiles) atomicOr(a.err, ERR_DOMAIN);
     if ((int)blockIdx.x >= ntx * nty) return;  // whole CTA
     const int x0 = box.x + (blockIdx.x % ntx) * TX, y0 = box.y + (blockIdx.x / ntx) * TY;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
