@@ -35,13 +35,14 @@ BYTES_PER_CELL = {0: 144, 1: 72, 2: 36, 3: 288}
 PREC_NAMES = {0: "f64", 1: "f32", 2: "f16-storage/f32", 3: "f32+3 tangents"}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per fluid-kernel launch (median
-# over the launches of one ncu capture of the bench command), keyed by the
-# hash of the kernel sources it was taken on, the workload, the precision
-# and the tile shape (profiles/k_fluid_sedimentation_400x1200.md)
+# over the launches of one ncu capture of the bench command; the launches
+# timed alone, as the roofline is), keyed by the hash of the kernel sources
+# it was taken on, the workload, the precision and the tile shape
+# (profiles/k_fluid_sedimentation_400x1200.md)
 NCU_TRAFFIC = {
-    ("5c7edde56c8ec884", "sedimentation_circle_400x1200", 1, 0): 18221568 + 150400,
-    ("5c7edde56c8ec884", "sedimentation_circle_400x1200", 1, 1): 18216704 + 147200,
-    ("5c7edde56c8ec884", "sedimentation_circle_400x1200", 1, 2): 18037504 + 0,
+    ("a396b30e9588dedb", "sedimentation_circle_400x1200", 1, 0): 18220544 + 147968,
+    ("a396b30e9588dedb", "sedimentation_circle_400x1200", 1, 1): 18216960 + 147200,
+    ("a396b30e9588dedb", "sedimentation_circle_400x1200", 1, 2): 18037504 + 256,
 }
 
 
