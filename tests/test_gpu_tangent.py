@@ -185,3 +185,24 @@ def test_autograd_backward_is_the_vector_jacobian_product():
     (out * g).sum().backward()
     _, J = sens.transport_jacobian(PARAMS[:2], THETAS[:2], steps=100)
     assert np.allclose(p.grad.numpy(), np.einsum("bo,bok->bk", g.numpy(), J), rtol=1e-12, atol=0)
+
+
+def test_batch_of_64_equals_single_contexts():
+    # the study's batch (64 channels in one context) gives every instance
+    # the values and tangents it gets alone, bit for bit
+    steps = 300
+    vals, J = sens.transport_jacobian(PARAMS, THETAS, steps=steps)
+    assert vals.shape == (64, 2) and J.shape == (64, 2, 3)
+    assert np.all(np.isfinite(J))
+    for b in (0, 31, 63):
+        wl = W.sensitivity_ellipse(*PARAMS[b], steps=steps, theta=float(THETAS[b]))
+        sim = lbib.Simulation(wl.nx, wl.ny, wl.tau, precision=TAN, **wl.lattice_kwargs())
+        seed, dwall = sens.seeds(PARAMS[b][0])
+        sim.set_wall_tangents(dwall)
+        sim.add_particle(**wl.particles[0].kwargs(), tangent=seed)
+        sim.step(steps)
+        p, t = sim.particles()[0], sim.particle_tangents()[0]
+        sim.close()
+        iy, iw = lbib.TANGENT_FIELDS.index("yc"), lbib.TANGENT_FIELDS.index("omega_sum")
+        assert vals[b, 0] == p["yc"] and vals[b, 1] == p["omega_sum"] / steps
+        assert np.array_equal(J[b, 0], t[:, iy]) and np.array_equal(J[b, 1], t[:, iw] / steps)
