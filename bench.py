@@ -382,8 +382,9 @@ def main():
             "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": 1,
             "steps": steps, "warmup": args.warmup, "ms_per_step": dt / steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": wl.name, "nx": wl.nx, "ny": wl.ny,
-                                            "particles": len(wl.particles)},
+            "data": "synthetic", "config": {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "tau": wl.tau,
+                                            "particles": len(wl.particles),
+                                            "precision": "fp64 oracle (populations and particle work)"},
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                              "sample": f"{steps} full-lattice steps after {args.warmup} warm-up"},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
