@@ -289,9 +289,9 @@ lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v, bool
     fa.insts = ctx->insts;
     fa.tasks = ctx->tasks[v];
     fa.ntasks = ctx->ntasks[v];
-    // one CTA per tile: the block scheduler keeps every SM filled as tiles
-    // finish (the kernel's task loop then runs once per CTA)
-    const int grid = std::max(1, fa.ntasks);
+    // one CTA per TASKS_PER_CTA tiles: the block scheduler keeps every SM
+    // filled as CTAs finish (the kernel's outer task loop then runs once)
+    const int grid = std::max(1, (fa.ntasks + TASKS_PER_CTA - 1) / TASKS_PER_CTA);
     CK(launch_fluid(ctx->prec, v, fa, ctx->ninst == 1 ? &ctx->hinst[0] : nullptr, grid, st, pdl));
     return LBM_OK;
 }

@@ -249,13 +249,17 @@ template <class S, int N, int BYt> struct FluidOccupancy {
         (sizeof(S) == 16 ? 2 : (N == 1 ? (sizeof(S) == 8 ? 3 : 5) : (sizeof(S) == 8 ? 2 : 4))) * 8 / BYt;
 };
 
-// persistent fused fluid step over the task list (all instances)
+// fused fluid step over the task list (all instances): CTA b takes the
+// TASKS_PER_CTA consecutive tasks from b * TASKS_PER_CTA (mostly tiles of one
+// lattice, whose task records and descriptor then come from L1 after the
+// first), and further ones a grid apart if the grid is smaller
 template <class S, class C, int N, int BYt>
 __global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value) k_fluid(FluidArgs a) {
     const S* fin = static_cast<const S*>(a.fin);
     S* fout = static_cast<S*>(a.fout);
     C* flb = static_cast<C*>(a.flb);
-    for (int t = blockIdx.x; t < a.ntasks; t += gridDim.x) {
+    for (int t0 = blockIdx.x * TASKS_PER_CTA; t0 < a.ntasks; t0 += gridDim.x * TASKS_PER_CTA)
+    for (int t = t0; t < min(t0 + TASKS_PER_CTA, a.ntasks); ++t) {
         const int4 task = a.tasks[t];
         const Inst& I = a.insts[task.x];
         fluid_tile<S, C, N, false>(I.G, fin + I.f_off, fout + I.f_off, flb + I.flb_off,

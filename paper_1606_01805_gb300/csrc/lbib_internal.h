@@ -135,6 +135,8 @@ struct FluidArgs {
     int ntasks;
 };
 
+constexpr int TASKS_PER_CTA = 4;  // consecutive tiles a CTA of the task-list kernel takes
+
 // fluid tile shapes: (cells per thread, rows per block); the autotuner picks one
 constexpr int N_FLUID_VARIANTS = LBM_TILE_VARIANTS;
 struct FluidVariant {
