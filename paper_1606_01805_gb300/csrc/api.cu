@@ -37,12 +37,13 @@ struct lbm_ctx {
     int sms = 1;
     size_t rsz, psz;                // bytes of the particle real type R / of DParticleT<R>
     char* parts;                    // two state buffers of cap_particles DParticleT<R> each
+    char* poses;                    // two buffers of cap_particles PoseC<C> each (beside parts)
+    size_t pcsz;                    // bytes of PoseC<C>
     int4* blk;
     void* partial;                  // R[3][blocks]
     unsigned* count;
-    void* rb;                       // Vec2<R>[markers]
-    void* nb;                       // Vec2<R>[markers]
-    void* S;                        // R[markers]
+    void* mg;                       // MGeo<C>[markers]
+    void* S;                        // C[markers]
     void* recs;
     int4* boxes;
     int4* ptab;                     // device copy of hpart
@@ -140,7 +141,7 @@ std::vector<int4> make_tasks(const std::vector<Inst>& insts, int v) {
 
 struct Layout {
     std::vector<Inst> insts;
-    size_t f0, f1, flb, flags, insts_off, tasks[N_FLUID_VARIANTS], parts, blk, partial, count, rb, nb,
+    size_t f0, f1, flb, flags, insts_off, tasks[N_FLUID_VARIANTS], parts, poses, blk, partial, count, mg,
         S, recs, boxes, ptab, err, scratch, total;
     int ntasks[N_FLUID_VARIANTS];
     int scratch_rows;
@@ -182,12 +183,12 @@ Layout layout(const lbm_config* cfgs, int n) {
         o = up(o + (size_t)L.ntasks[v] * sizeof(int4));
     }
     L.parts = o; o = up(o + 2 * P * particle_bytes(prec));
+    L.poses = o; o = up(o + 2 * P * pose_bytes(prec));
     L.blk = o; o = up(o + NB * sizeof(int4));
     L.partial = o; o = up(o + 3 * NB * R);
     L.count = o; o = up(o + P * sizeof(unsigned));
-    L.rb = o; o = up(o + M * 2 * R);
-    L.nb = o; o = up(o + M * 2 * R);
-    L.S = o; o = up(o + M * R);
+    L.mg = o; o = up(o + M * 4 * compute_bytes(prec));
+    L.S = o; o = up(o + M * compute_bytes(prec));
     L.recs = o; o = up(o + M * rec_bytes(prec));
     L.boxes = o; o = up(o + P * sizeof(int4));
     L.ptab = o; o = up(o + P * sizeof(int4));
@@ -224,9 +225,12 @@ lbm_status device_error(lbm_ctx* ctx) {
 
 constexpr int GRAPH_STEPS = 32;  // even, so a replay returns to the same buffer
 
-// particle state buffer `buf` (0 or 1)
+// particle state buffer `buf` (0 or 1), and its pose in the compute type
 char* state(const lbm_ctx* ctx, int buf) {
     return ctx->parts + (size_t)buf * cap_particles(ctx->cfg) * ctx->psz;
+}
+char* pose(const lbm_ctx* ctx, int buf) {
+    return ctx->poses + (size_t)buf * cap_particles(ctx->cfg) * ctx->pcsz;
 }
 
 ParticleArgs particle_args(lbm_ctx* ctx, int cur) {
@@ -235,11 +239,12 @@ ParticleArgs particle_args(lbm_ctx* ctx, int cur) {
     pa.insts = ctx->insts;
     pa.pin = state(ctx, cur);
     pa.pout = state(ctx, cur ^ 1);
+    pa.pcin = pose(ctx, cur);
+    pa.pcout = pose(ctx, cur ^ 1);
     pa.blk = ctx->blk;
     pa.partial = ctx->partial;
     pa.count = ctx->count;
-    pa.rb = ctx->rb;
-    pa.nb = ctx->nb;
+    pa.mg = ctx->mg;
     pa.S = ctx->S;
     pa.recs = ctx->recs;
     pa.boxes = ctx->boxes;
@@ -465,11 +470,12 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
     ctx->rsz = real_bytes(ctx->prec);
     ctx->psz = particle_bytes(ctx->prec);
     ctx->parts = b + L.parts;
+    ctx->pcsz = pose_bytes(ctx->prec);
+    ctx->poses = b + L.poses;
     ctx->blk = reinterpret_cast<int4*>(b + L.blk);
     ctx->partial = b + L.partial;
     ctx->count = reinterpret_cast<unsigned*>(b + L.count);
-    ctx->rb = b + L.rb;
-    ctx->nb = b + L.nb;
+    ctx->mg = b + L.mg;
     ctx->S = b + L.S;
     ctx->recs = b + L.recs;
     ctx->boxes = reinterpret_cast<int4*>(b + L.boxes);
@@ -516,7 +522,7 @@ template <> TD seeded<TD>(double v, const double* seed, int j) {
     return r;
 }
 
-template <class R>
+template <class R, class C>
 lbm_status add_particle_t(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, const double* seed,
                           int32_t* out_id) {
     using std::cos;
@@ -576,17 +582,38 @@ lbm_status add_particle_t(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, co
     std::vector<int4> blocks(P.nblk);
     for (int k = 0; k < P.nblk; ++k)
         blocks[k] = make_int4(ctx->np, P.m0 + k * MB, std::min(MB, n - k * MB), inst);
-    const size_t v2 = sizeof(Vec2<R>);
-    static_assert(sizeof(Vec2<R>) == 2 * sizeof(R), "marker arrays are packed pairs");
-    CK(cudaMemcpyAsync(static_cast<char*>(ctx->rb) + P.m0 * v2, rb.data(), n * v2, cudaMemcpyHostToDevice,
-                       ctx->stream));
-    CK(cudaMemcpyAsync(static_cast<char*>(ctx->nb) + P.m0 * v2, nb.data(), n * v2, cudaMemcpyHostToDevice,
-                       ctx->stream));
-    CK(cudaMemcpyAsync(static_cast<char*>(ctx->S) + P.m0 * sizeof(R), S.data(), n * sizeof(R),
+    // the marker kernels' geometry in the compute type C
+    static_assert(sizeof(MGeo<C>) == 4 * sizeof(C), "marker geometry is packed");
+    std::vector<MGeo<C>> mg(n);
+    std::vector<C> Sc(n);
+    for (int l = 0; l < n; ++l) {
+        mg[l] = MGeo<C>{C(rb[2 * l]), C(rb[2 * l + 1]), C(nb[2 * l]), C(nb[2 * l + 1])};
+        Sc[l] = C(S[l]);
+    }
+    // the initial pose in C (both stored levels equal: no changes)
+    PoseC<C> pc;
+    std::memset(&pc, 0, sizeof pc);
+    const double fx = std::floor(value_of(xc)), fy = std::floor(value_of(yc));
+    pc.ix = (int)fx;
+    pc.iy = (int)fy;
+    pc.v[PC_XF] = C(xc - R(fx));
+    pc.v[PC_YF] = C(yc - R(fy));
+    pc.v[PC_C] = C(c);
+    pc.v[PC_S] = C(s);
+    pc.v[PC_U] = C(R(d->u0[0]));
+    pc.v[PC_V] = C(R(d->u0[1]));
+    pc.v[PC_W] = pc.v[PC_W1] = C(R(d->omega0));
+    pc.v[PC_DU] = pc.v[PC_DV] = pc.v[PC_DW] = pc.v[PC_DC] = pc.v[PC_DS] = C(0.0f);
+    CK(cudaMemcpyAsync(static_cast<MGeo<C>*>(ctx->mg) + P.m0, mg.data(), n * sizeof(MGeo<C>),
                        cudaMemcpyHostToDevice, ctx->stream));
-    for (int buf = 0; buf < 2; ++buf)
+    CK(cudaMemcpyAsync(static_cast<C*>(ctx->S) + P.m0, Sc.data(), n * sizeof(C), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    for (int buf = 0; buf < 2; ++buf) {
         CK(cudaMemcpyAsync(state(ctx, buf) + (size_t)ctx->np * sizeof P, &P, sizeof P, cudaMemcpyHostToDevice,
                            ctx->stream));
+        CK(cudaMemcpyAsync(pose(ctx, buf) + (size_t)ctx->np * sizeof pc, &pc, sizeof pc,
+                           cudaMemcpyHostToDevice, ctx->stream));
+    }
     CK(cudaMemcpyAsync(ctx->blk + P.b0, blocks.data(), P.nblk * sizeof(int4), cudaMemcpyHostToDevice,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -617,8 +644,9 @@ lbm_status add_particle(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, cons
         return fail(ctx, LBM_EINVAL, "shape needs two dimensions");
     if (seed && ctx->prec != LBM_FP32_TANGENT)
         return fail(ctx, LBM_EINVAL, "tangent seeds need the LBM_FP32_TANGENT precision");
-    if (ctx->prec == LBM_FP32_TANGENT) return add_particle_t<TD>(ctx, inst, d, seed, out_id);
-    return add_particle_t<double>(ctx, inst, d, nullptr, out_id);
+    if (ctx->prec == LBM_FP32_TANGENT) return add_particle_t<TD, TF>(ctx, inst, d, seed, out_id);
+    if (ctx->prec == LBM_FP64) return add_particle_t<double, double>(ctx, inst, d, nullptr, out_id);
+    return add_particle_t<double, float>(ctx, inst, d, nullptr, out_id);
 }
 
 lbm_status get_fields(lbm_ctx* ctx, int inst, double* rho, double* ux, double* uy,

@@ -205,6 +205,7 @@ LBIB_HD T floor_value(const Dual<T, K>& a) {
 }
 
 LBIB_HD double floor_value(double a) { return std::floor(a); }
+LBIB_HD float floor_value(float a) { return std::floor(a); }
 
 template <class X> struct DualTraits {
     using value = X;

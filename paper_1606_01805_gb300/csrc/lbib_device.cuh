@@ -293,52 +293,4 @@ __device__ __forceinline__ W mls_weight(int kind, W r) {
     }
 }
 
-// MLS operator at (px, py) over the 3x3 nodes around the nearest node:
-// phi (Eq. 8 weights) and, if D, the weights of the two linear
-// coefficients (the x and y derivatives of the fit).  Linear basis in
-// coordinates relative to the point; the weights are evaluated in precision
-// W, the 3x3 moment matrix A = sum W p p^T is accumulated and inverted (by
-// its adjugate) in FP64.  (i0, j0) = lower-left node.
-template <bool D, class Wt>
-__device__ __forceinline__ void mls(int kind, double px, double py, int& i0, int& j0, Wt phi[9],
-                                    Wt dphx[9], Wt dphy[9]) {
-    const int ic = (int)floor(px + 0.5), jc = (int)floor(py + 0.5);
-    i0 = ic - 1;
-    j0 = jc - 1;
-    Wt W[9], DX[9], DY[9];
-    double a00 = 0, a01 = 0, a02 = 0, a11 = 0, a12 = 0, a22 = 0;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const double dx = (double)(i0 + k % 3) - px, dy = (double)(j0 + k / 3) - py;
-        const Wt dxw = (Wt)dx, dyw = (Wt)dy;
-        const Wt ww = mls_weight<Wt>(kind, sqrt(dxw * dxw + dyw * dyw) * Wt(1.0 / 2.6));
-        const double w = (double)ww;
-        W[k] = ww;
-        DX[k] = dxw;
-        DY[k] = dyw;
-        a00 += w;
-        a01 += w * dx;
-        a02 += w * dy;
-        a11 += w * dx * dx;
-        a12 += w * dx * dy;
-        a22 += w * dy * dy;
-    }
-    // adjugate of the symmetric matrix (FP64)
-    const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
-    const double det = a00 * c00 + a01 * c01 + a02 * c02;
-    const double id = 1.0 / det;
-    const Wt i00 = (Wt)(c00 * id), i01 = (Wt)(c01 * id), i02 = (Wt)(c02 * id);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) phi[k] = W[k] * (i00 + i01 * DX[k] + i02 * DY[k]);
-    if (D) {
-        const Wt i11 = (Wt)((a00 * a22 - a02 * a02) * id), i12 = (Wt)((a01 * a02 - a00 * a12) * id);
-        const Wt i22 = (Wt)((a00 * a11 - a01 * a01) * id);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            dphx[k] = W[k] * (i01 + i11 * DX[k] + i12 * DY[k]);
-            dphy[k] = W[k] * (i02 + i12 * DX[k] + i22 * DY[k]);
-        }
-    }
-}
-
 }  // namespace lbib

@@ -67,6 +67,27 @@ struct DParticleT {
 };
 using DParticle = DParticleT<double>;
 
+// Pose and velocities of a particle in the compute type C, written beside
+// DParticleT by the FP64 rigid-body update (and when the particle is added)
+// and double-buffered with it.  The marker kernels form marker and probe
+// positions in C relative to the node (ix, iy) at or below the centre, so
+// none of their geometry needs FP64.  v[]: centre minus (ix, iy); cos, sin
+// of the angle; u, v, omega; the changes of u, v, omega, cos, sin from the
+// previous level, and that level's omega (the marker acceleration of the
+// probe pressure).
+enum { PC_XF, PC_YF, PC_C, PC_S, PC_U, PC_V, PC_W, PC_DU, PC_DV, PC_DW, PC_W1, PC_DC, PC_DS, PC_N };
+template <class C>
+struct __align__(16) PoseC {
+    int ix, iy, pad_[2];
+    C v[PC_N];
+};
+
+// Body-frame position and outward normal of one marker, in C.
+template <class C>
+struct __align__(16) MGeo {
+    C rx, ry, nx, ny;
+};
+
 constexpr int MB = 8;         // markers per block of the marker kernels (one warp, 4 lanes each)
 constexpr int INLINE_BLOCKS = 128, INLINE_PARTICLES = 64;
 
@@ -84,18 +105,20 @@ enum : unsigned { ERR_DOMAIN = 1u, ERR_NONFINITE = 2u, ERR_TIMEOUT = 4u };
 // The particle state is double-buffered with the populations: a step that
 // reads populations buffer c reads particles pin = state[c] and writes the
 // updated bodies to pout = state[c ^ 1].
-// Arrays of the real type R are passed untyped (the kernel's R decides).
+// Arrays of the real type R and of the compute type C are passed untyped
+// (the kernel's R and C decide).
 struct ParticleArgs {
     const void* f;            // post-collision populations buffer (storage type)
     const Inst* insts;
     const void* pin;          // DParticleT<R>: bodies at the start of the step
     void* pout;               // DParticleT<R>: bodies after the rigid-body update
+    const void* pcin;         // PoseC<C> of pin
+    void* pcout;              // PoseC<C> of pout
     const int4* blk;          // per marker block: (particle, first marker, markers, instance)
     void* partial;            // R per marker block: F_x, F_y, M partial sums
     unsigned* count;          // per particle: probe blocks done (the last one resets it)
-    const void* rb;           // Vec2<R>: body-frame marker positions
-    const void* nb;           // Vec2<R>: body-frame normals
-    const void* S;            // R: marker arc lengths
+    const void* mg;           // MGeo<C>: body-frame marker positions and normals
+    const void* S;            // C: marker arc lengths
     void* recs;               // Rec<C>[max_markers]
     int4* boxes;              // per particle: support box (x0, y0, x1, y1)
     unsigned* err;
@@ -170,6 +193,7 @@ size_t compute_bytes(int prec);
 size_t rec_bytes(int prec);
 size_t real_bytes(int prec);      // the particle real type R
 size_t particle_bytes(int prec);  // sizeof(DParticleT<R>)
+size_t pose_bytes(int prec);      // sizeof(PoseC<C>)
 
 // shapes.cpp: body-frame markers and rigid-body properties of a shape, in
 // double or, with derivatives of the dimensions, in TD

@@ -9,7 +9,8 @@
 //   The last block of a particle to finish (a completion counter; nothing
 //   waits) adds the block sums (fixed lane assignment and shuffle tree, so
 //   deterministic) and applies the two-level rigid-body update (Eqs. 15-16,
-//   FP64), once per particle, into the other state buffer.
+//   FP64), once per particle, into the other state buffer, with the new
+//   pose in the compute type C (PoseC) beside it.
 // k_markers: the markers at the new level: MLS interpolation (Eq. 8),
 //   direct-forcing force (Eq. 11), the per-marker spreading record
 //   S_l phi_k F_l of Eq. 12 and the particle's support box.
@@ -18,6 +19,9 @@
 //   then adds the particle's sum into f_lb (the only atomic: one add per
 //   cell and particle, contended only where particles overlap) and flags the
 //   32-cell row segments the fluid kernel must read.
+// Marker and probe geometry runs in C, relative to the node at or below
+// the particle's centre; FP64 (the type R) is kept for the 3x3 MLS solve,
+// the force/torque sums and the rigid-body update.
 // Each kernel is a template on the population storage type S, the compute
 // type C and the particle real type R: (double, double, double) in FP64,
 // (float or half, float, double) in FP32 / FP16, and in the tangent mode
@@ -71,35 +75,40 @@ __device__ __forceinline__ T quad_sum(T v) {  // sum over the 4 lanes of a marke
 
 // The MLS operator of Eqs. 8-10 split over the 4 lanes of a marker: lane q
 // holds support nodes k = q, q + 4, q + 8 (k < 9) of the 3x3 block around
-// the nearest node of (px, py).  Weights and the moment matrix
-// A = sum W p p^T in precision C (reduced across the lanes); A is inverted
-// (adjugate) in the particle type R.  On return the lane has, for its
-// nodes, the first (phi) and, if D, second/third rows of A^-1 [W p].
+// the nearest node of the point.  The point is given in C relative to a
+// reference node (ix, iy) of the particle (lx, ly: under the particle's
+// size plus two cells).  Weights and the moment matrix A = sum W p p^T in
+// precision C (reduced across the lanes); A is inverted (adjugate) in the
+// particle type R.  On return the lane has, for its nodes, the first (phi)
+// and, if D, second/third rows of A^-1 [W p].
 template <bool D, class C, class R>
 struct QuadMLS {
     int i0, j0;      // lower-left node of the support
+    int li, lj;      // the same relative to the reference node
     int nk;          // nodes held by this lane (3 or 2)
     int kk[3];
     C phi[3], dpx[3], dpy[3];
 
-    // support of (px, py) and the nodes of lane q; the choice of support is
-    // piecewise constant in the position and carries no derivative
-    __device__ __forceinline__ void support(const R& px, const R& py, int q) {
-        i0 = (int)floor_value(px + 0.5) - 1;
-        j0 = (int)floor_value(py + 0.5) - 1;
+    // support of (ix + lx, iy + ly) and the nodes of lane q; the choice of
+    // support is piecewise constant in the position and carries no derivative
+    __device__ __forceinline__ void support(int ix, int iy, const C& lx, const C& ly, int q) {
+        li = (int)floor_value(lx + C(0.5)) - 1;
+        lj = (int)floor_value(ly + C(0.5)) - 1;
+        i0 = ix + li;
+        j0 = iy + lj;
         nk = q == 0 ? 3 : 2;
 #pragma unroll
         for (int j = 0; j < 3; ++j) kk[j] = q + 4 * j;
     }
 
     // weights and moment matrix in precision C, the 3x3 solve in R
-    // (after support())
-    __device__ __forceinline__ void build(int kind, const R& px, const R& py, bool active) {
+    // (after support(), the same lx, ly)
+    __device__ __forceinline__ void build(int kind, const C& lx, const C& ly, bool active) {
         C W[3], DX[3], DY[3];
         C b00 = C(0), b01 = C(0), b02 = C(0), b11 = C(0), b12 = C(0), b22 = C(0);
-        // offset from the support's lower-left node in R (one conversion),
-        // the steps to the other nodes added in C
-        const C ox = (C)(R((double)i0) - px), oy = (C)(R((double)j0) - py);
+        // offsets from the support's lower-left node (a small integer
+        // minus the point: no rounding beyond that of lx, ly)
+        const C ox = C(li) - lx, oy = C(lj) - ly;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int k = kk[j];
@@ -223,6 +232,32 @@ __device__ __forceinline__ Body<R> update_body(const DParticleT<R>* P, const R* 
     return B;
 }
 
+// The pose of the updated body B in C (PoseC), over the lanes: lane k
+// forms entry k as hi - lo in R (lo: the node at or below the centre, or
+// the previous level's value for a change) and converts it once, so the
+// whole conversion is a few FP64 warp instructions.
+template <class C, class R>
+__device__ __forceinline__ void publish_pose(PoseC<C>* out, const Body<R>& B, const DParticleT<R>* P,
+                                             int lane) {
+    const R zero = R(0.0);
+    const R hi[PC_N] = {B.X, B.Y, B.c, B.s, B.U, B.V, B.W, B.U, B.V, B.W, P->W[0], B.c, B.s};
+    const R lo[PC_N] = {zero, zero, zero, zero, zero, zero, zero,
+                        P->U[0][0], P->U[0][1], P->W[0], zero, P->cs[0][0], P->cs[0][1]};
+    R h = zero, l = zero;
+#pragma unroll
+    for (int k = 0; k < PC_N; ++k)
+        if (lane == k) {
+            h = hi[k];
+            l = lo[k];
+        }
+    const double fl = floor(value_of(h));  // used by lanes PC_XF, PC_YF
+    if (lane == PC_XF || lane == PC_YF) {
+        l = R(fl);
+        (&out->ix)[lane - PC_XF] = (int)fl;
+    }
+    if (lane < PC_N) out->v[lane] = (C)(h - l);
+}
+
 // The lattice of a marker block or particle: for a context of one lattice
 // its descriptor travels in the kernel parameters (ONE), else it is loaded.
 template <bool ONE, class A>
@@ -244,18 +279,17 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     const int ml = lane / LPM, m = bk.y + ml;  // marker (absolute index)
     const bool active = ml < bk.z;
     unsigned err = 0;
-    // body at its latest level (written by this kernel a step ago)
-    const R c0 = P->cs[0][0], s0 = P->cs[0][1];
-    Vec2<R> rb{R(0.0), R(0.0)}, nb{R(1.0), R(0.0)};
-    if (active) {
-        rb = static_cast<const Vec2<R>*>(a.rb)[m];
-        nb = static_cast<const Vec2<R>*>(a.nb)[m];
-    }
-    const R rx = c0 * rb.x - s0 * rb.y, ry = s0 * rb.x + c0 * rb.y;  // x_l - X_c
-    const R nx = c0 * nb.x - s0 * nb.y, ny = s0 * nb.x + c0 * nb.y;
-    const R px = P->X[0][0] + rx + PROBE * nx, py = P->X[0][1] + ry + PROBE * ny;
+    // body at its latest level (written by this kernel a step ago), in C
+    const PoseC<C>& pc = static_cast<const PoseC<C>*>(a.pcin)[bk.x];
+    MGeo<C> g{C(0), C(0), C(1), C(0)};
+    if (active) g = static_cast<const MGeo<C>*>(a.mg)[m];
+    const C c0 = pc.v[PC_C], s0 = pc.v[PC_S];
+    const C rx = c0 * g.rx - s0 * g.ry, ry = s0 * g.rx + c0 * g.ry;  // x_l - X_c
+    const C nx = c0 * g.nx - s0 * g.ny, ny = s0 * g.nx + c0 * g.ny;
+    // the probe x_l + 1.2 n_l relative to the node (ix, iy)
+    const C lx = pc.v[PC_XF] + rx + C(PROBE) * nx, ly = pc.v[PC_YF] + ry + C(PROBE) * ny;
     QuadMLS<true, C, R> M;
-    M.support(px, py, q);
+    M.support(pc.ix, pc.iy, lx, ly, q);
     pdl_wait();  // the populations come from the fluid kernel before this one
     pdl_trigger();
     if (lane == 0 && bk.y == P->m0)  // the particle's first block resets its box
@@ -273,7 +307,7 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
             }
         }
     }
-    M.build(a.weight, px, py, active);
+    M.build(a.weight, lx, ly, active);
     // MLS fit of rho and grad u at the probe (Section 2.3)
     C r = C(0), uxx = C(0), uxy = C(0), uyx = C(0), uyy = C(0);
 #pragma unroll
@@ -289,21 +323,23 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     r = quad_sum(r); uxx = quad_sum(uxx); uxy = quad_sum(uxy); uyx = quad_sum(uyx); uyy = quad_sum(uyy);
     R Fx = R(0.0), Fy = R(0.0), Mz = R(0.0);
     if (active && q == 0) {
-        // change of the marker's rigid velocity between the two stored levels
-        const R c1 = P->cs[1][0], s1 = P->cs[1][1];
-        const R r1x = c1 * rb.x - s1 * rb.y, r1y = s1 * rb.x + c1 * rb.y;
-        const C dvx = (C)((P->U[0][0] - P->W[0] * ry) - (P->U[1][0] - P->W[1] * r1y));
-        const C dvy = (C)((P->U[0][1] + P->W[0] * rx) - (P->U[1][1] + P->W[1] * r1x));
-        const C cnx = (C)nx, cny = (C)ny;
-        const C p = C(CS2) * (r - C(1)) + r * C(PROBE) * (dvx * cnx + dvy * cny);
+        // change of the marker's rigid velocity u + omega z x r between the
+        // two stored levels, from the changes of u, omega and r (r - r1 =
+        // (R(th) - R(th1)) r_b), free of cancellation
+        const C dc = pc.v[PC_DC], ds = pc.v[PC_DS], dw = pc.v[PC_DW], w1 = pc.v[PC_W1];
+        const C drx = dc * g.rx - ds * g.ry, dry = ds * g.rx + dc * g.ry;
+        const C dvx = pc.v[PC_DU] - (dw * ry + w1 * dry);
+        const C dvy = pc.v[PC_DV] + (dw * rx + w1 * drx);
+        const C p = C(CS2) * (r - C(1)) + r * C(PROBE) * (dvx * nx + dvy * ny);
         const C mu = r * C(CS2 * (G.tau - 0.5));
         const C txx = C(2) * mu * uxx, tyy = C(2) * mu * uyy, txy = mu * (uxy + uyx);
-        const R tx = (R)(txx * cnx + txy * cny - p * cnx);
-        const R ty = (R)(txy * cnx + tyy * cny - p * cny);
-        const R Sl = static_cast<const R*>(a.S)[m];
-        Fx = tx * Sl;
-        Fy = ty * Sl;
-        Mz = (rx * ty - ry * tx) * Sl;
+        const C tx = txx * nx + txy * ny - p * nx;
+        const C ty = txy * nx + tyy * ny - p * ny;
+        const C Sl = static_cast<const C*>(a.S)[m];
+        // the marker's force and torque in C, their sums (Eqs. 13-14) in R
+        Fx = (R)(tx * Sl);
+        Fy = (R)(ty * Sl);
+        Mz = (R)((rx * ty - ry * tx) * Sl);
     }
     // only the quad leaders (lanes 0, 4, ..., 28) hold a contribution
 #pragma unroll
@@ -326,6 +362,7 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     if (done != (unsigned)P->nblk - 1) return;  // not the last block (whole warp)
     __threadfence();
     const Body<R> B = update_body<R>(P, partial, G.grav, lane);
+    publish_pose<C, R>(static_cast<PoseC<C>*>(a.pcout) + bk.x, B, P, lane);
     if (lane == 0) {
         DParticleT<R>* Q = static_cast<DParticleT<R>*>(a.pout) + bk.x;
         *Q = *P;
@@ -347,7 +384,7 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
 template <class S, class C, class R, bool ONE>
 __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
     const int4 bk = a.nblk_inline ? a.blk_inline[blockIdx.x] : a.blk[blockIdx.x];
-    const DParticleT<R>* Q = static_cast<const DParticleT<R>*>(a.pout) + bk.x;  // after the update
+    const PoseC<C>* Q = static_cast<const PoseC<C>*>(a.pcout) + bk.x;  // after the update, in C
     const Inst& I = inst_of<ONE>(a, bk.w);
     const Geo& G = I.G;
     const Geo* Gg = &a.insts[ONE ? 0 : bk.w].G;
@@ -357,16 +394,16 @@ __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
     const int ml = lane / LPM, m = bk.y + ml;  // marker (absolute index)
     const bool active = ml < bk.z;
     unsigned err = 0;
-    Vec2<R> rb{R(0.0), R(0.0)};
-    if (active) rb = static_cast<const Vec2<R>*>(a.rb)[m];
+    MGeo<C> g{C(0), C(0), C(1), C(0)};
+    if (active) g = static_cast<const MGeo<C>*>(a.mg)[m];
     pdl_wait();  // the updated body comes from the probe kernel
     pdl_trigger();
-    const R X = Q->X[0][0], Y = Q->X[0][1], cn = Q->cs[0][0], sn = Q->cs[0][1];
-    const R BU = Q->U[0][0], BV = Q->U[0][1], BW = Q->W[0];
-    const R rx = cn * rb.x - sn * rb.y, ry = sn * rb.x + cn * rb.y;
-    const R mx = X + rx, my = Y + ry;
+    const C cn = Q->v[PC_C], sn = Q->v[PC_S];
+    const C BU = Q->v[PC_U], BV = Q->v[PC_V], BW = Q->v[PC_W];
+    const C rx = cn * g.rx - sn * g.ry, ry = sn * g.rx + cn * g.ry;
+    const C lx = Q->v[PC_XF] + rx, ly = Q->v[PC_YF] + ry;  // relative to (ix, iy)
     QuadMLS<false, C, R> M;
-    M.support(mx, my, q);
+    M.support(Q->ix, Q->iy, lx, ly, q);
     C uk[3], vk[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -380,7 +417,7 @@ __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
             }
         }
     }
-    M.build(a.weight, mx, my, active);
+    M.build(a.weight, lx, ly, active);
     C ux = C(0), uy = C(0);
 #pragma unroll
     for (int j = 0; j < 3; ++j)
@@ -393,9 +430,9 @@ __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
     int bx0 = INT_MAX, by0 = INT_MAX, bx1 = INT_MIN, by1 = INT_MIN;
     if (active) {
         // Eq. 11 with dt = 1, times the arc length c_l = S_l of Eq. 12
-        const R Sl = static_cast<const R*>(a.S)[m];
-        const C sx = (C)(Sl * ((BU - BW * ry) - (R)ux));
-        const C sy = (C)(Sl * ((BV + BW * rx) - (R)uy));
+        const C Sl = static_cast<const C*>(a.S)[m];
+        const C sx = Sl * ((BU - BW * ry) - ux);
+        const C sy = Sl * ((BV + BW * rx) - uy);
         Rec<C>* rc = recs + m;
 #pragma unroll
         for (int j = 0; j < 3; ++j)
@@ -529,6 +566,11 @@ size_t rec_bytes(int prec) {
 size_t real_bytes(int prec) { return prec == LBM_FP32_TANGENT ? sizeof(TD) : sizeof(double); }
 size_t particle_bytes(int prec) {
     return prec == LBM_FP32_TANGENT ? sizeof(DParticleT<TD>) : sizeof(DParticleT<double>);
+}
+size_t pose_bytes(int prec) {
+    if (prec == LBM_FP64) return sizeof(PoseC<double>);
+    if (prec == LBM_FP32_TANGENT) return sizeof(PoseC<TF>);
+    return sizeof(PoseC<float>);
 }
 
 // every IB kernel is launched with programmatic stream serialization: its
