@@ -161,33 +161,29 @@ struct Body {
 template <class R>
 __device__ __forceinline__ Body<R> update_body(const DParticleT<R>* P, const R* partial,
                                                const double gravity[2], int lane) {
-    // lane l adds the sums of blocks l, l + 32, l + 64, ... in that order;
-    // the loads of four of them are issued together (L2: other blocks wrote them)
-    R F0 = R(0.0), F1 = R(0.0), Mt = R(0.0);
+    // lane l sums component j = l % 4 (< 3) of the blocks g, g + 8, g + 16,
+    // ... (g = l / 4) in that order, eight loads issued together (L2: other
+    // blocks wrote them); a butterfly over the 8 groups then leaves every
+    // group with the totals, so one FP64 add per block and tree level
+    // serves all three components
+    const int j = lane & 3, g = lane >> 2;
     const int b0 = P->b0, nb = P->nblk;
-    for (int base = 0; base < nb; base += 128) {
-        R q[4][3];
+    R acc = R(0.0);
+    for (int base = 0; base < nb; base += 64) {
+        R q[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int b = base + 32 * u + lane;
-            const R* pb = partial + 3 * (long long)(b0 + b);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) q[u][j] = b < nb ? ldcg_r(pb + j) : R(0.0);
+        for (int u = 0; u < 8; ++u) {
+            const int b = base + 8 * u + g;
+            q[u] = j < 3 && b < nb ? ldcg_r(partial + 3 * (long long)(b0 + b) + j) : R(0.0);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (base + 32 * u + lane < nb) {
-                F0 += q[u][0];
-                F1 += q[u][1];
-                Mt += q[u][2];
-            }
+        for (int u = 0; u < 8; ++u)
+            if (base + 8 * u + g < nb) acc += q[u];
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {  // butterfly: every lane ends with the total
-        F0 += __shfl_xor_sync(0xffffffffu, F0, o);
-        F1 += __shfl_xor_sync(0xffffffffu, F1, o);
-        Mt += __shfl_xor_sync(0xffffffffu, Mt, o);
-    }
+    for (int o = 4; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const R F0 = __shfl_sync(0xffffffffu, acc, 0), F1 = __shfl_sync(0xffffffffu, acc, 1);
+    const R Mt = __shfl_sync(0xffffffffu, acc, 2);
     const R X0 = P->X[0][0], Y0 = P->X[0][1], th0 = P->th[0];
     const R U0 = P->U[0][0], V0 = P->U[0][1], W0 = P->W[0];
     const R buoy = (P->rho_s - 1.0) * P->area;
@@ -212,11 +208,20 @@ __device__ __forceinline__ Body<R> update_body(const DParticleT<R>* P, const R* 
         B.T = k * (2.0 * th0 - 0.5 * P->th[1] + B.W);
     }
     // (cos, sin) of the new angle: the stored pair of the old one turned by
-    // the increment d, with cos d and sin d from their Taylor series (to
-    // d^8 / d^9, below 1e-26 for |d| < 1e-2: exact in FP64); a larger
-    // increment takes sincos
+    // the increment d, with cos d and sin d from their Taylor series: for
+    // |d| < 1e-4 to d^4 / d^3 (the next terms below 1.4e-27 and 8.3e-19 |d|),
+    // for |d| < 1e-2 to d^8 / d^9 (below 1e-26), both far under half an
+    // FP64 ulp; a larger increment takes sincos
     const R d = B.T - th0;
-    if (fabs(value_of(d)) < 1e-2) {
+    const double ad = fabs(value_of(d));
+    if (ad < 1e-4) {
+        const R d2 = d * d;
+        const R cd = 1.0 + d2 * (-1.0 / 2 + d2 * (1.0 / 24));
+        const R sd = d + (d * d2) * (-1.0 / 6);
+        const R c0 = P->cs[0][0], s0 = P->cs[0][1];
+        B.c = c0 * cd - s0 * sd;
+        B.s = s0 * cd + c0 * sd;
+    } else if (ad < 1e-2) {
         const R d2 = d * d;
         const R cd = 1.0 + d2 * (-1.0 / 2 + d2 * (1.0 / 24 + d2 * (-1.0 / 720 + d2 * (1.0 / 40320))));
         const R sd = d * (1.0 + d2 * (-1.0 / 6 + d2 * (1.0 / 120 + d2 * (-1.0 / 5040 + d2 * (1.0 / 362880)))));
@@ -321,7 +326,7 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
         }
     }
     r = quad_sum(r); uxx = quad_sum(uxx); uxy = quad_sum(uxy); uyx = quad_sum(uyx); uyy = quad_sum(uyy);
-    R Fx = R(0.0), Fy = R(0.0), Mz = R(0.0);
+    C cF[3] = {C(0), C(0), C(0)};  // this marker's force and torque (quad leader)
     if (active && q == 0) {
         // change of the marker's rigid velocity u + omega z x r between the
         // two stored levels, from the changes of u, omega and r (r - r1 =
@@ -337,22 +342,29 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
         const C ty = txy * nx + tyy * ny - p * ny;
         const C Sl = static_cast<const C*>(a.S)[m];
         // the marker's force and torque in C, their sums (Eqs. 13-14) in R
-        Fx = (R)(tx * Sl);
-        Fy = (R)(ty * Sl);
-        Mz = (R)((rx * ty - ry * tx) * Sl);
+        cF[0] = tx * Sl;
+        cF[1] = ty * Sl;
+        cF[2] = (rx * ty - ry * tx) * Sl;
     }
-    // only the quad leaders (lanes 0, 4, ..., 28) hold a contribution
+    // lane q < 3 of each quad takes component q of its leader's values, so
+    // one FP64 conversion and one FP64 add per tree level sum all three
+    // (the same tree over the 8 quads for each component: lanes 0, 1, 2
+    // end with the block's F_x, F_y, M)
+    C mine = cF[0];
 #pragma unroll
-    for (int o = 16; o >= LPM; o >>= 1) {
-        Fx += __shfl_down_sync(0xffffffffu, Fx, o);
-        Fy += __shfl_down_sync(0xffffffffu, Fy, o);
-        Mz += __shfl_down_sync(0xffffffffu, Mz, o);
+    for (int j = 1; j < 3; ++j) {
+        const C v = __shfl_sync(0xffffffffu, cF[j], lane & ~(LPM - 1));
+        if (q == j) mine = v;
     }
+    R acc = q < 3 ? (R)mine : R(0.0);
+#pragma unroll
+    for (int o = 16; o >= LPM; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    const R Fy = __shfl_sync(0xffffffffu, acc, 1), Mz = __shfl_sync(0xffffffffu, acc, 2);
     if (err) atomicOr(a.err, err);
     unsigned done = 0;
     if (lane == 0) {
         R* part = partial + 3 * (long long)blockIdx.x;
-        part[0] = Fx;
+        part[0] = acc;
         part[1] = Fy;
         part[2] = Mz;
         __threadfence();  // the block sums are visible before the count says so
