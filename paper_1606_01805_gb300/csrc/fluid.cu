@@ -99,8 +99,12 @@ __device__ __forceinline__ void cell_update(C v[9], const Geo& G, C fx_ib, C fy_
 // index) of one row per thread, a warp covering 32 N cells of a row, the
 // block BY rows.  Populations move as vectors of N elements: a pull along
 // +-x is a one-lane shuffle of the neighbouring vector, with one extra
-// element load at the warp's two ends.  Cells on a wall or periodic edge
-// take the per-cell general path (emitted once, after the fast cells).
+// element load at the warp's two ends.  Cells of the first and last row
+// (y walls, corners, periodic y edges) take the per-cell general path
+// (emitted once, after the fast cells), and so do those of x walls when a
+// thread holds four cells; with one cell per thread the x-wall cells in
+// between stay on the vector path with their Zou-He completion.  The
+// periodic x edge patches the three populations that cross it.
 // PDL: launched with programmatic stream serialization after the spreading
 // kernel: the population loads come first, the force flags and the forces
 // after pdl_wait().  Otherwise the flags are loaded with the populations.
@@ -113,7 +117,8 @@ __device__ __forceinline__ void fluid_tile(const Geo& G, const S* __restrict__ f
     if (y >= G.ny) return;  // whole warp (one row)
     const long long row = (long long)y * G.pitch;
     // the vector values of cell x0 + k are its pulled populations whenever
-    // the cell is interior (all 9 sources inside, none of them clamped)
+    // all 9 sources are inside (none clamped); on an x wall all but the
+    // three that the Zou-He completion replaces
     const bool rows_in = y >= 1 && y <= G.ny - 2;
     const bool any = x0 < G.nx;
     // force flags of the 32-cell segment of this thread
@@ -186,15 +191,26 @@ __device__ __forceinline__ void fluid_tile(const Geo& G, const S* __restrict__ f
                     flb[G.plane + row + x0 + k] = C(0);
                 }
         }
-        // interior cells from the vector values
+        // interior cells from the vector values.  With one cell per thread
+        // so are the cells of an x wall between the two y edges: their six
+        // known populations come from inside the row range, and the Zou-He
+        // completion replaces the three that point into the fluid (with
+        // four cells per thread the completion inlined per cell costs the
+        // vector path registers, so those cells take the general path)
+        constexpr bool XW = N == 1;
         unsigned edge = 0;  // bit k: cell x0 + k lies on an edge (and inside the lattice)
 #pragma unroll
         for (int k = 0; k < N; ++k) {
             const int xk = x0 + k;
-            if (rows_in && xk < G.nx && (wrap || (xk >= 1 && xk <= G.nx - 2))) {
+            if (rows_in && xk < G.nx && (wrap || XW || (xk >= 1 && xk <= G.nx - 2))) {
                 C c[9];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) c[i] = v[i][k];
+                if (XW && !G.px && (xk == 0 || xk == G.nx - 1)) {
+                    const C gx = geo_g<C>(G, 0), gy = geo_g<C>(G, 1);
+                    if (xk == 0) zou_he_edge<1, 0, C>(c, geo_uw<C>(G, 0, 0), geo_uw<C>(G, 0, 1), gx, gy);
+                    else zou_he_edge<-1, 0, C>(c, geo_uw<C>(G, 1, 0), geo_uw<C>(G, 1, 1), gx, gy);
+                }
                 cell_update<C>(c, G, fxi[k], fyi[k]);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) v[i][k] = c[i];
