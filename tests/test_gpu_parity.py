@@ -84,6 +84,31 @@ def test_coupled_step_fp64_elementwise(case):
         np.testing.assert_allclose(gp[key], rp[key], rtol=1e-9, atol=1e-13)
 
 
+@pytest.mark.parametrize("omega0,rho_s,random_flow", [(2e-5, 1.2, False), (2e-2, 4.0, True)],
+                         ids=["short-series", "sincos"])
+def test_coupled_step_fp64_rotation_paths(omega0, rho_s, random_flow):
+    # The rigid update turns the stored (cos, sin) by the angle increment d:
+    # a short series for |d| < 1e-4, a long one for 1e-4 <= |d| < 1e-2 (the
+    # cases above, omega0 = 4e-4) and sincos beyond (a heavier body, whose
+    # spin the fluid slows less).  Each path against the oracle, which takes
+    # cos and sin of the angle itself, for 25 steps.
+    wl = _coupled("box", W.RECT, (12.0, 5.0), 33.0, 21.5, omega0=omega0, rho_s=rho_s)
+    f0 = (W.random_populations(67, 45, seed=5, base=rest_populations(), amp=0.005, smooth=0.01)
+          if random_flow else None)
+    ref, gpu = run_pair(wl, FP64, populations=f0)
+    rp, gp = ref.particles()[0], gpu.particles()[0]
+    # the increments stayed on the intended side of the thresholds
+    if omega0 < 1e-4:
+        assert abs(rp["omega"]) < 1e-4
+    else:
+        assert abs(rp["omega"]) > 1e-2
+    np.testing.assert_allclose(gpu.populations(), ref.populations(), rtol=0, atol=1e-13)
+    for key in ("xc", "yc", "theta", "omega", "M"):
+        assert gp[key] == pytest.approx(rp[key], rel=1e-9, abs=1e-13), key
+    for key in ("u", "F"):
+        np.testing.assert_allclose(gp[key], rp[key], rtol=1e-9, atol=1e-13)
+
+
 @pytest.mark.parametrize("case", COUPLED, ids=[f"{c[0]}-{c[1]}" for c in COUPLED])
 def test_coupled_step_fp32(case):
     kind, shape, dim, xc, yc, n = case
