@@ -40,9 +40,9 @@ PREC_NAMES = {0: "f64", 1: "f32", 2: "f16-storage/f32", 3: "f32+3 tangents"}
 # it was taken on, the workload, the precision and the tile shape
 # (profiles/k_fluid_sedimentation_400x1200.md)
 NCU_TRAFFIC = {
-    ("9077d154b05a7e3f", "sedimentation_circle_400x1200", 1, 0): 18220544 + 147456,
-    ("9077d154b05a7e3f", "sedimentation_circle_400x1200", 1, 1): 18218496 + 149248,
-    ("9077d154b05a7e3f", "sedimentation_circle_400x1200", 1, 2): 18039040 + 0,
+    ("9d21ee501d295afe", "sedimentation_circle_400x1200", 1, 0): 18310400 + 242688,
+    ("9d21ee501d295afe", "sedimentation_circle_400x1200", 1, 1): 18305024 + 239616,
+    ("9d21ee501d295afe", "sedimentation_circle_400x1200", 1, 2): 18037248 + 0,
 }
 
 

@@ -9,22 +9,25 @@ namespace {
 constexpr int BY = 8;  // rows per block of the init and field kernels
 
 // BGK relaxation of Eq. 4 towards the shifted equilibrium f~eq_i = f_eq_i - w_i
-// (Eq. 2), plus the Guo term (Eq. 5), in place on v.  Written over opposite
-// velocity pairs (i, i'): with e_i' = -e_i, both terms split into a part even
-// in e (shared) and a part odd in e (sign-flipped), so each pair costs one
-// evaluation: f~eq = w (drho + rho (4.5 (e.u)^2 - 1.5 u.u)) +- 3 w rho e.u and
-// G = (1 - omega/2) w [(9 (e.u)(e.F) - 3 u.F) +- 3 e.F].
+// (Eq. 2), plus the Guo term (Eq. 5), in place on v:
+//   v_i <- (1 - omega) v_i + omega f~eq_i + G_i.
+// Written over opposite velocity pairs (i, i'): with e_i' = -e_i both terms
+// split into a part even in e (shared) and a part odd in e (sign-flipped),
+// and their sum collects into
+//   omega f~eq_i + G_i = w (K0 + eu (a eu + b eF)) +- 3 w (c eu + cf eF)
+// with eu = e.u, eF = e.F, c = omega rho, a = 4.5 c, cf = 1 - omega / 2,
+// b = 9 cf and K0 = omega drho - 1.5 c u.u - 3 cf u.F (the rest population's
+// value, w = 4/9, has eu = eF = 0).
 template <class C>
 __device__ __forceinline__ void collide(C v[9], C drho, C ux, C uy, C Fx, C Fy, C omega) {
     const C rho = C(1) + drho;
     const C usq = ux * ux + uy * uy;
     const C cf = C(1) - C(0.5) * omega;
     const C uF = ux * Fx + uy * Fy;
-    {  // rest population
-        const C w = C(4.0 / 9.0);
-        const C feq = w * (drho - C(1.5) * rho * usq);
-        v[0] = v[0] - omega * (v[0] - feq) - C(3) * cf * w * uF;
-    }
+    const C keep = C(1) - omega;
+    const C c = omega * rho, a = C(4.5) * c, b = C(9) * cf;
+    const C K0 = omega * drho - C(1.5) * c * usq - C(3) * cf * uF;
+    v[0] = keep * v[0] + C(4.0 / 9.0) * K0;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         // pairs (1,3), (2,4), (5,7), (6,8): i has e = (ex, ey), i' has -e
@@ -33,12 +36,10 @@ __device__ __forceinline__ void collide(C v[9], C drho, C ux, C uy, C Fx, C Fy, 
         const C w = C(wt(i));
         const C eu = C(cx(i)) * ux + C(cy(i)) * uy;
         const C eF = C(cx(i)) * Fx + C(cy(i)) * Fy;
-        const C even = w * (drho + rho * (C(4.5) * eu * eu - C(1.5) * usq));
-        const C odd = C(3) * w * rho * eu;
-        const C geven = cf * w * (C(9) * eu * eF - C(3) * uF);
-        const C godd = C(3) * cf * w * eF;
-        v[i] = v[i] - omega * (v[i] - (even + odd)) + (geven + godd);
-        v[j] = v[j] - omega * (v[j] - (even - odd)) + (geven - godd);
+        const C even = w * (K0 + eu * (a * eu + b * eF));
+        const C odd = C(3) * w * (c * eu + cf * eF);
+        v[i] = keep * v[i] + (even + odd);
+        v[j] = keep * v[j] + (even - odd);
     }
 }
 
