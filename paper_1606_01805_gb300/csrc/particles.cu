@@ -475,16 +475,16 @@ __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
     }
 }
 
-// records examined per round of k_spread: as many as fit a 48 KB static list
+// records examined per round of k_spread: as many as fit the static list
+// (48 KB less the warp counts), at most two per thread
 template <class C>
 constexpr int spread_cap() {
-    int c = TX * TY;
-    while (c > 32 && sizeof(Rec<C>) * (size_t)c > 48 * 1024) c /= 2;
-    return c;
+    const int c = (int)((48 * 1024 - 256) / sizeof(Rec<C>));
+    return c < 2 * TX * TY ? c : 2 * TX * TY;
 }
 
 template <class C, class R, bool ONE>
-__global__ void __launch_bounds__(TX * TY) k_spread(SpreadArgs a) {
+__global__ void __launch_bounds__(TX * TY, sizeof(C) == 4 ? 2 : 1) k_spread(SpreadArgs a) {
     constexpr int CAP = spread_cap<C>();
     // the particle's markers, lattice and tile bound (fixed when it was added)
     const int4 pr = a.np_inline ? a.part_inline[blockIdx.y] : a.ptab[blockIdx.y];
@@ -495,8 +495,9 @@ __global__ void __launch_bounds__(TX * TY) k_spread(SpreadArgs a) {
     const Rec<C>* recs = static_cast<const Rec<C>*>(a.recs);
     C* flb = static_cast<C*>(a.flb) + I.flb_off;
     uint8_t* flags = a.flags + I.flags_off;
+    constexpr int NW = TX * TY / 32;
     __shared__ Rec<C> list[CAP];
-    __shared__ int wcount[TX * TY / 32];
+    __shared__ int wcount[2][NW];
     pdl_wait();  // boxes and records come from the marker kernel
     pdl_trigger();
     const int4 box = a.boxes[blockIdx.y];
@@ -510,23 +511,37 @@ __global__ void __launch_bounds__(TX * TY) k_spread(SpreadArgs a) {
     C ax = C(0), ay = C(0);
     bool touched = false;
     for (int base = 0; base < nm; base += CAP) {
-        const int l = base + t;
-        bool rel = false;
-        Rec<C> r;
-        if (t < CAP && l < nm) {
-            r = recs[m0 + l];
-            rel = r.i0 <= x0 + TX - 1 && r.i0 + 2 >= x0 && r.j0 <= y0 + TY - 1 && r.j0 + 2 >= y0;
+        // thread t examines records base + t (slot 0) and base + TX TY + t
+        // (slot 1); the relevant ones are compacted in marker order: all of
+        // slot 0 in thread order, then all of slot 1
+        bool rel[2] = {false, false};
+        Rec<C> r[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = h * TX * TY + t, l = base + k;
+            if (k < CAP && l < nm) {
+                r[h] = recs[m0 + l];
+                rel[h] = r[h].i0 <= x0 + TX - 1 && r[h].i0 + 2 >= x0 && r[h].j0 <= y0 + TY - 1 &&
+                         r[h].j0 + 2 >= y0;
+            }
         }
-        // order-preserving compaction of the relevant records
-        const unsigned bal = __ballot_sync(0xffffffffu, rel);
-        if (lane == 0) wcount[wid] = __popc(bal);
+        const unsigned bal0 = __ballot_sync(0xffffffffu, rel[0]), bal1 = __ballot_sync(0xffffffffu, rel[1]);
+        if (lane == 0) {
+            wcount[0][wid] = __popc(bal0);
+            wcount[1][wid] = __popc(bal1);
+        }
         __syncthreads();
-        int off = 0, total = 0;
-        for (int w = 0; w < TX * TY / 32; ++w) {
-            off += (w < wid) ? wcount[w] : 0;
-            total += wcount[w];
+        int off0 = 0, off1 = 0, total0 = 0, total1 = 0;
+        for (int w = 0; w < NW; ++w) {
+            off0 += (w < wid) ? wcount[0][w] : 0;
+            off1 += (w < wid) ? wcount[1][w] : 0;
+            total0 += wcount[0][w];
+            total1 += wcount[1][w];
         }
-        if (rel) list[off + __popc(bal & ((1u << lane) - 1u))] = r;
+        const unsigned below = (1u << lane) - 1u;
+        if (rel[0]) list[off0 + __popc(bal0 & below)] = r[0];
+        if (rel[1]) list[total0 + off1 + __popc(bal1 & below)] = r[1];
+        const int total = total0 + total1;
         __syncthreads();
         // warp wid holds tile row cyl: it picks, 32 at a time, the records
         // whose support has that row (one ballot), then every lane adds
