@@ -5,10 +5,11 @@ torque / rigid-body update, MLS marker interpolation and spreading, and the
 fused pull-stream + Zou-He + forced-BGK collide of every cell.
 
 Default workload: sedimentation of a circle (D = 50, density ratio 1.5) in a
-closed 400 x 1200 box, FP32 populations (stored as f - w_i) with FP64
-particle work.  Its 35 MB working set fits in L2, so L2 is flushed between
-timed steps.  Also reported: the same step on a 16384 x 4096 Couette lattice
-with 64 particles (4.8 GB of populations, beyond L2) for the HBM roofline.
+closed 400 x 1200 box, FP32 populations (stored as f - w_i) with the FP64
+particle state, 3x3 MLS solves, force sums and rigid-body update.  Its 35 MB
+working set fits in L2, so L2 is flushed between timed steps.  Also
+reported: the same step on a 16384 x 4096 Couette lattice with 64 particles
+(4.8 GB of populations, beyond L2) for the HBM roofline.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on the same workload instead.
@@ -420,7 +421,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAMES[prec], "data": "synthetic",
         "config": {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "tau": wl.tau,
                    "particles": len(wl.particles), "precision": args.precision +
-                   " populations, fp64 particle work",
+                   " populations, fp64 particle state / mls solve / force sums / rigid update",
                    "l2": "flushed before every timed step" if flush else "inputs larger than L2",
                    "parallelism": "replicas" if ws > 1 else "single",
                    "fluid_tile": {"variant": tile[0], "cells_per_thread": tile[1], "rows_per_block": tile[2],

@@ -56,9 +56,11 @@ typedef enum {
 /* side kinds, for sides ordered x-, x+, y-, y+ */
 typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_VELOCITY = 1 } lbm_bc;
 
-/* storage / arithmetic of the populations.  Particle work (probes, force
-   and torque reduction, MLS 3x3 solves, rigid-body update) is always FP64
-   (FP64 with derivatives in the tangent mode). */
+/* storage / arithmetic of the populations.  The particle state, the MLS
+   3x3 solves, the force and torque sums and the rigid-body update are
+   always FP64 (FP64 with derivatives in the tangent mode); marker and
+   probe geometry, MLS weights and moments, fits and tractions run in the
+   population arithmetic (FP32, or FP64 for LBM_FP64). */
 typedef enum {
     LBM_FP64 = 0,         /* FP64 populations, FP64 collision */
     LBM_FP32 = 1,         /* FP32 populations stored as f - w_i, FP32 collision */
