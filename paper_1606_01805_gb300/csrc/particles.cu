@@ -86,6 +86,7 @@ struct QuadMLS {
     int i0, j0;      // lower-left node of the support
     int li, lj;      // the same relative to the reference node
     int nk;          // nodes held by this lane (3 or 2)
+    int qd;          // the lane's place in its quad
     int kk[3];
     C phi[3], dpx[3], dpy[3];
 
@@ -97,6 +98,7 @@ struct QuadMLS {
         i0 = ix + li;
         j0 = iy + lj;
         nk = q == 0 ? 3 : 2;
+        qd = q;
 #pragma unroll
         for (int j = 0; j < 3; ++j) kk[j] = q + 4 * j;
     }
@@ -132,14 +134,29 @@ struct QuadMLS {
         R a00 = (R)quad_sum(b00), a01 = (R)quad_sum(b01), a02 = (R)quad_sum(b02);
         R a11 = (R)quad_sum(b11), a12 = (R)quad_sum(b12), a22 = (R)quad_sum(b22);
         if (!active) a00 = a11 = a22 = R(1.0);  // keep idle lanes finite
-        const R c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+        // The adjugate split over the marker's lanes (the FP64 unit takes a
+        // warp instruction whatever its lanes do): lane q forms cofactor
+        // c0q of the first row and, if D, c11 / c12 / c22 (q = 0 / 1 / 2;
+        // lane 3 repeats lane 0); the determinant and the rows of A^-1 then
+        // come from the quad by shuffles.
+        const int base = (threadIdx.x & 31) & ~(LPM - 1);
+        const R x = qd == 1 ? a02 : qd == 2 ? a01 : a11, y = qd == 1 || qd == 2 ? a12 : a22;
+        const R z = qd == 1 ? a01 : qd == 2 ? a02 : a12, w = qd == 1 ? a22 : qd == 2 ? a11 : a12;
+        const R cf = x * y - z * w;  // c00, c01, c02
+        const R c00 = __shfl_sync(0xffffffffu, cf, base), c01 = __shfl_sync(0xffffffffu, cf, base + 1);
+        const R c02 = __shfl_sync(0xffffffffu, cf, base + 2);
         const R id = recip(a00 * c00 + a01 * c01 + a02 * c02);
-        const C i00 = (C)(c00 * id), i01 = (C)(c01 * id), i02 = (C)(c02 * id);
+        const C ir = (C)(cf * id);
+        const C i00 = __shfl_sync(0xffffffffu, ir, base), i01 = __shfl_sync(0xffffffffu, ir, base + 1);
+        const C i02 = __shfl_sync(0xffffffffu, ir, base + 2);
         C i11 = C(0), i12 = C(0), i22 = C(0);
         if (D) {
-            i11 = (C)((a00 * a22 - a02 * a02) * id);
-            i12 = (C)((a01 * a02 - a00 * a12) * id);
-            i22 = (C)((a00 * a11 - a01 * a01) * id);
+            const R xs = qd == 1 ? a01 : a00, ys = qd == 1 ? a02 : qd == 2 ? a11 : a22;
+            const R zs = qd == 1 ? a00 : qd == 2 ? a01 : a02, ws = qd == 1 ? a12 : qd == 2 ? a01 : a02;
+            const C is = (C)((xs * ys - zs * ws) * id);  // c11, c12, c22 over det
+            i11 = __shfl_sync(0xffffffffu, is, base);
+            i12 = __shfl_sync(0xffffffffu, is, base + 1);
+            i22 = __shfl_sync(0xffffffffu, is, base + 2);
         }
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
