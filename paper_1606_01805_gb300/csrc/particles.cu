@@ -201,29 +201,36 @@ __device__ __forceinline__ Body<R> update_body(const DParticleT<R>* P, const R* 
     for (int o = 4; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     const R F0 = __shfl_sync(0xffffffffu, acc, 0), F1 = __shfl_sync(0xffffffffu, acc, 1);
     const R Mt = __shfl_sync(0xffffffffu, acc, 2);
-    const R X0 = P->X[0][0], Y0 = P->X[0][1], th0 = P->th[0];
-    const R U0 = P->U[0][0], V0 = P->U[0][1], W0 = P->W[0];
+    const R th0 = P->th[0];
     const R buoy = (P->rho_s - 1.0) * P->area;
-    const R ax = (F0 + buoy * gravity[0]) * P->inv_mass;
-    const R ay = (F1 + buoy * gravity[1]) * P->inv_mass;
-    const R al = Mt * P->inv_inertia;
-    Body<R> B;
+    // lane c = 0, 1, 2 integrates x, y, the angle (the FP64 unit takes a
+    // warp instruction whatever its lanes do); the others repeat lane 0
+    const int c = lane < 3 ? lane : 0;
+    const R fc = c == 0 ? F0 : c == 1 ? F1 : Mt;
+    const R gc = R(c == 1 ? gravity[1] : gravity[0]);
+    const R inv = c == 2 ? P->inv_inertia : P->inv_mass;
+    const R fg = fc + buoy * gc;
+    const R ac = (c == 2 ? fc : fg) * inv;  // a_x, a_y, alpha
+    const R v0 = c == 0 ? P->U[0][0] : c == 1 ? P->U[0][1] : P->W[0];
+    const R p0 = c == 0 ? P->X[0][0] : c == 1 ? P->X[0][1] : th0;
+    R vn, pn;
     if (P->nupd == 0) {  // one stored level: u1 = u0 + a, x1 = x0 + u1
-        B.U = U0 + ax;
-        B.V = V0 + ay;
-        B.W = W0 + al;
-        B.X = X0 + B.U;
-        B.Y = Y0 + B.V;
-        B.T = th0 + B.W;
+        vn = v0 + ac;
+        pn = p0 + vn;
     } else {  // Eqs. 15-16 and the same two-level form for position and angle
         const double k = 2.0 / 3.0;
-        B.U = k * (2.0 * U0 - 0.5 * P->U[1][0] + ax);
-        B.V = k * (2.0 * V0 - 0.5 * P->U[1][1] + ay);
-        B.W = k * (2.0 * W0 - 0.5 * P->W[1] + al);
-        B.X = k * (2.0 * X0 - 0.5 * P->X[1][0] + B.U);
-        B.Y = k * (2.0 * Y0 - 0.5 * P->X[1][1] + B.V);
-        B.T = k * (2.0 * th0 - 0.5 * P->th[1] + B.W);
+        const R v1 = c == 0 ? P->U[1][0] : c == 1 ? P->U[1][1] : P->W[1];
+        const R p1 = c == 0 ? P->X[1][0] : c == 1 ? P->X[1][1] : P->th[1];
+        vn = k * (2.0 * v0 - 0.5 * v1 + ac);
+        pn = k * (2.0 * p0 - 0.5 * p1 + vn);
     }
+    Body<R> B;
+    B.U = __shfl_sync(0xffffffffu, vn, 0);
+    B.V = __shfl_sync(0xffffffffu, vn, 1);
+    B.W = __shfl_sync(0xffffffffu, vn, 2);
+    B.X = __shfl_sync(0xffffffffu, pn, 0);
+    B.Y = __shfl_sync(0xffffffffu, pn, 1);
+    B.T = __shfl_sync(0xffffffffu, pn, 2);
     // (cos, sin) of the new angle: the stored pair of the old one turned by
     // the increment d, with cos d and sin d from their Taylor series: for
     // |d| < 1e-4 to d^4 / d^3 (the next terms below 1.4e-27 and 8.3e-19 |d|),
