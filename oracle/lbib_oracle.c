@@ -28,6 +28,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OB_MAXP 4096
 
@@ -254,6 +257,7 @@ static void stream(const ob_sim* s, const double* fp, double* fout) {
     int nx = s->c.nx, ny = s->c.ny;
     double gx = s->c.body_force[0], gy = s->c.body_force[1];
     double f[9];
+#pragma omp parallel for private(f)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             pull(s, fp, x, y, f);
@@ -284,6 +288,7 @@ static void stream(const ob_sim* s, const double* fp, double* fout) {
 /* Eqs. 6-7 without the immersed-boundary force: rho, u* = (sum f e + g_f/2)/rho */
 static void moments(const ob_sim* s, const double* f, double* rho, double* ux, double* uy) {
     int nx = s->c.nx, ny = s->c.ny;
+#pragma omp parallel for
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             double r = 0, jx = 0, jy = 0;
@@ -708,6 +713,7 @@ static void init_fields(ob_sim* s) {
     const double pi = acos(-1.0);
     int nx = s->c.nx, ny = s->c.ny;
     double H = ny - 1;
+#pragma omp parallel for
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             double rho = 1.0, ux = 0.0, uy = 0.0;
@@ -741,6 +747,11 @@ ob_sim* ob_create(const ob_config* cfg, int* err) {
        nu = c_s^2 (tau - 1/2) = (2 tau - 1)/6. */
     s->nu = CS2 * (cfg->tau - 0.5);
     ob_lattice(s->e, s->w);
+    {   /* fill the shared table before any parallel loop reads it */
+        const int(*e)[2];
+        const double* w;
+        lattice_cached(&e, &w);
+    }
     size_t nc = (size_t)cfg->nx * cfg->ny;
     s->f = calloc(9 * nc, sizeof(double));
     s->fpost = calloc(9 * nc, sizeof(double));
@@ -832,6 +843,7 @@ int ob_step(ob_sim* s, int nsteps) {
         }
         /* 5. forced collision with the total force g_f + f_lb */
         double f[9], fo[9];
+#pragma omp parallel for private(f, fo)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 size_t k = (size_t)y * nx + x;
@@ -847,6 +859,19 @@ int ob_step(ob_sim* s, int nsteps) {
 }
 
 const char* ob_last_error(const ob_sim* s) { return s->msg; }
+
+/* Threads of the lattice loops (built with OpenMP; otherwise one).  Each
+   row is computed by one thread with the same arithmetic, so the results
+   do not depend on the count. */
+int ob_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 int ob_nx(const ob_sim* s) { return s->c.nx; }
 int ob_ny(const ob_sim* s) { return s->c.ny; }
 long ob_steps_done(const ob_sim* s) { return s->step; }

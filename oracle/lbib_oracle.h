@@ -82,6 +82,9 @@ void ob_destroy(ob_sim* s);
 int ob_add_particle(ob_sim* s, const ob_particle_desc* d);
 int ob_step(ob_sim* s, int nsteps);
 const char* ob_last_error(const ob_sim* s);
+/* threads of the lattice loops (OpenMP builds; n <= 0 keeps the count);
+   returns the count in use.  Results do not depend on it. */
+int ob_set_threads(int n);
 int ob_nx(const ob_sim* s);
 int ob_ny(const ob_sim* s);
 long ob_steps_done(const ob_sim* s);

@@ -33,10 +33,11 @@ def build(force: bool = False) -> Path:
         SRC.stat().st_mtime, (HERE / "lbib_oracle.h").stat().st_mtime
     ):
         tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-             "-o", str(tmp), str(SRC), "-lm"]
-        )
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+               "-o", str(tmp), str(SRC), "-lm"]
+        # OpenMP threads over the rows of the lattice loops, where gcc has it
+        if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
+            subprocess.check_call(cmd)
         os.replace(tmp, LIB)
     return LIB
 
@@ -104,8 +105,18 @@ def lib():
                                      _dp, C.c_double, _dp, C.c_double]
         L.ob_spread_only.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp, C.POINTER(C.c_double)]
         L.ob_rigid_update.argtypes = [C.c_void_p, C.c_int, _dp, C.c_double]
+        L.ob_set_threads.restype = C.c_int
+        L.ob_set_threads.argtypes = [C.c_int]
+        # one thread unless asked otherwise (many oracle processes may run
+        # side by side)
+        L.ob_set_threads(int(os.environ.get("OB_THREADS", "1")))
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's lattice loops; returns the count in use."""
+    return lib().ob_set_threads(n)
 
 
 # ---- single-step functions -------------------------------------------------

@@ -29,7 +29,7 @@ def _rank(rank, world, port, out):
 
 def test_replica_throughput_takes_slowest_rank_and_all_work():
     world = 2
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
     for r in range(world):
         value, ms = out[r]
