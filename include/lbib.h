@@ -48,7 +48,9 @@ typedef enum {
     LBM_ENOMEM = 2,     /* workspace too small or allocation failed */
     LBM_ECUDA = 3,      /* a CUDA runtime call failed */
     LBM_ETIMEOUT = 4,   /* a bounded device wait expired */
-    LBM_ENONFINITE = 5, /* NaN/Inf or non-positive density detected */
+    LBM_ENONFINITE = 5, /* a lattice cell of non-positive or non-finite density
+                           (watchdog of the fluid kernel), or a non-finite
+                           particle state */
     LBM_EINTERNAL = 6,
     LBM_EDOMAIN = 7     /* a marker or probe support crossed a wall */
 } lbm_status;
@@ -104,6 +106,10 @@ typedef struct {
     void* cuda_stream;      /* cudaStream_t, or NULL */
     void* d_workspace;      /* caller-owned device memory, or NULL to allocate */
     size_t workspace_bytes; /* size of d_workspace */
+    int32_t check_every;    /* watchdog period: the fluid kernel checks every
+                               cell on the steps whose count since init is a
+                               multiple of check_every; 0 or 1: every step;
+                               else 2, 4, 8, 16 or 32 (LBM_EINVAL otherwise) */
 } lbm_config;
 
 typedef struct {
@@ -155,8 +161,13 @@ lbm_status lbm_add_particle(lbm_ctx* ctx, const lbm_particle_desc* desc, int32_t
 /*
  * Advance nsteps >= 0 time steps (the five stages above per step),
  * asynchronously on the context's stream.  Errors detected on the device
- * (a support crossing a wall: LBM_EDOMAIN) are reported by the next
- * lbm_sync / lbm_get_* call.
+ * are reported by the next lbm_sync / lbm_get_* call: LBM_EDOMAIN (a
+ * marker or probe support crossed a wall), LBM_ENONFINITE (the watchdog:
+ * on its steps, see lbm_config.check_every, the fluid kernel flags any
+ * cell whose streamed density rho = sum_i f_i of Eq. 6 is not positive or
+ * not finite -- a NaN or infinite population makes the sum non-finite;
+ * every rigid-body update flags a non-finite particle state).  The flags
+ * are sticky: once set, every later lbm_sync / lbm_get_* call reports them.
  */
 lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps);
 
@@ -171,8 +182,18 @@ lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps);
  */
 lbm_status lbm_step_timed(lbm_ctx* ctx, int32_t nsteps, double* ms_step, double* ms_fluid);
 
-/* Wait for the stream; report a device-side error flagged since init. */
+/* Wait for the stream; report a device-side error flagged since init
+   (LBM_EDOMAIN, LBM_ENONFINITE or LBM_ETIMEOUT, in that order of priority). */
 lbm_status lbm_sync(lbm_ctx* ctx);
+
+/*
+ * Test hook of the host's error path (the paper has no counterpart): sets,
+ * on the device and in stream order, the flag a kernel sets when it
+ * detects `status` (LBM_EDOMAIN, LBM_ENONFINITE or LBM_ETIMEOUT; else
+ * LBM_EINVAL), so that the next lbm_sync / lbm_get_* call reports it.
+ * Nothing faults; the context stays usable but keeps reporting the flag.
+ */
+lbm_status lbm_inject_status(lbm_ctx* ctx, int32_t status);
 
 /*
  * Density and velocity (host, nx*ny doubles each, y-major) of the
@@ -182,12 +203,31 @@ lbm_status lbm_sync(lbm_ctx* ctx);
  */
 lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* ux, double* uy);
 
-/* Stored post-collision populations f* (host, [9][ny][nx] doubles). */
+/*
+ * Stored post-collision populations f*_i of Eq. 4 (the right-hand side of
+ * the lattice BGK equation before streaming), unshifted (f_i, not f_i -
+ * w_i): host array of [9][ny][nx] doubles, caller-owned, in the velocity
+ * order of Eq. 3.  Synchronises.  Errors: LBM_EINVAL (null argument),
+ * LBM_ECUDA.
+ */
 lbm_status lbm_get_populations(lbm_ctx* ctx, double* f);
-/* Replace the stored post-collision populations (host, [9][ny][nx]). */
+/*
+ * Replace the stored post-collision populations f*_i of Eq. 4 (host,
+ * [9][ny][nx] doubles, caller-owned, read only; rounded to the storage
+ * precision).  The next step streams them.  Synchronises.  Errors as for
+ * lbm_get_populations.
+ */
 lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f);
 
-/* Particle states (host); *n receives the particle count. */
+/*
+ * Particle states (host, caller-owned array of cap entries): the centroid,
+ * angle, velocity and angular velocity of the latest rigid-body update
+ * (Eqs. 15-16) and the hydrodynamic force and torque it used (Eqs. 13-14,
+ * the surface integrals of Section 2.3).  *n receives the particle count;
+ * min(cap, count) entries are written, in the order the particles were
+ * added.  Synchronises.  Errors: a device flag as for lbm_sync (LBM_EDOMAIN
+ * still returns the states).
+ */
 lbm_status lbm_get_particles(lbm_ctx* ctx, lbm_particle_state* out, int32_t cap, int32_t* n);
 
 /*
@@ -205,12 +245,14 @@ lbm_status lbm_get_particles(lbm_ctx* ctx, lbm_particle_state* out, int32_t cap,
  * no allocating library routine; the populations and particle state it
  * reads and writes are the context's, as for lbm_step.
  *  - Limits: at most LBM_STATIC_MAX_PARTICLES particles and
- *    LBM_STATIC_MAX_MARKERS markers in the context, else LBM_EINVAL with
- *    the reason in lbm_last_error.
+ *    LBM_STATIC_MAX_MARKERS markers in the context, in every precision
+ *    (the array is sized for the largest per-marker record, that of
+ *    LBM_FP32_TANGENT), else LBM_EINVAL with the reason in lbm_last_error.
  *  - The static array is held by every GPU that loads the library until
  *    the process exits.  The first call on a device looks up its device
- *    address (once per device, with that device current); make that first
- *    call before any stream capture.
+ *    address (once per device, with that device current) and keeps it;
+ *    make that first call before any stream capture, and do not reset the
+ *    device (cudaDeviceReset) after it while the library stays loaded.
  *  - All calls share the one array, which keeps the last call's contents;
  *    each call clears the counters that must start at zero (every other
  *    entry is reset or written before it is read within a step).  Calls
@@ -219,7 +261,7 @@ lbm_status lbm_get_particles(lbm_ctx* ctx, lbm_particle_state* out, int32_t cap,
  *  - Launches directly on the context's stream, asynchronously; errors as
  *    for lbm_step.
  */
-#define LBM_STATIC_SCRATCH_BYTES (3u << 20)
+#define LBM_STATIC_SCRATCH_BYTES (6u << 20)
 #define LBM_STATIC_MAX_PARTICLES 1024
 #define LBM_STATIC_MAX_MARKERS 16384
 lbm_status lbm_step_static(lbm_ctx* ctx, int32_t nsteps);

@@ -16,6 +16,10 @@
 
 using namespace lbib;
 
+namespace {
+constexpr int GRAPH_STEPS = 32;  // even, so a replay returns to the same buffer
+}
+
 struct lbm_ctx {
     lbm_config cfg;                 // first configuration: stream, workspace, capacities
     std::vector<lbm_config> icfg;   // per instance
@@ -48,18 +52,21 @@ struct lbm_ctx {
     int4* boxes;
     int4* ptab;                     // device copy of hpart
     unsigned* err;
-    double* scratch;
-    int scratch_rows;
+    double* scratch;                // staging area of field and population copies
+    int scratch_rows, scratch_cols, scratch_planes;  // its capacity: planes x rows x cols doubles
     int np = 0, nmark = 0, nblk = 0;
     std::vector<int4> hblk;         // host copies of the marker-block table and
     std::vector<int4> hpart;        // of the per-particle (first marker, markers, instance)
     double rc_max = 0;
     int64_t steps = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // GRAPH_STEPS steps from buffer 0 / 1
+    int check_every = 1;            // watchdog period of the fluid kernel (steps)
+    // GRAPH_STEPS steps from buffer 0 / 1, starting at a step count of each
+    // residue modulo check_every (the watchdog steps sit at fixed places)
+    cudaGraphExec_t graph[2][GRAPH_STEPS] = {};
     bool graphs_ok = true;
-    cudaGraphExec_t timed[2] = {nullptr, nullptr};  // one step with its timing events
-    cudaGraphExec_t timed0[2] = {nullptr, nullptr}; // the same without the event before the fluid kernel
+    cudaGraphExec_t timed[2][2] = {};  // one step with its timing events (without / with the watchdog)
+    cudaGraphExec_t timed0[2][2] = {}; // the same without the event before the fluid kernel
     bool timed_ok = true;
     std::string msg;
 };
@@ -87,6 +94,8 @@ const char* check_config(const lbm_config* c) {
     if (c->weight < LBM_W_EXP || c->weight > LBM_W_POLY) return "unknown weight";
     if (c->init == LBM_INIT_COUETTE && c->bc[2] != LBM_BC_VELOCITY) return "Couette needs y walls";
     if ((long long)c->nx * c->ny > (1LL << 40)) return "lattice too large";
+    if (c->check_every < 0 || c->check_every > GRAPH_STEPS || (c->check_every > 0 && GRAPH_STEPS % c->check_every))
+        return "check_every must be 0 or divide 32";
     return nullptr;
 }
 
@@ -144,7 +153,7 @@ struct Layout {
     size_t f0, f1, flb, flags, insts_off, tasks[N_FLUID_VARIANTS], parts, poses, blk, partial, count, mg,
         S, recs, boxes, ptab, err, scratch, total;
     int ntasks[N_FLUID_VARIANTS];
-    int scratch_rows;
+    int scratch_rows, scratch_cols, scratch_planes;
 };
 
 Layout layout(const lbm_config* cfgs, int n) {
@@ -170,6 +179,9 @@ Layout layout(const lbm_config* cfgs, int n) {
     // the tangent mode adds KT derivative planes per field)
     const int fplanes = prec == LBM_FP32_TANGENT ? 3 * (1 + KT) : 3;
     L.scratch_rows = (int)std::max<size_t>(1, (size_t)(3u << 20) / fplanes / max_nx);
+    // at least one row of populations (9 planes) fits
+    L.scratch_planes = std::max(fplanes, (9 + L.scratch_rows - 1) / L.scratch_rows);
+    L.scratch_cols = max_nx;
     const size_t R = real_bytes(prec);
     size_t o = 0;
     L.f0 = o; o = up(o + fe * storage_bytes(prec));
@@ -193,7 +205,7 @@ Layout layout(const lbm_config* cfgs, int n) {
     L.boxes = o; o = up(o + P * sizeof(int4));
     L.ptab = o; o = up(o + P * sizeof(int4));
     L.err = o; o = up(o + 16);
-    L.scratch = o; o = up(o + fplanes * (size_t)L.scratch_rows * max_nx * sizeof(double));
+    L.scratch = o; o = up(o + (size_t)L.scratch_planes * L.scratch_rows * max_nx * sizeof(double));
     L.total = o;
     return L;
 }
@@ -218,12 +230,12 @@ lbm_status device_error(lbm_ctx* ctx) {
     CK(cudaMemcpyAsync(&e, ctx->err, sizeof e, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (e & ERR_DOMAIN) return fail(ctx, LBM_EDOMAIN, "a marker or probe support crossed a wall");
-    if (e & ERR_NONFINITE) return fail(ctx, LBM_ENONFINITE, "non-finite particle state");
+    if (e & ERR_NONFINITE)
+        return fail(ctx, LBM_ENONFINITE, "a non-finite value or a non-positive density in the lattice, "
+                                         "or a non-finite particle state");
     if (e & ERR_TIMEOUT) return fail(ctx, LBM_ETIMEOUT, "a device wait expired");
     return LBM_OK;
 }
-
-constexpr int GRAPH_STEPS = 32;  // even, so a replay returns to the same buffer
 
 // particle state buffer `buf` (0 or 1), and its pose in the compute type
 char* state(const lbm_ctx* ctx, int buf) {
@@ -282,10 +294,15 @@ int box_tiles(double rc) {
 }
 int spread_tiles(const lbm_ctx* ctx) { return box_tiles(ctx->rc_max); }
 
+// The fluid kernel's watchdog runs on the steps whose count since init
+// (1-based) is a multiple of check_every.
+bool watched(const lbm_ctx* ctx, int64_t step) { return (step + 1) % ctx->check_every == 0; }
+
 // pdl: launch the fluid kernel with programmatic stream serialization (only
 // right after the spreading kernel: its prologue loads the populations the
-// previous step's fluid kernel wrote)
-lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v, bool pdl = false) {
+// previous step's fluid kernel wrote); check: the kernel runs its watchdog
+lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v, bool pdl = false,
+                             bool check = false) {
     FluidArgs fa;
     fa.fin = ctx->f[cur];
     fa.fout = ctx->f[cur ^ 1];
@@ -294,6 +311,8 @@ lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v, bool
     fa.insts = ctx->insts;
     fa.tasks = ctx->tasks[v];
     fa.ntasks = ctx->ntasks[v];
+    fa.err = ctx->err;
+    fa.check = check ? 1 : 0;
     // one CTA per TASKS_PER_CTA tiles: the block scheduler keeps every SM
     // filled as CTAs finish (the kernel's outer task loop then runs once)
     const int grid = std::max(1, (fa.ntasks + TASKS_PER_CTA - 1) / TASKS_PER_CTA);
@@ -301,12 +320,13 @@ lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v, bool
     return LBM_OK;
 }
 
-// Part of one time step from buffer `cur` on stream `st`: the immersed-
-// boundary kernels (ib = true: probes / rigid update / markers, spreading)
-// or the fused fluid kernel over every instance (ib = false).  Bookkeeping
-// is the caller's.
-lbm_status enqueue_step_part(lbm_ctx* ctx, cudaStream_t st, int cur, bool ib, bool pdl = false) {
-    if (!ib) return launch_fluid_step(ctx, st, cur, ctx->variant, pdl && ctx->np > 0);
+// Part of time step number `step` (steps done before it) from buffer `cur`
+// on stream `st`: the immersed-boundary kernels (ib = true: probes / rigid
+// update / markers, spreading) or the fused fluid kernel over every
+// instance (ib = false).  Bookkeeping is the caller's.
+lbm_status enqueue_step_part(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t step, bool ib,
+                             bool pdl = false) {
+    if (!ib) return launch_fluid_step(ctx, st, cur, ctx->variant, pdl && ctx->np > 0, watched(ctx, step));
     if (ctx->np == 0) return LBM_OK;
     const ParticleArgs pa = particle_args(ctx, cur);
     CK(launch_probes(ctx->prec, pa, ctx->nblk, st));
@@ -315,52 +335,58 @@ lbm_status enqueue_step_part(lbm_ctx* ctx, cudaStream_t st, int cur, bool ib, bo
     return LBM_OK;
 }
 
-// one time step from buffer `cur` on stream `st` (mid: optional event
-// between the IB kernels and the fluid kernel, which then starts only after
-// it, so that mid -> end times the fluid kernel alone).  Bookkeeping is the
-// caller's.
-lbm_status enqueue_step(lbm_ctx* ctx, cudaStream_t st, int cur, cudaEvent_t mid) {
-    lbm_status s = enqueue_step_part(ctx, st, cur, true);
+// time step number `step` from buffer `cur` on stream `st` (mid: optional
+// event between the IB kernels and the fluid kernel, which then starts only
+// after it, so that mid -> end times the fluid kernel alone).  Bookkeeping
+// is the caller's.
+lbm_status enqueue_step(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t step, cudaEvent_t mid) {
+    lbm_status s = enqueue_step_part(ctx, st, cur, step, true);
     if (s != LBM_OK) return s;
     if (mid) CK(cudaEventRecord(mid, st));
-    return enqueue_step_part(ctx, st, cur, false, mid == nullptr);
+    return enqueue_step_part(ctx, st, cur, step, false, mid == nullptr);
 }
 
-// Capture GRAPH_STEPS steps starting from buffer `cur` on a private stream
-// (the caller's stream may be the legacy default stream, which cannot be
-// captured).  Returns false if capture is not possible here.
-bool capture_graph(lbm_ctx* ctx, int cur) {
+// Capture GRAPH_STEPS steps starting from buffer `cur` at step count
+// `step` on a private stream (the caller's stream may be the legacy
+// default stream, which cannot be captured).  The graph serves every start
+// with the same buffer and the same step count modulo check_every.
+// Returns false if capture is not possible here.
+bool capture_graph(lbm_ctx* ctx, int cur, int64_t step) {
+    cudaGraphExec_t& ge = ctx->graph[cur][step % ctx->check_every];
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return false;
     bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
         int c = cur;
-        for (int k = 0; k < GRAPH_STEPS && ok; ++k, c ^= 1) ok = enqueue_step(ctx, cs, c, nullptr) == LBM_OK;
+        for (int k = 0; k < GRAPH_STEPS && ok; ++k, c ^= 1)
+            ok = enqueue_step(ctx, cs, c, step + k, nullptr) == LBM_OK;
         cudaGraph_t g = nullptr;
         const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
-        ok = ok && ended && g && cudaGraphInstantiate(&ctx->graph[cur], g, 0) == cudaSuccess;
+        ok = ok && ended && g && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
         if (g) cudaGraphDestroy(g);
     }
     cudaStreamDestroy(cs);
     cudaGetLastError();  // a failed capture leaves no sticky error
-    if (!ok) ctx->graph[cur] = nullptr;
+    if (!ok) ge = nullptr;
     return ok;
 }
 
 // enqueue_step for capture: the event between the IB kernels and the fluid
 // kernel (with_mid) is an external record, i.e. a real event-record node
-lbm_status enqueue_timed_step(lbm_ctx* ctx, cudaStream_t st, int cur, bool with_mid) {
-    lbm_status s = enqueue_step_part(ctx, st, cur, true);
+lbm_status enqueue_timed_step(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t step, bool with_mid) {
+    lbm_status s = enqueue_step_part(ctx, st, cur, step, true);
     if (s != LBM_OK) return s;
     if (with_mid) CK(cudaEventRecordWithFlags(ctx->ev[1], st, cudaEventRecordExternal));
-    return enqueue_step_part(ctx, st, cur, false, !with_mid);
+    return enqueue_step_part(ctx, st, cur, step, false, !with_mid);
 }
 
 // One step from buffer `cur` with the timing events recorded inside the
 // graph (same launches as enqueue_step, replayed like lbm_step replays);
-// with_mid adds the event between the IB kernels and the fluid kernel.
-bool capture_timed(lbm_ctx* ctx, int cur, bool with_mid) {
-    cudaGraphExec_t& ge = with_mid ? ctx->timed[cur] : ctx->timed0[cur];
+// with_mid adds the event between the IB kernels and the fluid kernel.  The
+// graph serves every step with the same buffer and watchdog setting.
+bool capture_timed(lbm_ctx* ctx, int cur, int64_t step, bool with_mid) {
+    const int w = watched(ctx, step) ? 1 : 0;
+    cudaGraphExec_t& ge = with_mid ? ctx->timed[cur][w] : ctx->timed0[cur][w];
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return false;
     bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
@@ -368,7 +394,7 @@ bool capture_timed(lbm_ctx* ctx, int cur, bool with_mid) {
         // external records: real event-record nodes, not capture-internal
         // dependencies
         ok = cudaEventRecordWithFlags(ctx->ev[0], cs, cudaEventRecordExternal) == cudaSuccess &&
-             enqueue_timed_step(ctx, cs, cur, with_mid) == LBM_OK &&
+             enqueue_timed_step(ctx, cs, cur, step, with_mid) == LBM_OK &&
              cudaEventRecordWithFlags(ctx->ev[2], cs, cudaEventRecordExternal) == cudaSuccess;
         cudaGraph_t g = nullptr;
         const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
@@ -382,12 +408,19 @@ bool capture_timed(lbm_ctx* ctx, int cur, bool with_mid) {
 }
 
 void drop_graphs(lbm_ctx* ctx) {
-    for (auto* set : {ctx->graph, ctx->timed, ctx->timed0})
-        for (int k = 0; k < 2; ++k)
-            if (set[k]) {
-                cudaGraphExecDestroy(set[k]);
-                set[k] = nullptr;
+    for (int c = 0; c < 2; ++c) {
+        for (auto& g : ctx->graph[c])
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
             }
+        for (int w = 0; w < 2; ++w)
+            for (auto* g : {&ctx->timed[c][w], &ctx->timed0[c][w]})
+                if (*g) {
+                    cudaGraphExecDestroy(*g);
+                    *g = nullptr;
+                }
+    }
 }
 
 // Autotuner of the fluid tile shape: times every variant on the context's
@@ -443,6 +476,7 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
     ctx->sb = storage_bytes(ctx->prec);
     ctx->cb = compute_bytes(ctx->prec);
     ctx->stream = static_cast<cudaStream_t>(cfgs[0].cuda_stream);
+    ctx->check_every = cfgs[0].check_every > 0 ? cfgs[0].check_every : 1;
     if (cfgs[0].d_workspace) {
         if (cfgs[0].workspace_bytes < L.total) {
             delete ctx;
@@ -483,6 +517,8 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
     ctx->err = reinterpret_cast<unsigned*>(b + L.err);
     ctx->scratch = reinterpret_cast<double*>(b + L.scratch);
     ctx->scratch_rows = L.scratch_rows;
+    ctx->scratch_cols = L.scratch_cols;
+    ctx->scratch_planes = L.scratch_planes;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -687,29 +723,29 @@ lbm_status get_fields(lbm_ctx* ctx, int inst, double* rho, double* ux, double* u
     return LBM_OK;
 }
 
-double weight_of(int i) { return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+// rows of one population chunk through the staging area (9 planes of
+// doubles per row)
+int pop_rows(const lbm_ctx* ctx, int nx) {
+    const size_t cap = (size_t)ctx->scratch_rows * ctx->scratch_cols * ctx->scratch_planes;
+    return (int)std::max<size_t>(1, cap / (9 * (size_t)nx));
+}
 
+// populations host <-> device in chunks of rows through the staging area:
+// one 2-D copy (9 plane segments) and one conversion kernel per chunk, in
+// stream order; the host array is [9][ny][nx] doubles
 lbm_status get_populations(lbm_ctx* ctx, int inst, double* f) {
     if (!ctx || !f) return LBM_EINVAL;
     if (inst < 0 || inst >= ctx->ninst) return fail(ctx, LBM_EINVAL, "no such instance");
     const Inst& I = ctx->hinst[inst];
-    const int nx = I.G.nx, ny = I.G.ny, pitch = I.G.pitch;
-    const size_t n = 9 * (size_t)I.G.plane;
-    std::vector<unsigned char> h(n * ctx->sb);
-    const char* src = static_cast<const char*>(ctx->f[ctx->cur]) + I.f_off * ctx->sb;
-    CK(cudaMemcpyAsync(h.data(), src, h.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    const int nx = I.G.nx, ny = I.G.ny, R = pop_rows(ctx, nx);
+    for (int y0 = 0; y0 < ny; y0 += R) {
+        const int rows = std::min(R, ny - y0);
+        CK(launch_get_pops(ctx->prec, ctx->f[ctx->cur], I, y0, rows, ctx->scratch, ctx->stream));
+        const size_t w = (size_t)rows * nx * sizeof(double);
+        CK(cudaMemcpy2DAsync(f + (size_t)y0 * nx, (size_t)ny * nx * sizeof(double), ctx->scratch, w, w, 9,
+                             cudaMemcpyDeviceToHost, ctx->stream));
+    }
     CK(cudaStreamSynchronize(ctx->stream));
-    for (int i = 0; i < 9; ++i)
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x) {
-                const size_t k = (size_t)i * I.G.plane + (size_t)y * pitch + x;
-                double v;
-                if (ctx->prec == LBM_FP64) v = reinterpret_cast<double*>(h.data())[k];
-                else if (ctx->prec == LBM_FP32) v = reinterpret_cast<float*>(h.data())[k];
-                else if (ctx->prec == LBM_FP16_SHIFTED) v = __half2float(reinterpret_cast<__half*>(h.data())[k]);
-                else v = reinterpret_cast<TF*>(h.data())[k].v;
-                f[((size_t)i * ny + y) * nx + x] = v + weight_of(i);
-            }
     return LBM_OK;
 }
 
@@ -717,21 +753,14 @@ lbm_status set_populations(lbm_ctx* ctx, int inst, const double* f) {
     if (!ctx || !f) return LBM_EINVAL;
     if (inst < 0 || inst >= ctx->ninst) return fail(ctx, LBM_EINVAL, "no such instance");
     const Inst& I = ctx->hinst[inst];
-    const int nx = I.G.nx, ny = I.G.ny, pitch = I.G.pitch;
-    const size_t n = 9 * (size_t)I.G.plane;
-    std::vector<unsigned char> h(n * ctx->sb, 0);
-    for (int i = 0; i < 9; ++i)
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x) {
-                const size_t k = (size_t)i * I.G.plane + (size_t)y * pitch + x;
-                const double v = f[((size_t)i * ny + y) * nx + x] - weight_of(i);
-                if (ctx->prec == LBM_FP64) reinterpret_cast<double*>(h.data())[k] = v;
-                else if (ctx->prec == LBM_FP32) reinterpret_cast<float*>(h.data())[k] = (float)v;
-                else if (ctx->prec == LBM_FP16_SHIFTED) reinterpret_cast<__half*>(h.data())[k] = __float2half_rn((float)v);
-                else reinterpret_cast<TF*>(h.data())[k] = TF((float)v);  // no derivative
-            }
-    char* dst = static_cast<char*>(ctx->f[ctx->cur]) + I.f_off * ctx->sb;
-    CK(cudaMemcpyAsync(dst, h.data(), h.size(), cudaMemcpyHostToDevice, ctx->stream));
+    const int nx = I.G.nx, ny = I.G.ny, R = pop_rows(ctx, nx);
+    for (int y0 = 0; y0 < ny; y0 += R) {
+        const int rows = std::min(R, ny - y0);
+        const size_t w = (size_t)rows * nx * sizeof(double);
+        CK(cudaMemcpy2DAsync(ctx->scratch, w, f + (size_t)y0 * nx, (size_t)ny * nx * sizeof(double), w, 9,
+                             cudaMemcpyHostToDevice, ctx->stream));
+        CK(launch_put_pops(ctx->prec, ctx->scratch, I, y0, rows, ctx->f[ctx->cur], ctx->stream));
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;
 }
@@ -832,16 +861,17 @@ lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps) {
     // long runs replay a captured graph of GRAPH_STEPS steps (launch-bound
     // small lattices), the remainder is launched directly
     while (nsteps >= GRAPH_STEPS && ctx->graphs_ok) {
-        if (!ctx->graph[ctx->cur] && !capture_graph(ctx, ctx->cur)) {
+        cudaGraphExec_t& ge = ctx->graph[ctx->cur][ctx->steps % ctx->check_every];
+        if (!ge && !capture_graph(ctx, ctx->cur, ctx->steps)) {
             ctx->graphs_ok = false;
             break;
         }
-        CK(cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream));
+        CK(cudaGraphLaunch(ge, ctx->stream));
         ctx->steps += GRAPH_STEPS;
         nsteps -= GRAPH_STEPS;
     }
     for (int32_t k = 0; k < nsteps; ++k) {
-        lbm_status s = enqueue_step(ctx, ctx->stream, ctx->cur, nullptr);
+        lbm_status s = enqueue_step(ctx, ctx->stream, ctx->cur, ctx->steps, nullptr);
         if (s != LBM_OK) return s;
         ctx->cur ^= 1;
         ctx->steps += 1;
@@ -857,16 +887,16 @@ lbm_status lbm_step_timed(lbm_ctx* ctx, int32_t nsteps, double* ms_step, double*
     // the event before the fluid kernel only when its time is asked for: it
     // keeps the fluid kernel from starting before the spreading kernel ends
     const bool mid = ms_fluid != nullptr;
-    cudaGraphExec_t* set = mid ? ctx->timed : ctx->timed0;
     for (int32_t k = 0; k < nsteps; ++k) {
         // each step is a replay of its captured one-step graph (as lbm_step
         // replays steps), with the timing events inside it
-        if (ctx->timed_ok && !set[ctx->cur] && !capture_timed(ctx, ctx->cur, mid)) ctx->timed_ok = false;
+        cudaGraphExec_t& ge = (mid ? ctx->timed : ctx->timed0)[ctx->cur][watched(ctx, ctx->steps) ? 1 : 0];
+        if (ctx->timed_ok && !ge && !capture_timed(ctx, ctx->cur, ctx->steps, mid)) ctx->timed_ok = false;
         if (ctx->timed_ok) {
-            CK(cudaGraphLaunch(set[ctx->cur], ctx->stream));
+            CK(cudaGraphLaunch(ge, ctx->stream));
         } else {
             CK(cudaEventRecord(ctx->ev[0], ctx->stream));
-            lbm_status s = enqueue_step(ctx, ctx->stream, ctx->cur, mid ? ctx->ev[1] : nullptr);
+            lbm_status s = enqueue_step(ctx, ctx->stream, ctx->cur, ctx->steps, mid ? ctx->ev[1] : nullptr);
             if (s != LBM_OK) return s;
             CK(cudaEventRecord(ctx->ev[2], ctx->stream));
         }
@@ -887,6 +917,17 @@ lbm_status lbm_step_timed(lbm_ctx* ctx, int32_t nsteps, double* ms_step, double*
 lbm_status lbm_sync(lbm_ctx* ctx) {
     if (!ctx) return LBM_EINVAL;
     return device_error(ctx);
+}
+
+lbm_status lbm_inject_status(lbm_ctx* ctx, int32_t status) {
+    if (!ctx) return LBM_EINVAL;
+    unsigned bits = 0;
+    if (status == LBM_EDOMAIN) bits = ERR_DOMAIN;
+    else if (status == LBM_ENONFINITE) bits = ERR_NONFINITE;
+    else if (status == LBM_ETIMEOUT) bits = ERR_TIMEOUT;
+    else return fail(ctx, LBM_EINVAL, "only LBM_EDOMAIN, LBM_ENONFINITE and LBM_ETIMEOUT can be injected");
+    CK(launch_raise(ctx->err, bits, ctx->stream));
+    return LBM_OK;
 }
 
 lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* ux, double* uy) {
@@ -984,6 +1025,14 @@ namespace {
 // device that loads this library, until the process exits.
 static __device__ __align__(256) unsigned char g_ib_scratch[LBM_STATIC_SCRATCH_BYTES];
 
+// the limits of the header hold in every precision: the per-block sums of
+// the widest particle type and the widest spreading record fit
+static_assert(3 * ((size_t)LBM_STATIC_MAX_MARKERS / MB + LBM_STATIC_MAX_PARTICLES + 1) * sizeof(TD) + 256 +
+                      (size_t)LBM_STATIC_MAX_PARTICLES * (sizeof(unsigned) + sizeof(int4)) + 512 +
+                      (size_t)LBM_STATIC_MAX_MARKERS * sizeof(Rec<TF>) <=
+                  LBM_STATIC_SCRATCH_BYTES,
+              "the static scratch must hold the largest context the header allows");
+
 constexpr int MAX_DEVICES = 64;
 std::mutex g_scratch_mutex;
 void* g_scratch_addr[MAX_DEVICES] = {};
@@ -1042,7 +1091,8 @@ extern "C" lbm_status lbm_step_static(lbm_ctx* ctx, int32_t nsteps) {
             CK(launch_markers(ctx->prec, pa, ctx->nblk, ctx->stream));
             CK(launch_spread(ctx->prec, spread_args(ctx, pa), ctx->np, spread_tiles(ctx), ctx->stream));
         }
-        lbm_status s = launch_fluid_step(ctx, ctx->stream, ctx->cur, ctx->variant, ctx->np > 0);
+        lbm_status s = launch_fluid_step(ctx, ctx->stream, ctx->cur, ctx->variant, ctx->np > 0,
+                                         watched(ctx, ctx->steps));
         if (s != LBM_OK) return s;
         ctx->cur ^= 1;
         ctx->steps += 1;

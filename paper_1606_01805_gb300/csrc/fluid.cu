@@ -1,261 +1,12 @@
 // fluid.cu -- lattice kernels: initial field, the fused pull-stream /
 // Zou-He / moments / forced-BGK collide step, and field extraction.
-#include "lbib_device.cuh"
+#include "fluid_core.cuh"
 
 namespace lbib {
 
 namespace {
 
 constexpr int BY = 8;  // rows per block of the init and field kernels
-
-// BGK relaxation of Eq. 4 towards the shifted equilibrium f~eq_i = f_eq_i - w_i
-// (Eq. 2), plus the Guo term (Eq. 5), in place on v:
-//   v_i <- (1 - omega) v_i + omega f~eq_i + G_i.
-// Written over opposite velocity pairs (i, i'): with e_i' = -e_i both terms
-// split into a part even in e (shared) and a part odd in e (sign-flipped),
-// and their sum collects into
-//   omega f~eq_i + G_i = w (K0 + eu (a eu + b eF)) +- 3 w (c eu + cf eF)
-// with eu = e.u, eF = e.F, c = omega rho, a = 4.5 c, cf = 1 - omega / 2,
-// b = 9 cf and K0 = omega drho - 1.5 c u.u - 3 cf u.F (the rest population's
-// value, w = 4/9, has eu = eF = 0).
-template <class C>
-__device__ __forceinline__ void collide(C v[9], C drho, C ux, C uy, C Fx, C Fy, C omega) {
-    const C rho = C(1) + drho;
-    const C usq = ux * ux + uy * uy;
-    const C cf = C(1) - C(0.5) * omega;
-    const C uF = ux * Fx + uy * Fy;
-    const C keep = C(1) - omega;
-    const C c = omega * rho, a = C(4.5) * c, b = C(9) * cf;
-    const C K0 = omega * drho - C(1.5) * c * usq - C(3) * cf * uF;
-    v[0] = keep * v[0] + C(4.0 / 9.0) * K0;
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        // pairs (1,3), (2,4), (5,7), (6,8): i has e = (ex, ey), i' has -e
-        const int i = p == 0 ? 1 : p == 1 ? 2 : p == 2 ? 5 : 6;
-        const int j = p == 0 ? 3 : p == 1 ? 4 : p == 2 ? 7 : 8;
-        const C w = C(wt(i));
-        const C eu = C(cx(i)) * ux + C(cy(i)) * uy;
-        const C eF = C(cx(i)) * Fx + C(cy(i)) * Fy;
-        const C even = w * (K0 + eu * (a * eu + b * eF));
-        const C odd = C(3) * w * (c * eu + cf * eF);
-        v[i] = keep * v[i] + (even + odd);
-        v[j] = keep * v[j] + (even - odd);
-    }
-}
-
-// N consecutive storage elements starting at an N-aligned index
-template <class S, class C, int N> struct Vec;
-template <class S, class C> struct Vec<S, C, 1> {
-    static __device__ __forceinline__ void load(const S* p, C v[1]) { v[0] = ld<S, C>(p); }
-    static __device__ __forceinline__ void store(S* p, const C v[1]) { st<S, C>(p, v[0]); }
-};
-template <> struct Vec<float, float, 4> {
-    static __device__ __forceinline__ void load(const float* p, float v[4]) {
-        const float4 q = __ldg(reinterpret_cast<const float4*>(p));
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-    }
-    static __device__ __forceinline__ void store(float* p, const float v[4]) {
-        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    }
-};
-template <> struct Vec<double, double, 4> {
-    static __device__ __forceinline__ void load(const double* p, double v[4]) {
-        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-        const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-    }
-    static __device__ __forceinline__ void store(double* p, const double v[4]) {
-        reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
-        reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
-    }
-};
-template <> struct Vec<__half, float, 4> {
-    static __device__ __forceinline__ void load(const __half* p, float v[4]) {
-        const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
-        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
-        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-    }
-    static __device__ __forceinline__ void store(__half* p, const float v[4]) {
-        const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
-        uint2 q;
-        q.x = *reinterpret_cast<const unsigned*>(&a);
-        q.y = *reinterpret_cast<const unsigned*>(&b);
-        *reinterpret_cast<uint2*>(p) = q;
-    }
-};
-
-// one cell: moments, IB force, forced BGK collision (Eqs. 2, 4-7)
-template <class C>
-__device__ __forceinline__ void cell_update(C v[9], const Geo& G, C fx_ib, C fy_ib) {
-    C drho, jx, jy;
-    moments<C>(v, drho, jx, jy);
-    const C Fx = geo_g<C>(G, 0) + fx_ib, Fy = geo_g<C>(G, 1) + fy_ib;
-    const C inv = C(1) / (C(1) + drho);
-    const C ux = (jx + C(0.5) * Fx) * inv, uy = (jy + C(0.5) * Fy) * inv;
-    collide<C>(v, drho, ux, uy, Fx, Fy, geo_omega<C>(G));
-}
-
-// Fused step of one tile: N consecutive cells (x0 .. x0+N-1, x0 = N * lane
-// index) of one row per thread, a warp covering 32 N cells of a row, the
-// block BY rows.  Populations move as vectors of N elements: a pull along
-// +-x is a one-lane shuffle of the neighbouring vector, with one extra
-// element load at the warp's two ends.  Cells of the first and last row
-// (y walls, corners, periodic y edges) take the per-cell general path
-// (emitted once, after the fast cells), and so do those of x walls when a
-// thread holds four cells; with one cell per thread the x-wall cells in
-// between stay on the vector path with their Zou-He completion.  The
-// periodic x edge patches the three populations that cross it.
-// PDL: launched with programmatic stream serialization after the spreading
-// kernel: the population loads come first, the force flags and the forces
-// after pdl_wait().  Otherwise the flags are loaded with the populations.
-template <class S, class C, int N, bool PDL>
-__device__ __forceinline__ void fluid_tile(const Geo& G, const S* __restrict__ fin,
-                                           S* __restrict__ fout, C* __restrict__ flb,
-                                           uint8_t* __restrict__ flags, int tx, int y) {
-    const int lane = threadIdx.x;
-    const int x0 = (tx * 32 + lane) * N;
-    if (y >= G.ny) return;  // whole warp (one row)
-    const long long row = (long long)y * G.pitch;
-    // the vector values of cell x0 + k are its pulled populations whenever
-    // all 9 sources are inside (none clamped); on an x wall all but the
-    // three that the Zou-He completion replaces
-    const bool rows_in = y >= 1 && y <= G.ny - 2;
-    const bool any = x0 < G.nx;
-    // force flags of the 32-cell segment of this thread
-    const int seg = y * G.nseg + (x0 >> 5);
-    bool forced = false;
-    if (!PDL) forced = any && flags[seg] != 0;
-
-    C v[9][N];
-    // vector loads for every lane (addresses clamped in-bounds), shuffles by all
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int ys = min(max(y - cy(i), 0), G.ny - 1);
-        const S* rp = fin + (long long)i * G.plane + (long long)ys * G.pitch;
-        const int xa = min(x0, G.pitch - N);
-        C q[N];
-        Vec<S, C, N>::load(rp + xa, q);
-        if (cx(i) == 0) {
-#pragma unroll
-            for (int k = 0; k < N; ++k) v[i][k] = q[k];
-        } else if (cx(i) > 0) {  // source x - 1
-            C left = __shfl_up_sync(0xffffffffu, q[N - 1], 1);
-            if (lane == 0) left = ld<S, C>(rp + max(xa - 1, 0));
-            v[i][0] = left;
-#pragma unroll
-            for (int k = 1; k < N; ++k) v[i][k] = q[k - 1];
-        } else {  // source x + 1
-            C right = __shfl_down_sync(0xffffffffu, q[0], 1);
-            if (lane == 31) right = ld<S, C>(rp + min(xa + N, G.pitch - 1));
-#pragma unroll
-            for (int k = 0; k < N - 1; ++k) v[i][k] = q[k + 1];
-            v[i][N - 1] = right;
-        }
-    }
-    // periodic x: the cells x = 0 and x = nx - 1 get the three populations
-    // that cross the periodic edge by scalar loads; their other six are
-    // already in the vectors, so they stay on the fast path
-    const bool wrap = G.px && rows_in && any;
-    const int ke = G.nx - 1 - x0;  // position of x = nx - 1 in this thread's cells
-    if (wrap && (x0 == 0 || (ke >= 0 && ke < N))) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const S* rp = fin + (long long)i * G.plane + (long long)(y - cy(i)) * G.pitch;
-            if (cx(i) > 0 && x0 == 0) v[i][0] = ld<S, C>(rp + (G.nx - 1));
-            if (cx(i) < 0 && ke >= 0 && ke < N) {
-                const C w0 = ld<S, C>(rp);
-#pragma unroll
-                for (int k = 0; k < N; ++k)
-                    if (k == ke) v[i][k] = w0;
-            }
-        }
-    }
-    if (PDL) {
-        // the populations are on their way; the forces of this step come
-        // from the spreading kernel before this one
-        pdl_wait();
-        pdl_trigger();
-        forced = any && flags[seg] != 0;
-    }
-    if (any) {
-        C fxi[N], fyi[N];
-#pragma unroll
-        for (int k = 0; k < N; ++k) fxi[k] = fyi[k] = C(0);
-        if (forced) {
-#pragma unroll
-            for (int k = 0; k < N; ++k)
-                if (x0 + k < G.nx) {
-                    fxi[k] = flb[row + x0 + k];
-                    fyi[k] = flb[G.plane + row + x0 + k];
-                    flb[row + x0 + k] = C(0);
-                    flb[G.plane + row + x0 + k] = C(0);
-                }
-        }
-        // interior cells from the vector values.  With one cell per thread
-        // so are the cells of an x wall between the two y edges: their six
-        // known populations come from inside the row range, and the Zou-He
-        // completion replaces the three that point into the fluid (with
-        // four cells per thread the completion inlined per cell costs the
-        // vector path registers, so those cells take the general path)
-        constexpr bool XW = N == 1;
-        unsigned edge = 0;  // bit k: cell x0 + k lies on an edge (and inside the lattice)
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const int xk = x0 + k;
-            if (rows_in && xk < G.nx && (wrap || XW || (xk >= 1 && xk <= G.nx - 2))) {
-                C c[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) c[i] = v[i][k];
-                if (XW && !G.px && (xk == 0 || xk == G.nx - 1)) {
-                    const C gx = geo_g<C>(G, 0), gy = geo_g<C>(G, 1);
-                    if (xk == 0) zou_he_edge<1, 0, C>(c, geo_uw<C>(G, 0, 0), geo_uw<C>(G, 0, 1), gx, gy);
-                    else zou_he_edge<-1, 0, C>(c, geo_uw<C>(G, 1, 0), geo_uw<C>(G, 1, 1), gx, gy);
-                }
-                cell_update<C>(c, G, fxi[k], fyi[k]);
-#pragma unroll
-                for (int i = 0; i < 9; ++i) v[i][k] = c[i];
-            } else if (xk < G.nx) {
-                edge |= 1u << k;
-            }
-        }
-        if (edge == 0 && x0 + N - 1 < G.nx) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) Vec<S, C, N>::store(fout + (long long)i * G.plane + row + x0, v[i]);
-        } else {
-#pragma unroll
-            for (int k = 0; k < N; ++k)
-                if (x0 + k < G.nx && !(edge >> k & 1u)) {
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) st<S, C>(fout + (long long)i * G.plane + row + x0 + k, v[i][k]);
-                }
-            // cells on a wall or periodic edge: general pull, wall completion,
-            // collision, one at a time (emitted once, nothing else live)
-#pragma unroll 1
-            for (int k = 0; k < N; ++k) {
-                if (!(edge >> k & 1u)) continue;
-                const int xk = x0 + k;
-                C c[9];
-                pull_general<S, C>(fin, G, xk, y, c);
-                complete_walls<S, C>(fin, G, xk, y, c);
-                C gx = C(0), gy = C(0);
-                if (forced) {  // forces of this cell were read (and zeroed) above
-#pragma unroll
-                    for (int j = 0; j < N; ++j)
-                        if (j == k) {
-                            gx = fxi[j];
-                            gy = fyi[j];
-                        }
-                }
-                cell_update<C>(c, G, gx, gy);
-#pragma unroll
-                for (int i = 0; i < 9; ++i) st<S, C>(fout + (long long)i * G.plane + row + xk, c[i]);
-            }
-        }
-    }
-    __syncwarp();
-    if (forced && (lane & (32 / N - 1)) == 0) flags[seg] = 0;  // one lane per segment
-}
 
 // resident blocks per SM the register budget is sized for: 1024 threads per
 // SM for 4 FP32 / FP16 cells per thread, 512 for FP64 (two registers per
@@ -279,8 +30,9 @@ __global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value) k_
     for (int t = t0; t < min(t0 + TASKS_PER_CTA, a.ntasks); ++t) {
         const int4 task = a.tasks[t];
         const Inst& I = a.insts[task.x];
-        fluid_tile<S, C, N, false>(I.G, fin + I.f_off, fout + I.f_off, flb + I.flb_off,
-                            a.flags + I.flags_off, task.y, task.z * BYt + threadIdx.y);
+        fluid_tile<S, C, N, false>(global_src<S, C, N>(fin + I.f_off, I.G), I.G, fin + I.f_off,
+                                   fout + I.f_off, flb + I.flb_off, a.flags + I.flags_off, task.y,
+                                   task.z * BYt + threadIdx.y, a.check, a.err);
     }
 }
 
@@ -290,9 +42,10 @@ __global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value) k_
 template <class S, class C, int N, int BYt, bool PDL>
 __global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value)
     k_fluid_one(FluidArgs a, Inst I) {
-    fluid_tile<S, C, N, PDL>(I.G, static_cast<const S*>(a.fin) + I.f_off, static_cast<S*>(a.fout) + I.f_off,
-                        static_cast<C*>(a.flb) + I.flb_off, a.flags + I.flags_off, blockIdx.x,
-                        blockIdx.y * BYt + threadIdx.y);
+    const S* fin = static_cast<const S*>(a.fin) + I.f_off;
+    fluid_tile<S, C, N, PDL>(global_src<S, C, N>(fin, I.G), I.G, fin, static_cast<S*>(a.fout) + I.f_off,
+                             static_cast<C*>(a.flb) + I.flb_off, a.flags + I.flags_off, blockIdx.x,
+                             blockIdx.y * BYt + threadIdx.y, a.check, a.err);
 }
 
 // initial post-collision field f* = f^eq(rho, u) (Eq. 2), shifted; R is the
@@ -322,6 +75,30 @@ __global__ void k_init(S* f, Geo G, int kind, double U0) {
     }
 }
 
+// host-layout populations <-> stored shifted populations, a chunk of rows
+// [y0, y0 + rows) at a time: h is [9][rows][nx] doubles of unshifted f_i;
+// the storage holds f_i - w_i in S (the tangent mode: no derivative)
+template <class S, class C>
+__global__ void k_put_pops(const double* __restrict__ h, Geo G, int y0, int rows, S* __restrict__ f) {
+    const int x = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * BY + threadIdx.y;
+    if (x >= G.nx || r >= rows) return;
+    const long long c = (long long)(y0 + r) * G.pitch + x, k = (long long)r * G.nx + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const double v = h[(long long)i * rows * G.nx + k] - wt(i);
+        st<S, C>(f + (long long)i * G.plane + c, C(static_cast<typename DualTraits<C>::value>(v)));
+    }
+}
+template <class S, class C>
+__global__ void k_get_pops(const S* __restrict__ f, Geo G, int y0, int rows, double* __restrict__ h) {
+    const int x = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * BY + threadIdx.y;
+    if (x >= G.nx || r >= rows) return;
+    const long long c = (long long)(y0 + r) * G.pitch + x, k = (long long)r * G.nx + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        h[(long long)i * rows * G.nx + k] = (double)value_of(ld<S, C>(f + (long long)i * G.plane + c)) + wt(i);
+}
+
 __device__ __forceinline__ void put_tangents(double, double*, long long) {}
 __device__ __forceinline__ void put_tangents(float, double*, long long) {}
 __device__ __forceinline__ void put_tangents(const TF& v, double* out, long long stride) {
@@ -333,8 +110,9 @@ template <class S, class C>
 __global__ void k_fields(FieldArgs a) {
     const int x = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * BY + threadIdx.y;
     if (x >= a.I.G.nx || r >= a.rows) return;
-    C rho, ux, uy;
-    node_fields<S, C>(static_cast<const S*>(a.f) + a.I.f_off, a.I.G, &a.I.G, x, a.y0 + r, rho, ux, uy);
+    C drho, ux, uy;
+    node_fields<S, C>(static_cast<const S*>(a.f) + a.I.f_off, a.I.G, &a.I.G, x, a.y0 + r, drho, ux, uy);
+    const C rho = C(1) + drho;
     const long long k = (long long)r * a.I.G.nx + x;
     a.rho[k] = (double)value_of(rho);
     a.ux[k] = (double)value_of(ux);
@@ -433,6 +211,37 @@ int fluid_blocks_per_sm(int prec, int variant) {
     if (prec == LBM_FP32) return blocks_t<float, float>(variant);
     if (prec == LBM_FP16_SHIFTED) return blocks_t<__half, float>(variant);
     return blocks_v<TF, TF, 2>();
+}
+
+cudaError_t launch_put_pops(int prec, const double* h, const Inst& I, int y0, int rows, void* fbuf,
+                            cudaStream_t s) {
+    const dim3 b(32, BY), g = grid_for(I.G.nx, rows);
+    if (prec == LBM_FP64) k_put_pops<double, double><<<g, b, 0, s>>>(h, I.G, y0, rows, (double*)fbuf + I.f_off);
+    else if (prec == LBM_FP32) k_put_pops<float, float><<<g, b, 0, s>>>(h, I.G, y0, rows, (float*)fbuf + I.f_off);
+    else if (prec == LBM_FP16_SHIFTED)
+        k_put_pops<__half, float><<<g, b, 0, s>>>(h, I.G, y0, rows, (__half*)fbuf + I.f_off);
+    else k_put_pops<TF, TF><<<g, b, 0, s>>>(h, I.G, y0, rows, (TF*)fbuf + I.f_off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_pops(int prec, const void* fbuf, const Inst& I, int y0, int rows, double* h,
+                            cudaStream_t s) {
+    const dim3 b(32, BY), g = grid_for(I.G.nx, rows);
+    if (prec == LBM_FP64)
+        k_get_pops<double, double><<<g, b, 0, s>>>((const double*)fbuf + I.f_off, I.G, y0, rows, h);
+    else if (prec == LBM_FP32)
+        k_get_pops<float, float><<<g, b, 0, s>>>((const float*)fbuf + I.f_off, I.G, y0, rows, h);
+    else if (prec == LBM_FP16_SHIFTED)
+        k_get_pops<__half, float><<<g, b, 0, s>>>((const __half*)fbuf + I.f_off, I.G, y0, rows, h);
+    else k_get_pops<TF, TF><<<g, b, 0, s>>>((const TF*)fbuf + I.f_off, I.G, y0, rows, h);
+    return cudaGetLastError();
+}
+
+__global__ void k_raise(unsigned* err, unsigned bits) { atomicOr(err, bits); }
+
+cudaError_t launch_raise(unsigned* err, unsigned bits, cudaStream_t s) {
+    k_raise<<<1, 1, 0, s>>>(err, bits);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fields(int prec, const FieldArgs& a, cudaStream_t s) {

@@ -219,14 +219,15 @@ __device__ __forceinline__ void moments(const C v[9], C& drho, C& jx, C& jy) {
     jy = (v[2] - v[4]) + (v[5] - v[8]) + (v[6] - v[7]);
 }
 
-// Density and velocity u* (constant force with its half step, no IB force)
-// in the compute precision C, from shifted populations v.
+// Density deviation drho = rho - 1 and velocity u* (constant force with its
+// half step, no IB force) in the compute precision C, from shifted
+// populations v.  drho is the sum of the shifted values themselves, so it
+// carries no rounding of the 1 (FP32 would hold rho - 1 only to 6e-8).
 template <class C>
-__device__ __forceinline__ void fields_of(const C v[9], const Geo& G, C& rho, C& ux, C& uy) {
-    C d, jx, jy;
-    moments<C>(v, d, jx, jy);
-    rho = C(1) + d;
-    const C inv = C(1) / rho;
+__device__ __forceinline__ void fields_of(const C v[9], const Geo& G, C& drho, C& ux, C& uy) {
+    C jx, jy;
+    moments<C>(v, drho, jx, jy);
+    const C inv = C(1) / (C(1) + drho);
     ux = (jx + C(0.5) * geo_g<C>(G, 0)) * inv;
     uy = (jy + C(0.5) * geo_g<C>(G, 1)) * inv;
 }
@@ -235,7 +236,7 @@ __device__ __forceinline__ void fields_of(const C v[9], const Geo& G, C& rho, C&
 // of the marker kernels stay small
 template <class S, class C>
 __device__ __noinline__ bool node_fields_general(const S* __restrict__ f, const Geo& G, int ix,
-                                                 int iy, C& rho, C& ux, C& uy) {
+                                                 int iy, C& drho, C& ux, C& uy) {
     if (ix < 0 || ix >= G.nx) {
         if (!G.px) return false;
         ix = ((ix % G.nx) + G.nx) % G.nx;
@@ -247,26 +248,26 @@ __device__ __noinline__ bool node_fields_general(const S* __restrict__ f, const 
     C v[9];
     pull_general<S, C>(f, G, ix, iy, v);
     complete_walls<S, C>(f, G, ix, iy, v);
-    fields_of<C>(v, G, rho, ux, uy);
+    fields_of<C>(v, G, drho, ux, uy);
     return true;
 }
 
-// rho, u* at the unwrapped node (ix, iy); false if it lies across a wall.
+// rho - 1, u* at the unwrapped node (ix, iy); false if it lies across a wall.
 // Gg is the same geometry in global memory, for the out-of-line wrap / wall
 // path (G itself may live in the kernel's parameters).
 template <class S, class C>
 __device__ __forceinline__ bool node_fields(const S* __restrict__ f, const Geo& G, const Geo* Gg, int ix,
-                                            int iy, C& rho, C& ux, C& uy) {
+                                            int iy, C& drho, C& ux, C& uy) {
     if (ix > 0 && ix < G.nx - 1 && iy > 0 && iy < G.ny - 1) {
         C v[9];
         const long long c = (long long)iy * G.pitch + ix;
 #pragma unroll
         for (int i = 0; i < 9; ++i)
             v[i] = ld<S, C>(f + (long long)i * G.plane + c - (long long)cy(i) * G.pitch - cx(i));
-        fields_of<C>(v, G, rho, ux, uy);
+        fields_of<C>(v, G, drho, ux, uy);
         return true;
     }
-    return node_fields_general<S, C>(f, *Gg, ix, iy, rho, ux, uy);
+    return node_fields_general<S, C>(f, *Gg, ix, iy, drho, ux, uy);
 }
 
 // --------------------------------------------------------------- MLS ----

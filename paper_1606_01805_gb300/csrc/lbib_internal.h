@@ -156,6 +156,8 @@ struct FluidArgs {
     const Inst* insts;
     const int4* tasks;
     int ntasks;
+    int check;                // watchdog: flag a non-positive density or a non-finite value
+    unsigned* err;
 };
 
 constexpr int TASKS_PER_CTA = 4;  // consecutive tiles a CTA of the task-list kernel takes
@@ -185,6 +187,15 @@ cudaError_t launch_fluid(int prec, int variant, const FluidArgs& a, const Inst* 
                          cudaStream_t s, bool pdl);
 int fluid_blocks_per_sm(int prec, int variant);
 cudaError_t launch_fields(int prec, const FieldArgs& a, cudaStream_t s);
+// host-layout populations ([9][rows][nx] unshifted doubles at device
+// address h) into / out of the stored shifted populations of rows
+// [y0, y0 + rows) of lattice I in population buffer fbuf
+cudaError_t launch_put_pops(int prec, const double* h, const Inst& I, int y0, int rows, void* fbuf,
+                            cudaStream_t s);
+cudaError_t launch_get_pops(int prec, const void* fbuf, const Inst& I, int y0, int rows, double* h,
+                            cudaStream_t s);
+// OR `bits` into the device error word, as a kernel that detects an error does
+cudaError_t launch_raise(unsigned* err, unsigned bits, cudaStream_t s);
 cudaError_t launch_probes(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s);
 cudaError_t launch_markers(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s);
 cudaError_t launch_spread(int prec, const SpreadArgs& a, int np, int tiles, cudaStream_t s);

@@ -323,33 +323,36 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
     pdl_trigger();
     if (lane == 0 && bk.y == P->m0)  // the particle's first block resets its box
         a.boxes[bk.x] = make_int4(INT_MAX, INT_MAX, INT_MIN, INT_MIN);
-    // node fields first (their loads overlap the FP64 work of the solve)
+    // node fields first (their loads overlap the FP64 work of the solve);
+    // the density as rho - 1, whose fit at the probe then needs no
+    // cancellation against 1 (partition of unity: rho_P - 1 = sum phi (rho - 1))
     C rk[3], uk[3], vk[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        rk[j] = C(1); uk[j] = C(0); vk[j] = C(0);
+        rk[j] = C(0); uk[j] = C(0); vk[j] = C(0);
         if (j < M.nk && active) {
             const int k = M.kk[j];
             if (!node_fields<S, C>(f, G, Gg, M.i0 + k % 3, M.j0 + k / 3, rk[j], uk[j], vk[j])) {
                 err |= ERR_DOMAIN;
-                rk[j] = C(1); uk[j] = C(0); vk[j] = C(0);
+                rk[j] = C(0); uk[j] = C(0); vk[j] = C(0);
             }
         }
     }
     M.build(a.weight, lx, ly, active);
-    // MLS fit of rho and grad u at the probe (Section 2.3)
-    C r = C(0), uxx = C(0), uxy = C(0), uyx = C(0), uyy = C(0);
+    // MLS fit of rho - 1 and grad u at the probe (Section 2.3)
+    C dr = C(0), uxx = C(0), uxy = C(0), uyx = C(0), uyy = C(0);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         if (j < M.nk && active) {
-            r += M.phi[j] * rk[j];
+            dr += M.phi[j] * rk[j];
             uxx += M.dpx[j] * uk[j];
             uxy += M.dpy[j] * uk[j];
             uyx += M.dpx[j] * vk[j];
             uyy += M.dpy[j] * vk[j];
         }
     }
-    r = quad_sum(r); uxx = quad_sum(uxx); uxy = quad_sum(uxy); uyx = quad_sum(uyx); uyy = quad_sum(uyy);
+    dr = quad_sum(dr); uxx = quad_sum(uxx); uxy = quad_sum(uxy); uyx = quad_sum(uyx); uyy = quad_sum(uyy);
+    const C r = C(1) + dr;  // rho_P
     C cF[3] = {C(0), C(0), C(0)};  // this marker's force and torque (quad leader)
     if (active && q == 0) {
         // change of the marker's rigid velocity u + omega z x r between the
@@ -359,7 +362,7 @@ __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
         const C drx = dc * g.rx - ds * g.ry, dry = ds * g.rx + dc * g.ry;
         const C dvx = pc.v[PC_DU] - (dw * ry + w1 * dry);
         const C dvy = pc.v[PC_DV] + (dw * rx + w1 * drx);
-        const C p = C(CS2) * (r - C(1)) + r * C(PROBE) * (dvx * nx + dvy * ny);
+        const C p = C(CS2) * dr + r * C(PROBE) * (dvx * nx + dvy * ny);
         const C mu = r * C(CS2 * (G.tau - 0.5));
         const C txx = C(2) * mu * uxx, tyy = C(2) * mu * uyy, txy = mu * (uxy + uyx);
         const C tx = txx * nx + txy * ny - p * nx;

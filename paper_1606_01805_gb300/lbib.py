@@ -33,7 +33,7 @@ LBM_W_EXP, LBM_W_CUBIC, LBM_W_QUARTIC, LBM_W_COSINE, LBM_W_POLY = range(5)
 
 # every symbol include/lbib.h declares
 EXPORTS = ["lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "lbm_step_timed",
-           "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
+           "lbm_sync", "lbm_inject_status", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
            "lbm_get_particles", "lbm_steps_done", "lbm_last_error", "lbm_destroy",
            "lbm_step_static", "lbm_batch_workspace_bytes", "lbm_init_batch", "lbm_instances",
            "lbm_add_particle_to", "lbm_get_instance_fields", "lbm_get_instance_populations",
@@ -52,6 +52,7 @@ class lbm_config(C.Structure):
         ("weight", C.c_int32), ("marker_spacing", C.c_double),
         ("max_particles", C.c_int32), ("max_markers", C.c_int32),
         ("cuda_stream", C.c_void_p), ("d_workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
+        ("check_every", C.c_int32),
     ]
 
 
@@ -96,6 +97,7 @@ def load(path: os.PathLike | str | None = None):
     L.lbm_step.argtypes = [C.c_void_p, C.c_int32]
     L.lbm_step_timed.argtypes = [C.c_void_p, C.c_int32, _dp, _dp]
     L.lbm_sync.argtypes = [C.c_void_p]
+    L.lbm_inject_status.argtypes = [C.c_void_p, C.c_int32]
     L.lbm_get_fields.argtypes = [C.c_void_p, _dp, _dp, _dp]
     L.lbm_get_populations.argtypes = [C.c_void_p, _dp]
     L.lbm_set_populations.argtypes = [C.c_void_p, _dp]
@@ -125,7 +127,7 @@ def load(path: os.PathLike | str | None = None):
     L.lbm_get_particle_tangents.argtypes = [C.c_void_p, _dp, C.c_int32, C.POINTER(C.c_int32)]
     L.lbm_get_field_tangents.argtypes = [C.c_void_p, C.c_int32, _dp, _dp, _dp]
     for fn in ("lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "lbm_step_timed",
-               "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
+               "lbm_sync", "lbm_inject_status", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
                "lbm_get_particles", "lbm_step_static", "lbm_batch_workspace_bytes",
                "lbm_init_batch", "lbm_add_particle_to", "lbm_get_instance_fields",
                "lbm_get_instance_populations", "lbm_set_instance_populations", "lbm_get_tile",
@@ -142,7 +144,8 @@ def _ptr(a: np.ndarray):
 
 def make_config(nx, ny, tau, bc=(0, 0, 1, 1), wall_u=((0, 0),) * 4, body_force=(0, 0),
                 gravity=(0, 0), precision=LBM_FP32, init=LBM_INIT_REST, init_u=0.0,
-                weight=LBM_W_EXP, marker_spacing=0.3, max_particles=16, max_markers=16384):
+                weight=LBM_W_EXP, marker_spacing=0.3, max_particles=16, max_markers=16384,
+                check_every=1):
     c = lbm_config()
     c.nx, c.ny, c.tau = nx, ny, tau
     for i in range(4):
@@ -153,6 +156,7 @@ def make_config(nx, ny, tau, bc=(0, 0, 1, 1), wall_u=((0, 0),) * 4, body_force=(
     c.precision, c.init, c.init_u = precision, init, init_u
     c.weight, c.marker_spacing = weight, marker_spacing
     c.max_particles, c.max_markers = max_particles, max_markers
+    c.check_every = check_every
     return c
 
 
@@ -219,19 +223,27 @@ class Simulation:
     def sync(self):
         self._check(load().lbm_sync(self._h), "lbm_sync")
 
+    def inject_status(self, status):
+        """Test hook: the device flag of `status`, as a kernel sets it."""
+        self._check(load().lbm_inject_status(self._h, status), "lbm_inject_status")
+
     @property
     def steps_done(self):
         return load().lbm_steps_done(self._h)
 
-    def fields(self):
-        r = np.empty((self.ny, self.nx))
-        ux = np.empty_like(r)
-        uy = np.empty_like(r)
+    def fields(self, out=None):
+        """(rho, ux, uy) as [ny][nx] arrays; `out`: three caller arrays
+        (C-contiguous float64, e.g. in pinned memory) to fill instead."""
+        r, ux, uy = out if out is not None else [np.empty((self.ny, self.nx)) for _ in range(3)]
+        for a in (r, ux, uy):
+            assert a.dtype == np.float64 and a.shape == (self.ny, self.nx) and a.flags.c_contiguous
         self._check(load().lbm_get_fields(self._h, _ptr(r), _ptr(ux), _ptr(uy)), "lbm_get_fields")
         return r, ux, uy
 
-    def populations(self):
-        f = np.empty((9, self.ny, self.nx))
+    def populations(self, out=None):
+        """stored populations [9][ny][nx]; `out`: a caller array to fill"""
+        f = out if out is not None else np.empty((9, self.ny, self.nx))
+        assert f.dtype == np.float64 and f.shape == (9, self.ny, self.nx) and f.flags.c_contiguous
         self._check(load().lbm_get_populations(self._h, _ptr(f)), "lbm_get_populations")
         return f
 
@@ -322,6 +334,7 @@ class Batch:
     step = Simulation.step
     step_timed = Simulation.step_timed
     sync = Simulation.sync
+    inject_status = Simulation.inject_status
     particles = Simulation.particles
     steps_done = Simulation.steps_done
 

@@ -61,7 +61,8 @@ def test_struct_layouts_match_the_header(tmp_path):
 @pytest.mark.parametrize("bad", [dict(tau=0.5), dict(nx=2), dict(ny=2),
                                  dict(bc=(0, 1, 1, 1)), dict(bc=(0, 0, 0, 1)),
                                  dict(precision=7), dict(weight=9),
-                                 dict(init=1, bc=(0, 0, 0, 0))])
+                                 dict(init=1, bc=(0, 0, 0, 0)), dict(check_every=3),
+                                 dict(check_every=64), dict(check_every=-1)])
 def test_invalid_configurations_rejected(lib, bad):
     kw = dict(nx=40, ny=30, tau=0.8)
     kw.update(bad)
@@ -88,6 +89,7 @@ def test_workspace_size_grows_with_lattice_and_precision(lib):
 def test_null_arguments(lib):
     assert lib.lbm_step(None, 1) == lbib.LBM_EINVAL
     assert lib.lbm_sync(None) == lbib.LBM_EINVAL
+    assert lib.lbm_inject_status(None, lbib.LBM_ETIMEOUT) == lbib.LBM_EINVAL
     assert lib.lbm_steps_done(None) == 0
     assert lib.lbm_last_error(None) == b"null context"
     lib.lbm_destroy(None)

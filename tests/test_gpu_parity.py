@@ -304,3 +304,26 @@ def test_fp16_shifted_storage_error_per_field(name):
     if wl.particles:
         dpos, dom = particle_errs(ref.particles()[0], gpu.particles()[0], omega_floor=1e-6)
         assert dpos < bounds["pos"] and dom < bounds["om"]
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32, FP16S])
+def test_population_round_trip_through_staging(prec):
+    """lbm_set_populations / lbm_get_populations move the host array through
+    the device staging area in chunks of rows (18 chunks here) and convert
+    on the device: the round trip returns f rounded once to the storage
+    precision of f - w_i."""
+    nx, ny = 3000, 2000
+    sim = lbib.Simulation(nx, ny, 0.8, precision=prec, bc=(0, 0, 0, 0))
+    w = rest_populations()
+    f = W.random_populations(nx, ny, seed=9, base=w)
+    sim.set_populations(f)
+    got = sim.populations()
+    d = f - w.reshape(9, 1, 1)
+    if prec == FP64:
+        want = d + w.reshape(9, 1, 1)
+    elif prec == FP32:
+        want = d.astype(np.float32).astype(np.float64) + w.reshape(9, 1, 1)
+    else:
+        want = d.astype(np.float32).astype(np.float16).astype(np.float64) + w.reshape(9, 1, 1)
+    np.testing.assert_array_equal(got, want)
+    sim.close()
