@@ -184,6 +184,8 @@ def time_device(wl, prec, steps, warmup, flush, pick_tile=False):
         from paper_1606_01805_gb300 import lbib
 
         for v in range(lbib.LBM_TILE_VARIANTS):
+            if not lbib.tile_info(v, prec)[3]:
+                continue
             sim.set_tile(v)
             for _ in range(3):
                 do_flush()

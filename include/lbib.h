@@ -196,6 +196,19 @@ lbm_status lbm_sync(lbm_ctx* ctx);
 lbm_status lbm_inject_status(lbm_ctx* ctx, int32_t status);
 
 /*
+ * Test hook of the bounded device waits (the paper has no counterpart):
+ * the next step's fluid launch, which must be a staged variant (6..9, see
+ * lbm_get_tile; else LBM_EINVAL), arms the mbarrier of its first CTA's
+ * first tile for 16 bytes more than its copies bring, so that the CTA's
+ * wait for it runs out after wait_cycles clock cycles (1e6 .. 2e9, else
+ * LBM_EINVAL; the kernels' own limit is 2e9, about a second).  The CTA
+ * then sets the LBM_ETIMEOUT flag, lets its copies in flight land and
+ * returns without computing its tiles; the step is launched directly (not
+ * from a captured graph).  Nothing faults; lbm_sync reports LBM_ETIMEOUT.
+ */
+lbm_status lbm_inject_stall(lbm_ctx* ctx, int64_t wait_cycles);
+
+/*
  * Density and velocity (host, nx*ny doubles each, y-major) of the
  * populations after streaming of the stored state, i.e. the moments of
  * Eqs. 6-7 at the start of the next step (constant body force with its
@@ -306,17 +319,29 @@ lbm_status lbm_get_instance_populations(lbm_ctx* ctx, int32_t instance, double* 
 lbm_status lbm_set_instance_populations(lbm_ctx* ctx, int32_t instance, const double* f);
 
 /*
- * Tile shape of the fused fluid kernel.  lbm_init / lbm_init_batch time each
- * shape on the context's own lattices and keep the fastest (all shapes give
- * bit-identical results); lbm_get_tile reports the choice (index, cells per
- * thread, rows per block) and lbm_set_tile forces shape `variant`
- * (0 .. LBM_TILE_VARIANTS - 1; LBM_EINVAL otherwise).  The shapes: 4 cells
- * per thread in blocks of 8 or 4 rows, and 1 cell per thread in blocks of
- * 8 rows.  The tangent mode has shape 2 only.
+ * Tile variant of the fused fluid kernel.  lbm_init / lbm_init_batch time
+ * every variant the precision has on the context's own lattices and keep
+ * the fastest (all variants give bit-identical results); lbm_get_tile
+ * reports the choice (index, cells per thread, rows per tile) and
+ * lbm_set_tile forces variant `variant` (LBM_EINVAL for an index out of
+ * 0 .. LBM_TILE_VARIANTS - 1 or one the precision does not have).
+ * lbm_tile_info describes any variant: cells per thread (the tile is 32
+ * times as wide), rows per tile, and the stages of a staged variant (0 for
+ * a direct one), and whether `precision` has it (returns LBM_OK) or not
+ * (LBM_EINVAL).  The variants:
+ *   0..5  direct kernels, one CTA per tile, streamed populations loaded
+ *         from global memory: 4 x 8, 4 x 4, 1 x 8, 2 x 8, 2 x 4, 1 x 4;
+ *   6..9  the persistent kernel that stages each tile's rows in shared
+ *         memory with bulk asynchronous copies, 8 rows per tile: 4 cells
+ *         per thread with 2 or 3 stages, 2 cells with 3 or 4 stages
+ *         (LBM_FP32 and LBM_FP16_SHIFTED only).
+ * LBM_FP64 has variants 0..5, the tangent mode variant 2 only.
  */
-#define LBM_TILE_VARIANTS 3
+#define LBM_TILE_VARIANTS 10
 lbm_status lbm_get_tile(const lbm_ctx* ctx, int32_t* variant, int32_t* cells_per_thread,
                         int32_t* rows_per_block);
+lbm_status lbm_tile_info(int32_t variant, int32_t precision, int32_t* cells_per_thread, int32_t* rows,
+                         int32_t* stages);
 lbm_status lbm_set_tile(lbm_ctx* ctx, int32_t variant);
 
 /*

@@ -18,6 +18,9 @@ using namespace lbib;
 
 namespace {
 constexpr int GRAPH_STEPS = 32;  // even, so a replay returns to the same buffer
+// clock cycles a CTA of the staged fluid kernel waits for a tile's copies
+// before it reports ERR_TIMEOUT (about a second at the GB300's 2.07 GHz)
+constexpr long long WAIT_LIMIT = 2000000000LL;
 }
 
 struct lbm_ctx {
@@ -37,6 +40,11 @@ struct lbm_ctx {
     Inst* insts;
     int4* tasks[N_FLUID_VARIANTS];
     int ntasks[N_FLUID_VARIANTS];
+    // tensor maps of the staged variants: [buffer][cells per thread 2, 4][instance]
+    // on the device, and their host copies; staged_ok: they could be made
+    char* tmaps = nullptr;
+    std::vector<unsigned char> htmaps;
+    bool staged_ok = false;
     int variant = 0;                // fluid tile shape in use
     int sms = 1;
     size_t rsz, psz;                // bytes of the particle real type R / of DParticleT<R>
@@ -61,6 +69,7 @@ struct lbm_ctx {
     int64_t steps = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     int check_every = 1;            // watchdog period of the fluid kernel (steps)
+    long long stall_limit = 0;      // lbm_inject_stall: wait limit of the next step's stalled launch
     // GRAPH_STEPS steps from buffer 0 / 1, starting at a step count of each
     // residue modulo check_every (the watchdog steps sit at fixed places)
     cudaGraphExec_t graph[2][GRAPH_STEPS] = {};
@@ -150,7 +159,7 @@ std::vector<int4> make_tasks(const std::vector<Inst>& insts, int v) {
 
 struct Layout {
     std::vector<Inst> insts;
-    size_t f0, f1, flb, flags, insts_off, tasks[N_FLUID_VARIANTS], parts, poses, blk, partial, count, mg,
+    size_t f0, f1, flb, flags, insts_off, tasks[N_FLUID_VARIANTS], tmaps, parts, poses, blk, partial, count, mg,
         S, recs, boxes, ptab, err, scratch, total;
     int ntasks[N_FLUID_VARIANTS];
     int scratch_rows, scratch_cols, scratch_planes;
@@ -194,6 +203,7 @@ Layout layout(const lbm_config* cfgs, int n) {
         L.tasks[v] = o;
         o = up(o + (size_t)L.ntasks[v] * sizeof(int4));
     }
+    L.tmaps = o; o = up(o + 4 * (size_t)n * TMAP_BYTES);
     L.parts = o; o = up(o + 2 * P * particle_bytes(prec));
     L.poses = o; o = up(o + 2 * P * pose_bytes(prec));
     L.blk = o; o = up(o + NB * sizeof(int4));
@@ -294,15 +304,21 @@ int box_tiles(double rc) {
 }
 int spread_tiles(const lbm_ctx* ctx) { return box_tiles(ctx->rc_max); }
 
+// the tile variants this context can run (the staged ones need their tensor maps)
+bool ctx_variant_ok(const lbm_ctx* ctx, int v) {
+    return variant_valid(ctx->prec, v) && (FLUID_VARIANTS[v].stages == 0 || ctx->staged_ok);
+}
+
 // The fluid kernel's watchdog runs on the steps whose count since init
 // (1-based) is a multiple of check_every.
 bool watched(const lbm_ctx* ctx, int64_t step) { return (step + 1) % ctx->check_every == 0; }
 
 // pdl: launch the fluid kernel with programmatic stream serialization (only
 // right after the spreading kernel: its prologue loads the populations the
-// previous step's fluid kernel wrote); check: the kernel runs its watchdog
+// previous step's fluid kernel wrote); check: the kernel runs its watchdog;
+// stall: the test hook of lbm_inject_stall
 lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v, bool pdl = false,
-                             bool check = false) {
+                             bool check = false, bool stall = false) {
     FluidArgs fa;
     fa.fin = ctx->f[cur];
     fa.fout = ctx->f[cur ^ 1];
@@ -313,10 +329,18 @@ lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v, bool
     fa.ntasks = ctx->ntasks[v];
     fa.err = ctx->err;
     fa.check = check ? 1 : 0;
-    // one CTA per TASKS_PER_CTA tiles: the block scheduler keeps every SM
-    // filled as CTAs finish (the kernel's outer task loop then runs once)
+    fa.stall = stall ? 1 : 0;
+    fa.tmaps = fa.tmap_one = nullptr;
+    if (FLUID_VARIANTS[v].stages) {
+        const size_t k = (size_t)(cur * 2 + (FLUID_VARIANTS[v].cpt == 4 ? 1 : 0)) * ctx->ninst;
+        fa.tmaps = ctx->tmaps + k * TMAP_BYTES;
+        fa.tmap_one = ctx->htmaps.data() + k * TMAP_BYTES;
+    }
+    // direct task-list kernel: one CTA per TASKS_PER_CTA tiles (the block
+    // scheduler keeps every SM filled as CTAs finish)
     const int grid = std::max(1, (fa.ntasks + TASKS_PER_CTA - 1) / TASKS_PER_CTA);
-    CK(launch_fluid(ctx->prec, v, fa, ctx->ninst == 1 ? &ctx->hinst[0] : nullptr, grid, st, pdl));
+    CK(launch_fluid(ctx->prec, v, fa, ctx->ninst == 1 ? &ctx->hinst[0] : nullptr, grid, ctx->sms, st, pdl,
+                    stall ? ctx->stall_limit : WAIT_LIMIT));
     return LBM_OK;
 }
 
@@ -325,8 +349,9 @@ lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v, bool
 // update / markers, spreading) or the fused fluid kernel over every
 // instance (ib = false).  Bookkeeping is the caller's.
 lbm_status enqueue_step_part(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t step, bool ib,
-                             bool pdl = false) {
-    if (!ib) return launch_fluid_step(ctx, st, cur, ctx->variant, pdl && ctx->np > 0, watched(ctx, step));
+                             bool pdl = false, bool stall = false) {
+    if (!ib)
+        return launch_fluid_step(ctx, st, cur, ctx->variant, pdl && ctx->np > 0, watched(ctx, step), stall);
     if (ctx->np == 0) return LBM_OK;
     const ParticleArgs pa = particle_args(ctx, cur);
     CK(launch_probes(ctx->prec, pa, ctx->nblk, st));
@@ -339,11 +364,12 @@ lbm_status enqueue_step_part(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t ste
 // event between the IB kernels and the fluid kernel, which then starts only
 // after it, so that mid -> end times the fluid kernel alone).  Bookkeeping
 // is the caller's.
-lbm_status enqueue_step(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t step, cudaEvent_t mid) {
+lbm_status enqueue_step(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t step, cudaEvent_t mid,
+                        bool stall = false) {
     lbm_status s = enqueue_step_part(ctx, st, cur, step, true);
     if (s != LBM_OK) return s;
     if (mid) CK(cudaEventRecord(mid, st));
-    return enqueue_step_part(ctx, st, cur, step, false, mid == nullptr);
+    return enqueue_step_part(ctx, st, cur, step, false, mid == nullptr, stall);
 }
 
 // Capture GRAPH_STEPS steps starting from buffer `cur` at step count
@@ -423,11 +449,12 @@ void drop_graphs(lbm_ctx* ctx) {
     }
 }
 
-// Autotuner of the fluid tile shape: times every variant on the context's
-// own lattices (fluid kernel only; it reads buffer cur and writes the other
-// one, which the next step overwrites, and no force flag is set yet) and
-// keeps the fastest.  All variants compute the same cells with the same
-// arithmetic, so the choice changes speed only.
+// Autotuner of the fluid tile variant: times every variant the precision
+// has (FLUID_VARIANTS: cells per thread x rows per tile x staging depth) on
+// the context's own lattices (fluid kernel only; it reads buffer cur and
+// writes the other one, which the next step overwrites, and no force flag
+// is set yet) and keeps the fastest.  All variants compute the same cells
+// with the same arithmetic, so the choice changes speed only.
 lbm_status autotune(lbm_ctx* ctx) {
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a));
@@ -439,11 +466,13 @@ lbm_status autotune(lbm_ctx* ctx) {
     }
     for (int v = 0; v < N_FLUID_VARIANTS; ++v) {  // warm every shape first
         best[v] = 1e30f;
+        if (!ctx_variant_ok(ctx, v)) continue;
         lbm_status s = launch_fluid_step(ctx, ctx->stream, ctx->cur, v);
         if (s != LBM_OK) return s;
     }
     for (int round = 0; round < 2; ++round)
         for (int v = 0; v < N_FLUID_VARIANTS; ++v) {
+            if (!ctx_variant_ok(ctx, v)) continue;
             CK(cudaEventRecord(a, ctx->stream));
             for (int k = 0; k < 2; ++k) {
                 lbm_status s = launch_fluid_step(ctx, ctx->stream, ctx->cur, v);
@@ -501,6 +530,7 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
         ctx->tasks[v] = reinterpret_cast<int4*>(b + L.tasks[v]);
         ctx->ntasks[v] = L.ntasks[v];
     }
+    ctx->tmaps = b + L.tmaps;
     ctx->rsz = real_bytes(ctx->prec);
     ctx->psz = particle_bytes(ctx->prec);
     ctx->parts = b + L.parts;
@@ -533,6 +563,20 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
     for (int v = 0; v < N_FLUID_VARIANTS && e == cudaSuccess; ++v)
         e = cudaMemcpyAsync(ctx->tasks[v], tasks[v].data(), tasks[v].size() * sizeof(int4),
                             cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && (ctx->prec == LBM_FP32 || ctx->prec == LBM_FP16_SHIFTED)) {
+        // the staged variants' tensor maps; without them those variants are off
+        ctx->htmaps.assign(4 * (size_t)n * TMAP_BYTES, 0);
+        ctx->staged_ok = true;
+        for (int bf = 0; bf < 2 && ctx->staged_ok; ++bf)
+            for (int c = 0; c < 2 && ctx->staged_ok; ++c)
+                for (int i = 0; i < n && ctx->staged_ok; ++i)
+                    ctx->staged_ok = encode_stage_map(ctx->prec, c ? 4 : 2, ctx->f[bf], L.insts[i],
+                                                      ctx->htmaps.data() + ((bf * 2 + c) * (size_t)n + i) *
+                                                                               TMAP_BYTES) == cudaSuccess;
+        if (ctx->staged_ok)
+            e = cudaMemcpyAsync(ctx->tmaps, ctx->htmaps.data(), ctx->htmaps.size(), cudaMemcpyHostToDevice,
+                                ctx->stream);
+    }
     for (int i = 0; i < n && e == cudaSuccess; ++i)
         e = launch_init(ctx->prec, ctx->f[0], L.insts[i], cfgs[i].init, cfgs[i].init_u, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -858,6 +902,14 @@ lbm_status lbm_set_wall_tangents(lbm_ctx* ctx, int32_t instance, const double* d
 
 lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps) {
     if (!ctx || nsteps < 0) return LBM_EINVAL;
+    if (ctx->stall_limit && nsteps > 0) {  // lbm_inject_stall: this step alone, launched directly
+        lbm_status s = enqueue_step(ctx, ctx->stream, ctx->cur, ctx->steps, nullptr, true);
+        ctx->stall_limit = 0;
+        if (s != LBM_OK) return s;
+        ctx->cur ^= 1;
+        ctx->steps += 1;
+        nsteps -= 1;
+    }
     // long runs replay a captured graph of GRAPH_STEPS steps (launch-bound
     // small lattices), the remainder is launched directly
     while (nsteps >= GRAPH_STEPS && ctx->graphs_ok) {
@@ -917,6 +969,16 @@ lbm_status lbm_step_timed(lbm_ctx* ctx, int32_t nsteps, double* ms_step, double*
 lbm_status lbm_sync(lbm_ctx* ctx) {
     if (!ctx) return LBM_EINVAL;
     return device_error(ctx);
+}
+
+lbm_status lbm_inject_stall(lbm_ctx* ctx, int64_t wait_cycles) {
+    if (!ctx) return LBM_EINVAL;
+    if (!FLUID_VARIANTS[ctx->variant].stages)
+        return fail(ctx, LBM_EINVAL, "the tile variant in use has no staged copies to stall");
+    if (wait_cycles < 1000000 || wait_cycles > WAIT_LIMIT)
+        return fail(ctx, LBM_EINVAL, "wait_cycles must lie in [1e6, 2e9]");
+    ctx->stall_limit = wait_cycles;
+    return LBM_OK;
 }
 
 lbm_status lbm_inject_status(lbm_ctx* ctx, int32_t status) {
@@ -987,11 +1049,21 @@ lbm_status lbm_get_tile(const lbm_ctx* ctx, int32_t* variant, int32_t* cells_per
     return LBM_OK;
 }
 
+lbm_status lbm_tile_info(int32_t variant, int32_t precision, int32_t* cells_per_thread, int32_t* rows,
+                         int32_t* stages) {
+    if (variant < 0 || variant >= N_FLUID_VARIANTS) return LBM_EINVAL;
+    const FluidVariant& fv = FLUID_VARIANTS[variant];
+    if (cells_per_thread) *cells_per_thread = fv.cpt;
+    if (rows) *rows = fv.by;
+    if (stages) *stages = fv.stages;
+    return variant_valid(precision, variant) ? LBM_OK : LBM_EINVAL;
+}
+
 lbm_status lbm_set_tile(lbm_ctx* ctx, int32_t variant) {
     if (!ctx) return LBM_EINVAL;
     if (variant < 0 || variant >= N_FLUID_VARIANTS) return fail(ctx, LBM_EINVAL, "no such tile variant");
-    if (ctx->prec == LBM_FP32_TANGENT && variant != 2)
-        return fail(ctx, LBM_EINVAL, "the tangent mode has tile variant 2 only");
+    if (!ctx_variant_ok(ctx, variant))
+        return fail(ctx, LBM_EINVAL, "the precision has no such tile variant");
     if (variant != ctx->variant) {
         ctx->variant = variant;
         drop_graphs(ctx);  // captured steps launch the old shape

@@ -8,46 +8,6 @@ namespace {
 
 constexpr int BY = 8;  // rows per block of the init and field kernels
 
-// resident blocks per SM the register budget is sized for: 1024 threads per
-// SM for 4 FP32 / FP16 cells per thread, 512 for FP64 (two registers per
-// value), 1280 (FP64: 768) for one cell per thread; 512 for one tangent-mode
-// cell (four registers per value)
-template <class S, int N, int BYt> struct FluidOccupancy {
-    static constexpr int value =
-        (sizeof(S) == 16 ? 2 : (N == 1 ? (sizeof(S) == 8 ? 3 : 5) : (sizeof(S) == 8 ? 2 : 4))) * 8 / BYt;
-};
-
-// fused fluid step over the task list (all instances): CTA b takes the
-// TASKS_PER_CTA consecutive tasks from b * TASKS_PER_CTA (mostly tiles of one
-// lattice, whose task records and descriptor then come from L1 after the
-// first), and further ones a grid apart if the grid is smaller
-template <class S, class C, int N, int BYt>
-__global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value) k_fluid(FluidArgs a) {
-    const S* fin = static_cast<const S*>(a.fin);
-    S* fout = static_cast<S*>(a.fout);
-    C* flb = static_cast<C*>(a.flb);
-    for (int t0 = blockIdx.x * TASKS_PER_CTA; t0 < a.ntasks; t0 += gridDim.x * TASKS_PER_CTA)
-    for (int t = t0; t < min(t0 + TASKS_PER_CTA, a.ntasks); ++t) {
-        const int4 task = a.tasks[t];
-        const Inst& I = a.insts[task.x];
-        fluid_tile<S, C, N, false>(global_src<S, C, N>(fin + I.f_off, I.G), I.G, fin + I.f_off,
-                                   fout + I.f_off, flb + I.flb_off, a.flags + I.flags_off, task.y,
-                                   task.z * BYt + threadIdx.y, a.check, a.err);
-    }
-}
-
-// the same step for a context holding one lattice: its descriptor arrives
-// by value (constant bank) and the grid is the tile grid itself, so no load
-// stands in front of the population loads
-template <class S, class C, int N, int BYt, bool PDL>
-__global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value)
-    k_fluid_one(FluidArgs a, Inst I) {
-    const S* fin = static_cast<const S*>(a.fin) + I.f_off;
-    fluid_tile<S, C, N, PDL>(global_src<S, C, N>(fin, I.G), I.G, fin, static_cast<S*>(a.fout) + I.f_off,
-                             static_cast<C*>(a.flb) + I.flb_off, a.flags + I.flags_off, blockIdx.x,
-                             blockIdx.y * BYt + threadIdx.y, a.check, a.err);
-}
-
 // initial post-collision field f* = f^eq(rho, u) (Eq. 2), shifted; R is the
 // real type of the field (with tangents, the Couette profile carries the
 // derivatives of the wall speeds)
@@ -127,47 +87,6 @@ __global__ void k_fields(FieldArgs a) {
 
 dim3 grid_for(int nx, int rows) { return dim3((nx + 31) / 32, (rows + BY - 1) / BY); }
 
-template <class S, class C, int V>
-cudaError_t launch_fluid_v(const FluidArgs& a, const Inst* one, int grid, cudaStream_t s, bool pdl) {
-    constexpr int N = FLUID_VARIANTS[V].cpt, BYt = FLUID_VARIANTS[V].by;
-    if (one) {
-        const dim3 g((one->G.nx + 32 * N - 1) / (32 * N), (one->G.ny + BYt - 1) / BYt);
-        if (pdl) return launch_k(true, k_fluid_one<S, C, N, BYt, true>, g, dim3(32, BYt), s, a, *one);
-        return launch_k(false, k_fluid_one<S, C, N, BYt, false>, g, dim3(32, BYt), s, a, *one);
-    }
-    // the task-list kernel of a batch is launched without PDL: its CTAs are
-    // small and many, and the flags load is best issued with the populations
-    return launch_k(false, k_fluid<S, C, N, BYt>, dim3(grid), dim3(32, BYt), s, a);
-}
-
-template <class S, class C>
-cudaError_t launch_fluid_t(int variant, const FluidArgs& a, const Inst* one, int grid, cudaStream_t s,
-                           bool pdl) {
-    switch (variant) {
-        case 1: return launch_fluid_v<S, C, 1>(a, one, grid, s, pdl);
-        case 2: return launch_fluid_v<S, C, 2>(a, one, grid, s, pdl);
-        default: return launch_fluid_v<S, C, 0>(a, one, grid, s, pdl);
-    }
-}
-
-template <class S, class C, int V>
-int blocks_v() {
-    constexpr int N = FLUID_VARIANTS[V].cpt, BYt = FLUID_VARIANTS[V].by;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fluid<S, C, N, BYt>, 32 * BYt, 0) != cudaSuccess)
-        n = 1;
-    return n > 0 ? n : 1;
-}
-
-template <class S, class C>
-int blocks_t(int variant) {
-    switch (variant) {
-        case 1: return blocks_v<S, C, 1>();
-        case 2: return blocks_v<S, C, 2>();
-        default: return blocks_v<S, C, 0>();
-    }
-}
-
 }  // namespace
 
 size_t storage_bytes(int prec) {
@@ -195,22 +114,20 @@ cudaError_t launch_init(int prec, void* fbuf, const Inst& I, int kind, double in
     return cudaGetLastError();
 }
 
-// the tangent mode has the one-cell tile only (variant 2): a cell's 9
-// populations with their derivatives already take 36 registers
-cudaError_t launch_fluid(int prec, int variant, const FluidArgs& a, const Inst* one, int grid,
-                         cudaStream_t s, bool pdl) {
+// Fused fluid step with tile variant `variant` (FLUID_VARIANTS): the direct
+// kernels (fluid_direct.cuh) in two translation units, or the staged
+// persistent kernel (fluid_staged.cu).  The tangent mode has the one-cell
+// direct tile only (variant 2): a cell's 9 populations with their
+// derivatives already take 36 registers.
+cudaError_t launch_fluid(int prec, int variant, const FluidArgs& a, const Inst* one, int grid, int sms,
+                         cudaStream_t s, bool pdl, long long wait_limit) {
     if (a.ntasks <= 0) return cudaSuccess;
-    if (prec == LBM_FP64) return launch_fluid_t<double, double>(variant, a, one, grid, s, pdl);
-    if (prec == LBM_FP32) return launch_fluid_t<float, float>(variant, a, one, grid, s, pdl);
-    if (prec == LBM_FP16_SHIFTED) return launch_fluid_t<__half, float>(variant, a, one, grid, s, pdl);
-    return launch_fluid_v<TF, TF, 2>(a, one, grid, s, pdl);
-}
-
-int fluid_blocks_per_sm(int prec, int variant) {
-    if (prec == LBM_FP64) return blocks_t<double, double>(variant);
-    if (prec == LBM_FP32) return blocks_t<float, float>(variant);
-    if (prec == LBM_FP16_SHIFTED) return blocks_t<__half, float>(variant);
-    return blocks_v<TF, TF, 2>();
+    if (!variant_valid(prec, variant)) return cudaErrorInvalidValue;
+    const FluidVariant& fv = FLUID_VARIANTS[variant];
+    if (fv.stages) return launch_fluid_staged(prec, fv.cpt, fv.stages, a, one, sms, s, pdl, wait_limit);
+    cudaError_t e = launch_fluid_direct_a(prec, fv.cpt, fv.by, a, one, grid, s, pdl);
+    if (e == cudaErrorInvalidValue) e = launch_fluid_direct_b(prec, fv.cpt, fv.by, a, one, grid, s, pdl);
+    return e;
 }
 
 cudaError_t launch_put_pops(int prec, const double* h, const Inst& I, int y0, int rows, void* fbuf,

@@ -45,7 +45,8 @@ struct Geo {
 // One lattice of a context (a context holds one or a batch of them).  Its
 // populations start at element f_off of each population buffer, its force
 // field at element flb_off of the force buffer, its flags at byte flags_off.
-struct Inst {
+// 16-byte aligned, so that a kernel can copy it in 16-byte pieces.
+struct alignas(16) Inst {
     Geo G;
     long long f_off, flb_off, flags_off;
 };
@@ -157,17 +158,34 @@ struct FluidArgs {
     const int4* tasks;
     int ntasks;
     int check;                // watchdog: flag a non-positive density or a non-finite value
+    int stall;                // test hook: the staged kernel's first CTA waits for 16 bytes too many
     unsigned* err;
+    // staged variants: the tensor maps of the population buffer read, per
+    // instance (device array of CUtensorMap), and of a single lattice (host)
+    const void* tmaps;
+    const void* tmap_one;
 };
 
 constexpr int TASKS_PER_CTA = 4;  // consecutive tiles a CTA of the task-list kernel takes
 
-// fluid tile shapes: (cells per thread, rows per block); the autotuner picks one
+// fluid tile variants: (cells per thread, rows per block, stages); the
+// autotuner picks one.  stages = 0: a direct kernel (one CTA per tile, the
+// streamed populations loaded from global memory); stages > 0: the
+// persistent kernel that stages that many tiles ahead in shared memory
+// (FP32 and FP16 storage only; 8 rows per tile).
 constexpr int N_FLUID_VARIANTS = LBM_TILE_VARIANTS;
 struct FluidVariant {
-    int cpt, by;
+    int cpt, by, stages;
 };
-constexpr FluidVariant FLUID_VARIANTS[N_FLUID_VARIANTS] = {{4, 8}, {4, 4}, {1, 8}};
+constexpr FluidVariant FLUID_VARIANTS[N_FLUID_VARIANTS] = {
+    {4, 8, 0}, {4, 4, 0}, {1, 8, 0}, {2, 8, 0}, {2, 4, 0},
+    {1, 4, 0}, {4, 8, 2}, {4, 8, 3}, {2, 8, 3}, {2, 8, 4}};
+// the variants a precision has: the tangent mode the one-cell direct tile
+// only, FP64 the direct kernels, FP32 and FP16 storage all
+constexpr bool variant_valid(int prec, int v) {
+    return v >= 0 && v < N_FLUID_VARIANTS &&
+           (prec == LBM_FP32_TANGENT ? v == 2 : (prec == LBM_FP64 ? FLUID_VARIANTS[v].stages == 0 : true));
+}
 
 struct FieldArgs {
     const void* f;            // population buffer
@@ -177,15 +195,30 @@ struct FieldArgs {
     double* tan;              // tangent mode, optional: [3][KT][rows][nx] (rho, ux, uy)
 };
 
-// kernel launchers (fluid.cu / particles.cu); prec is an lbm_precision
+// kernel launchers (fluid*.cu / particles.cu); prec is an lbm_precision
 cudaError_t launch_init(int prec, void* fbuf, const Inst& I, int kind, double init_u, cudaStream_t s);
-// one != nullptr: the context holds that single lattice (2-D tile grid,
-// descriptor by value); otherwise the task list over all instances
-// pdl: launched with programmatic stream serialization (see pdl_wait); only
-// when the kernel before it in the stream is the spreading kernel
-cudaError_t launch_fluid(int prec, int variant, const FluidArgs& a, const Inst* one, int grid,
-                         cudaStream_t s, bool pdl);
-int fluid_blocks_per_sm(int prec, int variant);
+// one != nullptr: the context holds that single lattice (tile grid,
+// descriptor by value); otherwise the task list over all instances.
+// grid: CTAs of a direct task-list kernel; sms: the device's SMs (the staged
+// kernel's grid); pdl: launched with programmatic stream serialization (see
+// pdl_wait), only when the kernel before it in the stream is the spreading
+// kernel; wait_limit: clock cycles a staged CTA waits for a tile's copies
+// before it gives up with ERR_TIMEOUT.  cudaErrorInvalidValue for a
+// variant the precision does not have.
+cudaError_t launch_fluid(int prec, int variant, const FluidArgs& a, const Inst* one, int grid, int sms,
+                         cudaStream_t s, bool pdl, long long wait_limit);
+cudaError_t launch_fluid_direct_a(int prec, int cpt, int by, const FluidArgs& a, const Inst* one, int grid,
+                                  cudaStream_t s, bool pdl);
+cudaError_t launch_fluid_direct_b(int prec, int cpt, int by, const FluidArgs& a, const Inst* one, int grid,
+                                  cudaStream_t s, bool pdl);
+cudaError_t launch_fluid_staged(int prec, int cpt, int stages, const FluidArgs& a, const Inst* one, int sms,
+                                cudaStream_t s, bool pdl, long long wait_limit);
+// the tensor map (CUtensorMap, 128 bytes at out) of lattice I in population
+// buffer fbuf for the staged variants of `cpt` cells per thread: a 3-D
+// tensor [9][ny][pitch] with boxes of one plane, 8 rows and the tile width
+// plus 16 bytes on each side
+constexpr size_t TMAP_BYTES = 128;
+cudaError_t encode_stage_map(int prec, int cpt, const void* fbuf, const Inst& I, void* out);
 cudaError_t launch_fields(int prec, const FieldArgs& a, cudaStream_t s);
 // host-layout populations ([9][rows][nx] unshifted doubles at device
 // address h) into / out of the stored shifted populations of rows

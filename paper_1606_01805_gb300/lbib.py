@@ -23,7 +23,7 @@ STATUS_NAMES = ["LBM_OK", "LBM_EINVAL", "LBM_ENOMEM", "LBM_ECUDA", "LBM_ETIMEOUT
 LBM_BC_PERIODIC, LBM_BC_VELOCITY = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16_SHIFTED, LBM_FP32_TANGENT = 0, 1, 2, 3
 LBM_TANGENTS = 3            # derivative directions of the tangent mode
-LBM_TILE_VARIANTS = 3       # fluid tile shapes (lbm_get_tile / lbm_set_tile)
+LBM_TILE_VARIANTS = 10      # fluid tile variants (lbm_get_tile / lbm_set_tile / lbm_tile_info)
 LBM_TANGENT_FIELDS = 10     # xc, yc, theta, u[0], u[1], omega, F[0], F[1], M, omega_sum
 TANGENT_FIELDS = ("xc", "yc", "theta", "ux", "uy", "omega", "Fx", "Fy", "M", "omega_sum")
 SEED_FIELDS = ("dim0", "dim1", "xc", "yc", "theta", "rho_s")
@@ -33,7 +33,7 @@ LBM_W_EXP, LBM_W_CUBIC, LBM_W_QUARTIC, LBM_W_COSINE, LBM_W_POLY = range(5)
 
 # every symbol include/lbib.h declares
 EXPORTS = ["lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "lbm_step_timed",
-           "lbm_sync", "lbm_inject_status", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
+           "lbm_sync", "lbm_inject_status", "lbm_inject_stall", "lbm_tile_info", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
            "lbm_get_particles", "lbm_steps_done", "lbm_last_error", "lbm_destroy",
            "lbm_step_static", "lbm_batch_workspace_bytes", "lbm_init_batch", "lbm_instances",
            "lbm_add_particle_to", "lbm_get_instance_fields", "lbm_get_instance_populations",
@@ -98,6 +98,8 @@ def load(path: os.PathLike | str | None = None):
     L.lbm_step_timed.argtypes = [C.c_void_p, C.c_int32, _dp, _dp]
     L.lbm_sync.argtypes = [C.c_void_p]
     L.lbm_inject_status.argtypes = [C.c_void_p, C.c_int32]
+    L.lbm_inject_stall.argtypes = [C.c_void_p, C.c_int64]
+    L.lbm_tile_info.argtypes = [C.c_int32, C.c_int32] + [C.POINTER(C.c_int32)] * 3
     L.lbm_get_fields.argtypes = [C.c_void_p, _dp, _dp, _dp]
     L.lbm_get_populations.argtypes = [C.c_void_p, _dp]
     L.lbm_set_populations.argtypes = [C.c_void_p, _dp]
@@ -127,7 +129,7 @@ def load(path: os.PathLike | str | None = None):
     L.lbm_get_particle_tangents.argtypes = [C.c_void_p, _dp, C.c_int32, C.POINTER(C.c_int32)]
     L.lbm_get_field_tangents.argtypes = [C.c_void_p, C.c_int32, _dp, _dp, _dp]
     for fn in ("lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "lbm_step_timed",
-               "lbm_sync", "lbm_inject_status", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
+               "lbm_sync", "lbm_inject_status", "lbm_inject_stall", "lbm_tile_info", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
                "lbm_get_particles", "lbm_step_static", "lbm_batch_workspace_bytes",
                "lbm_init_batch", "lbm_add_particle_to", "lbm_get_instance_fields",
                "lbm_get_instance_populations", "lbm_set_instance_populations", "lbm_get_tile",
@@ -226,6 +228,11 @@ class Simulation:
     def inject_status(self, status):
         """Test hook: the device flag of `status`, as a kernel sets it."""
         self._check(load().lbm_inject_status(self._h, status), "lbm_inject_status")
+
+    def inject_stall(self, wait_cycles):
+        """Test hook: the next step's staged fluid launch waits for a copy
+        that never comes, for wait_cycles clock cycles (lbm_inject_stall)."""
+        self._check(load().lbm_inject_stall(self._h, wait_cycles), "lbm_inject_stall")
 
     @property
     def steps_done(self):
@@ -335,6 +342,7 @@ class Batch:
     step_timed = Simulation.step_timed
     sync = Simulation.sync
     inject_status = Simulation.inject_status
+    inject_stall = Simulation.inject_stall
     particles = Simulation.particles
     steps_done = Simulation.steps_done
 
@@ -403,6 +411,14 @@ def _tile(self):
     v, c, b = C.c_int32(), C.c_int32(), C.c_int32()
     self._check(load().lbm_get_tile(self._h, C.byref(v), C.byref(c), C.byref(b)), "lbm_get_tile")
     return v.value, c.value, b.value
+
+
+def tile_info(variant, precision):
+    """(cells per thread, rows per tile, stages, available) of a tile variant
+    for a precision (lbm_tile_info)."""
+    c, r, s = C.c_int32(), C.c_int32(), C.c_int32()
+    rc = load().lbm_tile_info(variant, precision, C.byref(c), C.byref(r), C.byref(s))
+    return c.value, r.value, s.value, rc == LBM_OK
 
 
 def _set_tile(self, variant):

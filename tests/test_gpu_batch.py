@@ -67,7 +67,9 @@ def test_batch_instances_match_oracle_fp32():
 def test_every_tile_shape_gives_the_same_bits(prec):
     wls = small_batch(n=3, seed=5)
     results = []
-    for v in range(lbib.LBM_TILE_VARIANTS):
+    variants = [v for v in range(lbib.LBM_TILE_VARIANTS) if lbib.tile_info(v, prec)[3]]
+    assert len(variants) == (6 if prec == FP64 else 10)
+    for v in variants:
         b = make_batch(wls, prec)
         b.set_tile(v)
         assert b.tile()[0] == v
@@ -82,9 +84,14 @@ def test_every_tile_shape_gives_the_same_bits(prec):
 def test_autotuner_reports_a_valid_shape():
     b = make_batch(small_batch(n=2), FP32)
     v, cpt, by = b.tile()
-    assert 0 <= v < lbib.LBM_TILE_VARIANTS and cpt in (1, 4) and by in (4, 8)
+    assert 0 <= v < lbib.LBM_TILE_VARIANTS and cpt in (1, 2, 4) and by in (4, 8)
+    assert lbib.tile_info(v, FP32)[:2] == (cpt, by)
     with pytest.raises(lbib.LbmError):
         b.set_tile(lbib.LBM_TILE_VARIANTS)
+    b64 = make_batch(small_batch(n=2), FP64)
+    with pytest.raises(lbib.LbmError):
+        b64.set_tile(6)  # staged variants: FP32 and FP16 storage only
+    assert lbib.tile_info(6, FP64)[3] is False and lbib.tile_info(6, FP32)[2] == 2
 
 
 def test_full_screening_batch_runs():

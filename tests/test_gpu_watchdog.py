@@ -154,3 +154,34 @@ def test_timed_steps_keep_the_watchdog():
     sim.step_timed(1)
     with pytest.raises(lbib.LbmError):
         sim.sync()
+
+
+def test_bounded_copy_wait_runs_out_and_reports_timeout():
+    """lbm_inject_stall arms one barrier of the staged fluid kernel for bytes
+    no copy brings: the CTA's bounded wait runs out, the kernel reports
+    LBM_ETIMEOUT and returns; the device stays usable."""
+    sim = _channel(n=(700, 90))
+    sim.set_tile(6)  # staged, 4 cells x 8 rows, 2 stages
+    sim.step(2)
+    sim.sync()
+    sim.inject_stall(2_000_000)  # about a millisecond
+    sim.step(1)
+    with pytest.raises(lbib.LbmError) as ei:
+        sim.sync()
+    assert ei.value.status == lbib.LBM_ETIMEOUT
+    # the device is fine: a new context runs clean
+    other = _channel(n=(700, 90))
+    other.set_tile(6)
+    other.step(40)
+    other.sync()
+
+
+def test_inject_stall_needs_a_staged_variant():
+    sim = _channel()
+    sim.set_tile(0)
+    with pytest.raises(lbib.LbmError) as ei:
+        sim.inject_stall(2_000_000)
+    assert ei.value.status == lbib.LBM_EINVAL
+    sim.set_tile(7)
+    with pytest.raises(lbib.LbmError):
+        sim.inject_stall(10)  # below the allowed range
