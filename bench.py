@@ -63,8 +63,10 @@ def ncu_traffic(workload, prec, variant):
 
 
 def kernel_hash():
+    """hash of the sources that define the direct fluid kernels"""
     h = hashlib.sha256()
-    for name in ("fluid.cu", "lbib_device.cuh", "lbib_internal.h"):
+    for name in ("fluid_core.cuh", "fluid_direct.cuh", "fluid_direct_a.cu", "fluid_direct_b.cu",
+                 "lbib_device.cuh"):
         h.update((ROOT / "paper_1606_01805_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:16]
 
@@ -161,7 +163,7 @@ def gpu_sim(wl, prec):
     return sim
 
 
-def time_device(wl, prec, steps, warmup, flush, pick_tile=False):
+def time_device(wl, prec, steps, warmup, flush, pick_tile=False, tile=None):
     """Device time of `steps` steps (CUDA events inside the library on the
     context's stream), optionally flushing L2 before each step.  With
     pick_tile, every fluid tile shape is first timed under the same protocol
@@ -171,6 +173,9 @@ def time_device(wl, prec, steps, warmup, flush, pick_tile=False):
     import torch
 
     sim = gpu_sim(wl, prec)
+    if tile is not None:  # a given tile variant (no tuning)
+        sim.set_tile(tile)
+        pick_tile = False
     big = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if flush else None
     big2 = torch.ones(64 << 20, dtype=torch.float32, device="cuda") if flush else None
 
@@ -230,13 +235,15 @@ def screening_batch(prec, wls):
     return b
 
 
-def time_batched(prec, steps, warmup, instances=512):
+def time_batched(prec, steps, warmup, instances=512, mode=0):
     """The screening batch (512 uneven lattices, 63 M cells, beyond L2) as
-    one context: device time per step from the library's events."""
+    one context, in step mode `mode` (separate kernels or the fused
+    persistent launch): device time per step from the library's events."""
     from paper_1606_01805_gb300 import workloads as W
 
     wls = W.batched_screening(steps=0)[:instances]
     b = screening_batch(prec, wls)
+    b.set_step_mode(mode)
     b.step_timed(warmup, fluid=False)
     ms_step = b.step_timed(steps, fluid=False)[0]
     ms_fluid = b.step_timed(steps)[1]
@@ -297,14 +304,17 @@ def time_per_instance(prec, sweeps):
     return sum(w.cells for w in wls), ms
 
 
-def time_e2e(wl, prec, steps):
+def time_e2e(wl, prec, steps, tile):
     """The user's job through the public C ABI with host buffers in pinned
     memory: upload the initial populations (FP64, [9][ny][nx]), advance
     `steps` steps, read back the fields (rho, ux, uy) and the particle
-    states.  Returns (seconds, host-to-device bytes, device-to-host bytes)."""
+    states.  The tile variant is the one the device timing used (set before
+    the timed region, so that the library's first-step tuning stays out of
+    it).  Returns (seconds, host-to-device bytes, device-to-host bytes)."""
     import torch
 
     sim = gpu_sim(wl, prec)
+    sim.set_tile(tile)
     pinned = lambda *shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
     f0 = sim.populations(out=pinned(9, wl.ny, wl.nx))  # the job's input (initial state)
     outs = [pinned(wl.ny, wl.nx) for _ in range(3)]
@@ -372,14 +382,14 @@ def dist_env():
     return ws, rank, local
 
 
-def lattice_measure(wl, prec, steps, warmup, peak):
+def lattice_measure(wl, prec, steps, warmup, peak, tile=None):
     """Device-timed steps of one lattice workload: the whole step (value)
     and the fluid kernel alone (roofline), with the traffic of the fluid
     kernel from the recorded ncu captures when they match the current
     kernel sources.  L2 is flushed before every timed step unless the
     populations alone exceed it."""
     flush = BYTES_PER_CELL[prec] * wl.cells < 2 * (129 << 20)
-    ms_step, ms_fluid, launches, tile = time_device(wl, prec, steps, warmup, flush, pick_tile=flush)
+    ms_step, ms_fluid, launches, tile = time_device(wl, prec, steps, warmup, flush, pick_tile=flush, tile=tile)
     algo = BYTES_PER_CELL[prec] * wl.cells
     achieved = algo / (ms_fluid * 1e-3 / steps) / 1e9
     tr = ncu_traffic(wl.name, prec, tile[0])
@@ -406,6 +416,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the screening batch and the tangent-mode batch")
+    ap.add_argument("--tile", type=int, default=None,
+                    help="force this fluid tile variant (lbm_set_tile) instead of the tuned one")
     ap.add_argument("--instances", type=int, default=512,
                     help="screening workload: first N lattices of the batch (profiling subsets)")
     args = ap.parse_args()
@@ -456,7 +468,7 @@ def main():
     build.build()
     peak, peak_kind = hbm_peak()
     with ClockSampler(local) as clk:
-        m = lattice_measure(wl, prec, args.steps, args.warmup, peak)
+        m = lattice_measure(wl, prec, args.steps, args.warmup, peak, tile=args.tile)
     if ws > 1:
         dist.barrier()
     cells = wl.cells
@@ -473,8 +485,9 @@ def main():
                    "l2": "flushed before every timed step" if m["flush"] else "inputs larger than L2",
                    "parallelism": "replicas" if ws > 1 else "single",
                    "fluid_tile": {"variant": tile[0], "cells_per_thread": tile[1], "rows_per_block": tile[2],
-                                  "chosen_by": "bench.py, each shape timed over 20 L2-flushed steps"
-                                  if m["flush"] else "the library's autotuner"}},
+                                  "chosen_by": "--tile" if args.tile is not None else
+                                  "bench.py, each shape timed over 20 L2-flushed steps"
+                                  if m["flush"] else "the library's autotuner (first step)"}},
         "roofline": roof,
         "gpu_launches": m["launches"],
         "clocks": clk.summary(),
@@ -482,7 +495,7 @@ def main():
     }
     out["frac_of_roofline_mlups"] = value / ws / (peak * 1e3 / BYTES_PER_CELL[prec])
     if rank == 0:
-        e2e_s, h2d, d2h = time_e2e(wl, prec, args.steps)
+        e2e_s, h2d, d2h = time_e2e(wl, prec, args.steps, tile[0])
         out["e2e"] = {"value": cells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
                       "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                       "job": f"through the C ABI from pinned host memory: upload f0 (FP64), "

@@ -196,15 +196,19 @@ lbm_status lbm_sync(lbm_ctx* ctx);
 lbm_status lbm_inject_status(lbm_ctx* ctx, int32_t status);
 
 /*
- * Test hook of the bounded device waits (the paper has no counterpart):
- * the next step's fluid launch, which must be a staged variant (6..9, see
- * lbm_get_tile; else LBM_EINVAL), arms the mbarrier of its first CTA's
- * first tile for 16 bytes more than its copies bring, so that the CTA's
- * wait for it runs out after wait_cycles clock cycles (1e6 .. 2e9, else
- * LBM_EINVAL; the kernels' own limit is 2e9, about a second).  The CTA
- * then sets the LBM_ETIMEOUT flag, lets its copies in flight land and
- * returns without computing its tiles; the step is launched directly (not
- * from a captured graph).  Nothing faults; lbm_sync reports LBM_ETIMEOUT.
+ * Test hook of the bounded device waits (the paper has no counterpart).
+ * With a staged tile variant (6..9, see lbm_get_tile), the next step's
+ * fluid launch arms the mbarrier of its first CTA's first tile for 16
+ * bytes more than its copies bring, so that the CTA's wait for it runs out
+ * after wait_cycles clock cycles; the CTA then sets the LBM_ETIMEOUT flag,
+ * lets its copies in flight land and returns without computing its tiles.
+ * In the fused step mode (lbm_set_step_mode), the next step's first fluid
+ * item waits for one spreading tile more than its instance has; its wait
+ * runs out after wait_cycles, sets the flag and aborts the step's other
+ * waits.  Else LBM_EINVAL, as for wait_cycles outside 1e6 .. 2e9 (the
+ * kernels' own limit is 2e9, about a second).  The step is launched
+ * directly (not from a captured graph).  Nothing faults; lbm_sync reports
+ * LBM_ETIMEOUT, and the step's results are not usable.
  */
 lbm_status lbm_inject_stall(lbm_ctx* ctx, int64_t wait_cycles);
 
@@ -343,6 +347,28 @@ lbm_status lbm_get_tile(const lbm_ctx* ctx, int32_t* variant, int32_t* cells_per
 lbm_status lbm_tile_info(int32_t variant, int32_t precision, int32_t* cells_per_thread, int32_t* rows,
                          int32_t* stages);
 lbm_status lbm_set_tile(lbm_ctx* ctx, int32_t variant);
+
+/*
+ * Step mode of a batch.  LBM_STEP_SEPARATE (the default): each step is the
+ * immersed-boundary kernels (probes and rigid update, markers, spreading)
+ * and then the fluid kernel, each one launch over all instances.
+ * LBM_STEP_FUSED: each step is one persistent launch whose CTAs take the
+ * step's work items in a fixed order -- probe blocks, marker blocks,
+ * spreading tiles and fluid tiles of every instance, the stages of one
+ * instance a few instances apart, so that the particle work of some
+ * instances runs beside the fluid work of others.  Within an instance an
+ * item waits (bounded; LBM_ETIMEOUT on expiry) for the items it needs.
+ * Both modes give the same results, bit for bit.  The fused mode needs a
+ * batch of two or more instances (lbm_init_batch) in LBM_FP64, LBM_FP32 or
+ * LBM_FP16_SHIFTED (else LBM_EINVAL); it uses its own fluid tile (2 cells
+ * per thread, 8 rows: lbm_get_tile reports variant 3) and lbm_step_timed
+ * then reports the fused launch as the fluid time.  Set it before or
+ * between steps.
+ */
+#define LBM_STEP_SEPARATE 0
+#define LBM_STEP_FUSED 1
+lbm_status lbm_set_step_mode(lbm_ctx* ctx, int32_t mode);
+lbm_status lbm_get_step_mode(const lbm_ctx* ctx, int32_t* mode);
 
 /*
  * Tangent mode (precision LBM_FP32_TANGENT) -- forward-mode

@@ -38,7 +38,7 @@ struct lbm_ctx {
     void* flb;
     uint8_t* flags;
     Inst* insts;
-    int4* tasks[N_FLUID_VARIANTS];
+    Task* tasks[N_FLUID_VARIANTS];
     int ntasks[N_FLUID_VARIANTS];
     // tensor maps of the staged variants: [buffer][cells per thread 2, 4][instance]
     // on the device, and their host copies; staged_ok: they could be made
@@ -77,6 +77,16 @@ struct lbm_ctx {
     cudaGraphExec_t timed[2][2] = {};  // one step with its timing events (without / with the watchdog)
     cudaGraphExec_t timed0[2][2] = {}; // the same without the event before the fluid kernel
     bool timed_ok = true;
+    bool tuned = false;             // the tile variant was picked (tune_step or lbm_set_tile)
+    // fused step of a batch (lbm_set_step_mode): work list and counters
+    int step_mode = LBM_STEP_SEPARATE;
+    int4* items = nullptr;
+    size_t items_cap = 0;
+    std::vector<int4> hitems;
+    bool items_dirty = true;
+    unsigned* counters = nullptr;
+    size_t counter_words = 0;       // per set
+    std::vector<double> hrc;        // per particle: circumscribed radius
     std::string msg;
 };
 
@@ -146,21 +156,31 @@ Geo make_geo(const lbm_config& c) {
 }
 
 // fluid tiles of variant v over all instances
-std::vector<int4> make_tasks(const std::vector<Inst>& insts, int v) {
+std::vector<Task> make_tasks(const std::vector<Inst>& insts, int v) {
     const int w = 32 * FLUID_VARIANTS[v].cpt, by = FLUID_VARIANTS[v].by;
-    std::vector<int4> t;
+    std::vector<Task> t;
     for (int i = 0; i < (int)insts.size(); ++i) {
         const Geo& G = insts[i].G;
         for (int ty = 0; ty < (G.ny + by - 1) / by; ++ty)
-            for (int tx = 0; tx < (G.nx + w - 1) / w; ++tx) t.push_back(make_int4(i, tx, ty, 0));
+            for (int tx = 0; tx < (G.nx + w - 1) / w; ++tx) {
+                Task k{};
+                k.inst = i;
+                k.tx = tx;
+                k.ty = ty;
+                k.pitch = G.pitch;
+                k.f_off = insts[i].f_off;
+                k.ny = G.ny;
+                t.push_back(k);
+            }
     }
     return t;
 }
 
 struct Layout {
     std::vector<Inst> insts;
-    size_t f0, f1, flb, flags, insts_off, tasks[N_FLUID_VARIANTS], tmaps, parts, poses, blk, partial, count, mg,
-        S, recs, boxes, ptab, err, scratch, total;
+    size_t f0, f1, flb, flags, insts_off, tasks[N_FLUID_VARIANTS], tmaps, items, counters, parts, poses, blk,
+        partial, count, mg, S, recs, boxes, ptab, err, scratch, total;
+    size_t items_cap, counter_words;
     int ntasks[N_FLUID_VARIANTS];
     int scratch_rows, scratch_cols, scratch_planes;
 };
@@ -201,9 +221,23 @@ Layout layout(const lbm_config* cfgs, int n) {
     for (int v = 0; v < N_FLUID_VARIANTS; ++v) {
         L.ntasks[v] = (int)make_tasks(L.insts, v).size();
         L.tasks[v] = o;
-        o = up(o + (size_t)L.ntasks[v] * sizeof(int4));
+        o = up(o + (size_t)L.ntasks[v] * sizeof(Task));
     }
     L.tmaps = o; o = up(o + 4 * (size_t)n * TMAP_BYTES);
+    // the fused step's work list (batches): fluid tiles of its task list,
+    // probe and marker items (at most one per 8 marker blocks and one more
+    // per particle each), spreading tiles (a particle's support box lies in
+    // its lattice: at most (nx / 32 + 3) (ny / 8 + 3) tiles of 32 x 8)
+    L.items_cap = 0;
+    L.counter_words = 2 * P + n + 2;
+    if (n >= 2) {
+        int max_ny = 0;
+        for (const Inst& I : L.insts) max_ny = std::max(max_ny, I.G.ny);
+        L.items_cap = (size_t)L.ntasks[fused_fluid_variant()] + 2 * (NB / MB + P + 1) +
+                      P * (size_t)(max_nx / 32 + 3) * (max_ny / fused_spread_rows() + 3);
+    }
+    L.items = o; o = up(o + L.items_cap * sizeof(int4));
+    L.counters = o; o = up(o + 2 * L.counter_words * sizeof(unsigned));
     L.parts = o; o = up(o + 2 * P * particle_bytes(prec));
     L.poses = o; o = up(o + 2 * P * pose_bytes(prec));
     L.blk = o; o = up(o + NB * sizeof(int4));
@@ -298,9 +332,9 @@ SpreadArgs spread_args(lbm_ctx* ctx, const ParticleArgs& pa) {
 // tiles of 32 x 16 cells covering the support box of a particle whose
 // markers lie within rc of its centroid (the box spans at most 2 rc + 4
 // cells per side), and for the largest particle of the context
-int box_tiles(double rc) {
+int box_tiles(double rc, int rows = 16) {
     const double ext = 2.0 * rc + 4.0;
-    return ((int)std::ceil(ext / 32.0) + 1) * ((int)std::ceil(ext / 16.0) + 1);
+    return ((int)std::ceil(ext / 32.0) + 1) * ((int)std::ceil(ext / rows) + 1);
 }
 int spread_tiles(const lbm_ctx* ctx) { return box_tiles(ctx->rc_max); }
 
@@ -316,9 +350,10 @@ bool watched(const lbm_ctx* ctx, int64_t step) { return (step + 1) % ctx->check_
 // pdl: launch the fluid kernel with programmatic stream serialization (only
 // right after the spreading kernel: its prologue loads the populations the
 // previous step's fluid kernel wrote); check: the kernel runs its watchdog;
-// stall: the test hook of lbm_inject_stall
+// stall: the test hook of lbm_inject_stall; keep: leave the forces and
+// their flags in place (the autotuner's repeated launches of one step)
 lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v, bool pdl = false,
-                             bool check = false, bool stall = false) {
+                             bool check = false, bool stall = false, bool keep = false) {
     FluidArgs fa;
     fa.fin = ctx->f[cur];
     fa.fout = ctx->f[cur ^ 1];
@@ -330,6 +365,7 @@ lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v, bool
     fa.err = ctx->err;
     fa.check = check ? 1 : 0;
     fa.stall = stall ? 1 : 0;
+    fa.keep = keep ? 1 : 0;
     fa.tmaps = fa.tmap_one = nullptr;
     if (FLUID_VARIANTS[v].stages) {
         const size_t k = (size_t)(cur * 2 + (FLUID_VARIANTS[v].cpt == 4 ? 1 : 0)) * ctx->ninst;
@@ -344,12 +380,98 @@ lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v, bool
     return LBM_OK;
 }
 
+// The fused step's work list, in rounds: round r holds the probe items of
+// instance r, the marker items of instance r - D, the spreading tiles of
+// r - 2D and the fluid tiles of r - 3D, so that within one instance every
+// item follows the items it waits for by about D rounds.  D is chosen so
+// that D rounds outlast one stage of a particle (tens of microseconds:
+// a probe or marker item is a chain of dependent loads and FP64 work) while
+// a round's fluid tiles take about a microsecond of the whole GPU.
+constexpr int FUSED_LAG = 32;
+
+lbm_status build_items(lbm_ctx* ctx) {
+    const int n = ctx->ninst, rows = fused_spread_rows(), fv = fused_fluid_variant();
+    std::vector<std::vector<int4>> pi(n), mi(n), si(n), fi(n);
+    std::vector<int> nsp(n, 0);
+    for (int p = 0; p < ctx->np; ++p) {
+        const int4 pr = ctx->hpart[p];  // (first marker, markers, instance, tiles of 32 x 16)
+        const int inst = pr.z, tiles = box_tiles(ctx->hrc[p], rows);
+        nsp[inst] += tiles;
+        for (int t = 0; t < tiles; ++t) si[inst].push_back(make_int4(FI_SPREAD, t, p, tiles));
+    }
+    for (int b = 0; b < ctx->nblk;) {  // runs of up to 8 blocks of one particle
+        const int p = ctx->hblk[b].x;
+        int e = b;
+        while (e < ctx->nblk && e - b < 8 && ctx->hblk[e].x == p) ++e;
+        const int inst = ctx->hblk[b].w;
+        pi[inst].push_back(make_int4(FI_PROBES, b, e - b, p));
+        mi[inst].push_back(make_int4(FI_MARKERS, b, e - b, p));
+        b = e;
+    }
+    const std::vector<Task> tasks = make_tasks(ctx->hinst, fv);
+    for (int t = 0; t < (int)tasks.size(); ++t)
+        fi[tasks[t].inst].push_back(make_int4(FI_FLUID, t, tasks[t].inst, nsp[tasks[t].inst]));
+    std::vector<int4>& out = ctx->hitems;
+    out.clear();
+    for (int r = 0; r < n + 3 * FUSED_LAG; ++r) {
+        const int ip = r, im = r - FUSED_LAG, is = r - 2 * FUSED_LAG, iF = r - 3 * FUSED_LAG;
+        if (ip < n) out.insert(out.end(), pi[ip].begin(), pi[ip].end());
+        if (im >= 0 && im < n) out.insert(out.end(), mi[im].begin(), mi[im].end());
+        if (is >= 0 && is < n) out.insert(out.end(), si[is].begin(), si[is].end());
+        if (iF >= 0 && iF < n) out.insert(out.end(), fi[iF].begin(), fi[iF].end());
+    }
+    if (out.size() > ctx->items_cap) return fail(ctx, LBM_EINTERNAL, "fused step work list exceeds its space");
+    CK(cudaMemcpyAsync(ctx->items, out.data(), out.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->items_dirty = false;
+    return LBM_OK;
+}
+
+// the whole step `step` from buffer `cur` as one fused launch
+lbm_status launch_fused_step(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t step, bool stall) {
+    FusedArgs f;
+    std::memset(&f, 0, sizeof f);
+    const int fv = fused_fluid_variant();
+    f.fa.fin = ctx->f[cur];
+    f.fa.fout = ctx->f[cur ^ 1];
+    f.fa.flb = ctx->flb;
+    f.fa.flags = ctx->flags;
+    f.fa.insts = ctx->insts;
+    f.fa.tasks = ctx->tasks[fv];
+    f.fa.ntasks = ctx->ntasks[fv];
+    f.fa.check = watched(ctx, step) ? 1 : 0;
+    f.fa.err = ctx->err;
+    f.pa = particle_args(ctx, cur);
+    f.pa.nblk_inline = 0;  // the block table from memory (the items carry block indices)
+    f.sa = spread_args(ctx, f.pa);
+    f.items = ctx->items;
+    f.nitems = (int)ctx->hitems.size();
+    f.np = ctx->np;
+    f.ninst = ctx->ninst;
+    f.parity = cur;
+    f.counters[0] = ctx->counters;
+    f.counters[1] = ctx->counters + ctx->counter_words;
+    f.wait_limit = stall ? ctx->stall_limit : WAIT_LIMIT;
+    f.stall = stall ? 1 : 0;
+    f.stall_ticket = 0;
+    for (int t = 0; t < f.nitems; ++t)
+        if (ctx->hitems[t].x == FI_FLUID) {
+            f.stall_ticket = t;
+            break;
+        }
+    CK(launch_step_fused(ctx->prec, f, ctx->sms, st));
+    return LBM_OK;
+}
+
+bool fused(const lbm_ctx* ctx) { return ctx->step_mode == LBM_STEP_FUSED; }
+
 // Part of time step number `step` (steps done before it) from buffer `cur`
 // on stream `st`: the immersed-boundary kernels (ib = true: probes / rigid
 // update / markers, spreading) or the fused fluid kernel over every
 // instance (ib = false).  Bookkeeping is the caller's.
 lbm_status enqueue_step_part(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t step, bool ib,
                              bool pdl = false, bool stall = false) {
+    if (fused(ctx)) return ib ? LBM_OK : launch_fused_step(ctx, st, cur, step, stall);
     if (!ib)
         return launch_fluid_step(ctx, st, cur, ctx->variant, pdl && ctx->np > 0, watched(ctx, step), stall);
     if (ctx->np == 0) return LBM_OK;
@@ -449,44 +571,59 @@ void drop_graphs(lbm_ctx* ctx) {
     }
 }
 
-// Autotuner of the fluid tile variant: times every variant the precision
-// has (FLUID_VARIANTS: cells per thread x rows per tile x staging depth) on
-// the context's own lattices (fluid kernel only; it reads buffer cur and
-// writes the other one, which the next step overwrites, and no force flag
-// is set yet) and keeps the fastest.  All variants compute the same cells
-// with the same arithmetic, so the choice changes speed only.
-lbm_status autotune(lbm_ctx* ctx) {
-    cudaEvent_t a, b;
-    CK(cudaEventCreate(&a));
-    CK(cudaEventCreate(&b));
+// Autotuner of the fluid tile variant, run as the context's first step:
+// the immersed-boundary kernels of that step run once (so the force field
+// and its flags are those of a real step), then the fluid kernel of every
+// variant the context has (FLUID_VARIANTS: cells per thread x rows per tile
+// x staging depth) is timed on the context's own lattices, reading buffer
+// cur, writing the other one and leaving the forces in place; the fastest is
+// kept and launched once more as the step's own fluid kernel.  All variants
+// compute the same cells with the same arithmetic, so the choice changes
+// speed only.  lbm_set_tile before the first step skips it.
+lbm_status tune_step(lbm_ctx* ctx, bool* stepped) {
+    ctx->tuned = true;
+    *stepped = false;
+    if (ctx->prec == LBM_FP32_TANGENT || fused(ctx)) return LBM_OK;  // one tile variant only
+    struct Events {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Events() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    CK(cudaEventCreate(&ev.a));
+    CK(cudaEventCreate(&ev.b));
+    lbm_status s = enqueue_step_part(ctx, ctx->stream, ctx->cur, ctx->steps, true);
+    if (s != LBM_OK) return s;
     float best[N_FLUID_VARIANTS];
-    if (ctx->prec == LBM_FP32_TANGENT) {  // one tile shape only
-        ctx->variant = 2;
-        return LBM_OK;
-    }
     for (int v = 0; v < N_FLUID_VARIANTS; ++v) {  // warm every shape first
         best[v] = 1e30f;
         if (!ctx_variant_ok(ctx, v)) continue;
-        lbm_status s = launch_fluid_step(ctx, ctx->stream, ctx->cur, v);
+        s = launch_fluid_step(ctx, ctx->stream, ctx->cur, v, false, false, false, true);
         if (s != LBM_OK) return s;
     }
     for (int round = 0; round < 2; ++round)
         for (int v = 0; v < N_FLUID_VARIANTS; ++v) {
             if (!ctx_variant_ok(ctx, v)) continue;
-            CK(cudaEventRecord(a, ctx->stream));
+            CK(cudaEventRecord(ev.a, ctx->stream));
             for (int k = 0; k < 2; ++k) {
-                lbm_status s = launch_fluid_step(ctx, ctx->stream, ctx->cur, v);
+                s = launch_fluid_step(ctx, ctx->stream, ctx->cur, v, false, false, false, true);
                 if (s != LBM_OK) return s;
             }
-            CK(cudaEventRecord(b, ctx->stream));
-            CK(cudaEventSynchronize(b));
+            CK(cudaEventRecord(ev.b, ctx->stream));
+            CK(cudaEventSynchronize(ev.b));
             float ms = 0;
-            CK(cudaEventElapsedTime(&ms, a, b));
+            CK(cudaEventElapsedTime(&ms, ev.a, ev.b));
             best[v] = std::min(best[v], ms);
         }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    ctx->variant = (int)(std::min_element(best, best + N_FLUID_VARIANTS) - best);
+    const int pick = (int)(std::min_element(best, best + N_FLUID_VARIANTS) - best);
+    if (pick != ctx->variant) drop_graphs(ctx);
+    ctx->variant = pick;
+    s = launch_fluid_step(ctx, ctx->stream, ctx->cur, pick, false, watched(ctx, ctx->steps));
+    if (s != LBM_OK) return s;
+    ctx->cur ^= 1;
+    ctx->steps += 1;
+    *stepped = true;
     return LBM_OK;
 }
 
@@ -506,6 +643,7 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
     ctx->cb = compute_bytes(ctx->prec);
     ctx->stream = static_cast<cudaStream_t>(cfgs[0].cuda_stream);
     ctx->check_every = cfgs[0].check_every > 0 ? cfgs[0].check_every : 1;
+    if (ctx->prec == LBM_FP32_TANGENT) ctx->variant = 2;  // its one tile variant
     if (cfgs[0].d_workspace) {
         if (cfgs[0].workspace_bytes < L.total) {
             delete ctx;
@@ -527,10 +665,14 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
     ctx->flags = reinterpret_cast<uint8_t*>(b + L.flags);
     ctx->insts = reinterpret_cast<Inst*>(b + L.insts_off);
     for (int v = 0; v < N_FLUID_VARIANTS; ++v) {
-        ctx->tasks[v] = reinterpret_cast<int4*>(b + L.tasks[v]);
+        ctx->tasks[v] = reinterpret_cast<Task*>(b + L.tasks[v]);
         ctx->ntasks[v] = L.ntasks[v];
     }
     ctx->tmaps = b + L.tmaps;
+    ctx->items = reinterpret_cast<int4*>(b + L.items);
+    ctx->items_cap = L.items_cap;
+    ctx->counters = reinterpret_cast<unsigned*>(b + L.counters);
+    ctx->counter_words = L.counter_words;
     ctx->rsz = real_bytes(ctx->prec);
     ctx->psz = particle_bytes(ctx->prec);
     ctx->parts = b + L.parts;
@@ -553,7 +695,7 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
     if (ctx->sms < 1) ctx->sms = 1;
-    std::vector<std::vector<int4>> tasks(N_FLUID_VARIANTS);
+    std::vector<std::vector<Task>> tasks(N_FLUID_VARIANTS);
     for (int v = 0; v < N_FLUID_VARIANTS; ++v) tasks[v] = make_tasks(L.insts, v);
     // zero everything (padding columns, force fields, flags, error word),
     // then the instance table, the tile lists and the initial fields
@@ -561,7 +703,7 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->insts, L.insts.data(), n * sizeof(Inst), cudaMemcpyHostToDevice, ctx->stream);
     for (int v = 0; v < N_FLUID_VARIANTS && e == cudaSuccess; ++v)
-        e = cudaMemcpyAsync(ctx->tasks[v], tasks[v].data(), tasks[v].size() * sizeof(int4),
+        e = cudaMemcpyAsync(ctx->tasks[v], tasks[v].data(), tasks[v].size() * sizeof(Task),
                             cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess && (ctx->prec == LBM_FP32 || ctx->prec == LBM_FP16_SHIFTED)) {
         // the staged variants' tensor maps; without them those variants are off
@@ -579,8 +721,6 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
     }
     for (int i = 0; i < n && e == cudaSuccess; ++i)
         e = launch_init(ctx->prec, ctx->f[0], L.insts[i], cfgs[i].init, cfgs[i].init_u, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e == cudaSuccess && autotune(ctx) != LBM_OK) e = cudaErrorUnknown;
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -699,6 +839,8 @@ lbm_status add_particle_t(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, co
     CK(cudaStreamSynchronize(ctx->stream));
     drop_graphs(ctx);  // captured steps do not know this particle
     ctx->rc_max = std::max(ctx->rc_max, so.rcirc);
+    ctx->hrc.push_back(so.rcirc);
+    ctx->items_dirty = true;
     ctx->hblk.insert(ctx->hblk.end(), blocks.begin(), blocks.end());
     ctx->hpart.push_back(make_int4(P.m0, n, inst, box_tiles(so.rcirc)));
     CK(cudaMemcpyAsync(ctx->ptab + ctx->np, &ctx->hpart.back(), sizeof(int4), cudaMemcpyHostToDevice,
@@ -902,6 +1044,16 @@ lbm_status lbm_set_wall_tangents(lbm_ctx* ctx, int32_t instance, const double* d
 
 lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps) {
     if (!ctx || nsteps < 0) return LBM_EINVAL;
+    if (fused(ctx) && ctx->items_dirty && nsteps > 0) {  // the work list, before any capture
+        lbm_status s = build_items(ctx);
+        if (s != LBM_OK) return s;
+    }
+    if (!ctx->tuned && nsteps > 0) {  // the first step picks the tile variant
+        bool stepped = false;
+        lbm_status s = tune_step(ctx, &stepped);
+        if (s != LBM_OK) return s;
+        if (stepped) nsteps -= 1;
+    }
     if (ctx->stall_limit && nsteps > 0) {  // lbm_inject_stall: this step alone, launched directly
         lbm_status s = enqueue_step(ctx, ctx->stream, ctx->cur, ctx->steps, nullptr, true);
         ctx->stall_limit = 0;
@@ -939,6 +1091,16 @@ lbm_status lbm_step_timed(lbm_ctx* ctx, int32_t nsteps, double* ms_step, double*
     // the event before the fluid kernel only when its time is asked for: it
     // keeps the fluid kernel from starting before the spreading kernel ends
     const bool mid = ms_fluid != nullptr;
+    if (fused(ctx) && ctx->items_dirty && nsteps > 0) {
+        lbm_status s = build_items(ctx);
+        if (s != LBM_OK) return s;
+    }
+    if (!ctx->tuned && nsteps > 0) {  // the first step picks the tile variant (untimed)
+        bool stepped = false;
+        lbm_status s = tune_step(ctx, &stepped);
+        if (s != LBM_OK) return s;
+        if (stepped) nsteps -= 1;
+    }
     for (int32_t k = 0; k < nsteps; ++k) {
         // each step is a replay of its captured one-step graph (as lbm_step
         // replays steps), with the timing events inside it
@@ -973,8 +1135,8 @@ lbm_status lbm_sync(lbm_ctx* ctx) {
 
 lbm_status lbm_inject_stall(lbm_ctx* ctx, int64_t wait_cycles) {
     if (!ctx) return LBM_EINVAL;
-    if (!FLUID_VARIANTS[ctx->variant].stages)
-        return fail(ctx, LBM_EINVAL, "the tile variant in use has no staged copies to stall");
+    if (!FLUID_VARIANTS[ctx->variant].stages && !fused(ctx))
+        return fail(ctx, LBM_EINVAL, "neither a staged tile variant nor the fused step: nothing to stall");
     if (wait_cycles < 1000000 || wait_cycles > WAIT_LIMIT)
         return fail(ctx, LBM_EINVAL, "wait_cycles must lie in [1e6, 2e9]");
     ctx->stall_limit = wait_cycles;
@@ -1064,10 +1226,36 @@ lbm_status lbm_set_tile(lbm_ctx* ctx, int32_t variant) {
     if (variant < 0 || variant >= N_FLUID_VARIANTS) return fail(ctx, LBM_EINVAL, "no such tile variant");
     if (!ctx_variant_ok(ctx, variant))
         return fail(ctx, LBM_EINVAL, "the precision has no such tile variant");
+    ctx->tuned = true;
     if (variant != ctx->variant) {
         ctx->variant = variant;
         drop_graphs(ctx);  // captured steps launch the old shape
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_step_mode(lbm_ctx* ctx, int32_t mode) {
+    if (!ctx) return LBM_EINVAL;
+    if (mode != LBM_STEP_SEPARATE && mode != LBM_STEP_FUSED) return fail(ctx, LBM_EINVAL, "no such step mode");
+    if (mode == LBM_STEP_FUSED && ctx->prec == LBM_FP32_TANGENT)
+        return fail(ctx, LBM_EINVAL, "the fused step has no tangent mode");
+    if (mode == LBM_STEP_FUSED && ctx->items_cap == 0)
+        return fail(ctx, LBM_EINVAL, "the fused step is for batches (lbm_init_batch, two or more instances)");
+    if (mode == ctx->step_mode) return LBM_OK;
+    drop_graphs(ctx);
+    ctx->step_mode = mode;
+    if (mode == LBM_STEP_FUSED) {
+        ctx->items_dirty = true;
+        ctx->variant = fused_fluid_variant();
+        ctx->tuned = true;
+        CK(cudaMemsetAsync(ctx->counters, 0, 2 * ctx->counter_words * sizeof(unsigned), ctx->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_step_mode(const lbm_ctx* ctx, int32_t* mode) {
+    if (!ctx || !mode) return LBM_EINVAL;
+    *mode = ctx->step_mode;
     return LBM_OK;
 }
 
@@ -1169,5 +1357,8 @@ extern "C" lbm_status lbm_step_static(lbm_ctx* ctx, int32_t nsteps) {
         ctx->cur ^= 1;
         ctx->steps += 1;
     }
+    // a context in the fused step mode: its next fused step finds its counters cleared
+    if (ctx->step_mode == LBM_STEP_FUSED && nsteps > 0)
+        CK(cudaMemsetAsync(ctx->counters, 0, 2 * ctx->counter_words * sizeof(unsigned), ctx->stream));
     return LBM_OK;
 }

@@ -172,11 +172,12 @@ __device__ __forceinline__ GlobalSrc<S, C, N> global_src(const S* f, const Geo& 
     return GlobalSrc<S, C, N>{f, G.plane, G.pitch, G.ny};
 }
 // StageSrc: a tile's rows copied into shared memory, [9][rows][sw] elements
-// per plane and destination row, element 0 of a row holding column xs.
+// per plane and destination row, element 0 of a row holding column xs
+// (pitch, ny: the lattice's row pitch and rows).
 template <class S, class C, int N>
 struct StageSrc {
     const S* st;
-    int sw, rows, y0, xs;
+    int sw, rows, y0, xs, pitch, ny;
     __device__ __forceinline__ const S* row(int i, int y) const {
         return st + (i * rows + (y - y0)) * sw - xs;
     }
@@ -208,6 +209,68 @@ __device__ __forceinline__ bool cell_update(C v[9], const Geo& G, C fx_ib, C fy_
     return density_ok(drho);
 }
 
+// When a tile may read the forces of this step.  NoWait: at once (the
+// flags load goes out with the population loads).  PdlWait: launched with
+// programmatic stream serialization after the spreading kernel: the
+// populations are loaded first, then the kernel waits for the spreading
+// kernel before it reads the flags.  A hook with LATE = true is called
+// after the population loads (per warp).
+struct NoWait {
+    static constexpr bool LATE = false;
+    __device__ __forceinline__ void operator()() const {}
+};
+struct PdlWait {
+    static constexpr bool LATE = true;
+    __device__ __forceinline__ void operator()() const {
+        pdl_wait();
+        pdl_trigger();
+    }
+};
+
+// The forces of this thread's cells when its segment is flagged (zero
+// otherwise); the field is cleared for the next step after the tile.
+template <class C, int N>
+__device__ __forceinline__ void load_forces(bool forced, const C* flb, long long row, long long plane, int x0,
+                                            int nx, C fx[N], C fy[N]) {
+    if (!forced) return;
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+        if (x0 + k < nx) {
+            fx[k] = flb[row + x0 + k];
+            fy[k] = flb[plane + row + x0 + k];
+        }
+}
+
+// Pulled values of plane i for the thread's N cells from its loaded vector
+// q: a pull along +-x is a one-lane shuffle of the neighbouring vector; bnd
+// is the element past the warp's row end (lanes 0 / 31); on the periodic x
+// edge the cell x = 0 (wrap_l) or x = nx - 1 (at ke, wrap_r) takes wl.
+template <class C, int N>
+__device__ __forceinline__ void pulled_plane(int i, const C q[N], C bnd, C wl, int lane, bool wrap_l, bool wrap_r,
+                                             int ke, C v[N]) {
+    if (cx(i) == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[k] = q[k];
+    } else if (cx(i) > 0) {  // source x - 1
+        C left = __shfl_up_sync(0xffffffffu, q[N - 1], 1);
+        if (lane == 0) left = bnd;
+        v[0] = wrap_l ? wl : left;
+#pragma unroll
+        for (int k = 1; k < N; ++k) v[k] = q[k - 1];
+    } else {  // source x + 1
+        C right = __shfl_down_sync(0xffffffffu, q[0], 1);
+        if (lane == 31) right = bnd;
+#pragma unroll
+        for (int k = 0; k < N - 1; ++k) v[k] = q[k + 1];
+        v[N - 1] = right;
+        if (wrap_r) {
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+                if (k == ke) v[k] = wl;
+        }
+    }
+}
+
 // Fused step of one tile: N consecutive cells (x0 .. x0+N-1, x0 = N * lane
 // index) of one row per thread, a warp covering 32 N cells of a row, the
 // block BY rows.  Populations move as vectors of N elements: a pull along
@@ -218,21 +281,28 @@ __device__ __forceinline__ bool cell_update(C v[9], const Geo& G, C fx_ib, C fy_
 // thread holds four cells; with one cell per thread the x-wall cells in
 // between stay on the vector path with their Zou-He completion.  The
 // periodic x edge patches the three populations that cross it.
-// PDL: launched with programmatic stream serialization after the spreading
-// kernel: the population loads come first, the force flags and the forces
-// after pdl_wait().  Otherwise the flags are loaded with the populations.
+// wait: when the forces may be read (NoWait, PdlWait, or the fused step's
+// wait for its instance's spreading tiles): with a LATE hook the population
+// loads come first, the force flags and the forces after the hook;
+// otherwise the flags are loaded with the populations.
 // Watchdog (check != 0): a warp with a cell of non-positive or non-finite
-// density sets ERR_NONFINITE in *err (one atomic per such warp).
+// density sets ERR_NONFINITE in *err (one atomic per such warp).  keep != 0
+// leaves the force field and its flags for another launch of the same step.
 // src: where the streamed populations come from (GlobalSrc or StageSrc);
 // the periodic patch and the per-cell general path read fin itself.
-template <class S, class C, int N, bool PDL, class Src>
+template <class S, class C, int N, class Src, class Wait>
 __device__ __forceinline__ void fluid_tile(const Src& src, const Geo& G, const S* __restrict__ fin,
                                            S* __restrict__ fout, C* __restrict__ flb,
                                            uint8_t* __restrict__ flags, int tx, int y, int check,
-                                           unsigned* err) {
+                                           unsigned* err, int keep, const Wait& wait) {
+    constexpr bool PDL = Wait::LATE;
     const int lane = threadIdx.x & 31;
     const int x0 = (tx * 32 + lane) * N;
-    if (y >= G.ny) return;  // whole warp (one row)
+    // (FP32 vector tiles take the row count and pitch from the source, so
+    // that their loads need no descriptor load; the others from G, which
+    // measured faster for them on GB300)
+    constexpr bool HOIST = sizeof(S) == 4 && N >= 2;
+    if (y >= (HOIST ? src.ny : G.ny)) return;  // whole warp (one row)
     const long long row = (long long)y * G.pitch;
     // the vector values of cell x0 + k are its pulled populations whenever
     // all 9 sources are inside (none clamped); on an x wall all but the
@@ -245,69 +315,83 @@ __device__ __forceinline__ void fluid_tile(const Src& src, const Geo& G, const S
     if (!PDL) forced = any && flags[seg] != 0;
     bool bad = false;  // watchdog
 
-    C v[9][N];
-    // vector loads for every lane (addresses clamped in-bounds), shuffles by all
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const S* rp = src.row(i, y);
-        const int xa = min(x0, G.pitch - N);
-        C q[N];
-        src.vec(rp + xa, q);
-        if (cx(i) == 0) {
-#pragma unroll
-            for (int k = 0; k < N; ++k) v[i][k] = q[k];
-        } else if (cx(i) > 0) {  // source x - 1
-            C left = __shfl_up_sync(0xffffffffu, q[N - 1], 1);
-            if (lane == 0) left = src.one(rp + max(xa - 1, 0));
-            v[i][0] = left;
-#pragma unroll
-            for (int k = 1; k < N; ++k) v[i][k] = q[k - 1];
-        } else {  // source x + 1
-            C right = __shfl_down_sync(0xffffffffu, q[0], 1);
-            if (lane == 31) right = src.one(rp + min(xa + N, G.pitch - 1));
-#pragma unroll
-            for (int k = 0; k < N - 1; ++k) v[i][k] = q[k + 1];
-            v[i][N - 1] = right;
-        }
-    }
-    // periodic x: the cells x = 0 and x = nx - 1 get the three populations
-    // that cross the periodic edge by scalar loads; their other six are
-    // already in the vectors, so they stay on the fast path
+    C v[9][N], fxh[N], fyh[N];  // (fxh, fyh: the forces read early, HOIST)
     const bool wrap = G.px && rows_in && any;
     const int ke = G.nx - 1 - x0;  // position of x = nx - 1 in this thread's cells
-    if (wrap && (x0 == 0 || (ke >= 0 && ke < N))) {
+    const bool wrap_l = wrap && x0 == 0, wrap_r = wrap && ke >= 0 && ke < N;
+    // Two load orders, chosen per storage type and width by measurement on
+    // GB300: FP32 vectors of two or four cells issue every population load
+    // and the force loads of a flagged segment before consuming any (the
+    // flag -> force chain then overlaps the population loads); FP16, FP64
+    // and one-cell tiles load and shuffle plane by plane and read the forces
+    // after the populations (fewer live registers).
+    if constexpr (HOIST) {
+        C q[9][N], bnd[9], wl[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const S* rp = fin + (long long)i * G.plane + (long long)(y - cy(i)) * G.pitch;
-            if (cx(i) > 0 && x0 == 0) v[i][0] = ld<S, C>(rp + (G.nx - 1));
-            if (cx(i) < 0 && ke >= 0 && ke < N) {
-                const C w0 = ld<S, C>(rp);
+            const S* rp = src.row(i, y);
+            const int xa = min(x0, src.pitch - N);
+            src.vec(rp + xa, q[i]);
+            bnd[i] = wl[i] = C(0);
+            if (cx(i) > 0 && lane == 0) bnd[i] = src.one(rp + max(xa - 1, 0));
+            if (cx(i) < 0 && lane == 31) bnd[i] = src.one(rp + min(xa + N, src.pitch - 1));
+            const S* wp = fin + (long long)i * G.plane + (long long)(y - cy(i)) * G.pitch;
+            if (cx(i) > 0 && wrap_l) wl[i] = ld<S, C>(wp + (G.nx - 1));
+            if (cx(i) < 0 && wrap_r) wl[i] = ld<S, C>(wp);
+        }
+        if (PDL) {
+            // the populations are on their way; the forces of this step
+            // come from the spreading items before this one
+            wait();
+            forced = any && flags[seg] != 0;
+        }
 #pragma unroll
-                for (int k = 0; k < N; ++k)
-                    if (k == ke) v[i][k] = w0;
+        for (int k = 0; k < N; ++k) fxh[k] = fyh[k] = C(0);
+        load_forces<C, N>(forced, flb, row, G.plane, x0, G.nx, fxh, fyh);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) pulled_plane<C, N>(i, q[i], bnd[i], wl[i], lane, wrap_l, wrap_r, ke, v[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const S* rp = src.row(i, y);
+            const int xa = min(x0, G.pitch - N);
+            C q[N], bnd = C(0), wl = C(0);
+            src.vec(rp + xa, q);
+            if (cx(i) > 0 && lane == 0) bnd = src.one(rp + max(xa - 1, 0));
+            if (cx(i) < 0 && lane == 31) bnd = src.one(rp + min(xa + N, G.pitch - 1));
+            pulled_plane<C, N>(i, q, bnd, wl, lane, false, false, ke, v[i]);
+        }
+        // periodic x: the three populations that cross the edge
+        if (wrap_l || wrap_r) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const S* wp = fin + (long long)i * G.plane + (long long)(y - cy(i)) * G.pitch;
+                if (cx(i) > 0 && wrap_l) v[i][0] = ld<S, C>(wp + (G.nx - 1));
+                if (cx(i) < 0 && wrap_r) {
+                    const C w0 = ld<S, C>(wp);
+#pragma unroll
+                    for (int k = 0; k < N; ++k)
+                        if (k == ke) v[i][k] = w0;
+                }
             }
         }
-    }
-    if (PDL) {
-        // the populations are on their way; the forces of this step come
-        // from the spreading kernel before this one
-        pdl_wait();
-        pdl_trigger();
-        forced = any && flags[seg] != 0;
+        if (PDL) {
+            wait();
+            forced = any && flags[seg] != 0;
+        }
     }
     if (any) {
         C fxi[N], fyi[N];
 #pragma unroll
         for (int k = 0; k < N; ++k) fxi[k] = fyi[k] = C(0);
-        if (forced) {
+        if constexpr (HOIST) {
 #pragma unroll
-            for (int k = 0; k < N; ++k)
-                if (x0 + k < G.nx) {
-                    fxi[k] = flb[row + x0 + k];
-                    fyi[k] = flb[G.plane + row + x0 + k];
-                    flb[row + x0 + k] = C(0);
-                    flb[G.plane + row + x0 + k] = C(0);
-                }
+            for (int k = 0; k < N; ++k) {
+                fxi[k] = fxh[k];
+                fyi[k] = fyh[k];
+            }
+        } else {
+            load_forces<C, N>(forced, flb, row, G.plane, x0, G.nx, fxi, fyi);
         }
         // interior cells from the vector values.  With one cell per thread
         // so are the cells of an x wall between the two y edges: their six
@@ -357,7 +441,7 @@ __device__ __forceinline__ void fluid_tile(const Src& src, const Geo& G, const S
                 pull_general<S, C>(fin, G, xk, y, c);
                 complete_walls<S, C>(fin, G, xk, y, c);
                 C gx = C(0), gy = C(0);
-                if (forced) {  // forces of this cell were read (and zeroed) above
+                if (forced) {  // forces of this cell were read above
 #pragma unroll
                     for (int j = 0; j < N; ++j)
                         if (j == k) {
@@ -372,9 +456,21 @@ __device__ __forceinline__ void fluid_tile(const Src& src, const Geo& G, const S
         }
         bad = !ok;
     }
+    // the force field and the flag are cleared for the next step only now,
+    // after their values were used (stores right behind the loads of the
+    // same words measured 35 % slower on the screening batch); keep: the
+    // autotuner's repeated launches of one step leave them in place
+    if (forced && !keep) {
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            if (x0 + k < G.nx) {
+                flb[row + x0 + k] = C(0);
+                flb[G.plane + row + x0 + k] = C(0);
+            }
+    }
     __syncwarp();
     if (check && __any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
-    if (forced && (lane & (32 / N - 1)) == 0) flags[seg] = 0;  // one lane per segment
+    if (forced && !keep && (lane & (32 / N - 1)) == 0) flags[seg] = 0;  // one lane per segment
 }
 
 }  // namespace

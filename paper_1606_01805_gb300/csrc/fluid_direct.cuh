@@ -5,6 +5,8 @@
 // fluid_direct_a.cu and fluid_direct_b.cu.
 #pragma once
 
+#include <type_traits>
+
 #include "fluid_core.cuh"
 
 namespace lbib {
@@ -21,9 +23,11 @@ template <class S, int N, int BYt> struct FluidOccupancy {
 };
 
 // fused fluid step over the task list (all instances): CTA b takes the
-// TASKS_PER_CTA consecutive tasks from b * TASKS_PER_CTA (mostly tiles of one
-// lattice, whose task records and descriptor then come from L1 after the
-// first), and further ones a grid apart if the grid is smaller
+// TASKS_PER_CTA consecutive tasks from b * TASKS_PER_CTA, and further ones a
+// grid apart if the grid is smaller.  A task record carries the geometry
+// that addresses the tile's populations, so their loads follow the task's
+// load directly; the instance descriptor (constants, flags, forces) is read
+// beside them.
 template <class S, class C, int N, int BYt>
 __global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value) k_fluid(FluidArgs a) {
     const S* fin = static_cast<const S*>(a.fin);
@@ -31,11 +35,11 @@ __global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value) k_
     C* flb = static_cast<C*>(a.flb);
     for (int t0 = blockIdx.x * TASKS_PER_CTA; t0 < a.ntasks; t0 += gridDim.x * TASKS_PER_CTA)
     for (int t = t0; t < min(t0 + TASKS_PER_CTA, a.ntasks); ++t) {
-        const int4 task = a.tasks[t];
-        const Inst& I = a.insts[task.x];
-        fluid_tile<S, C, N, false>(global_src<S, C, N>(fin + I.f_off, I.G), I.G, fin + I.f_off,
-                                   fout + I.f_off, flb + I.flb_off, a.flags + I.flags_off, task.y,
-                                   task.z * BYt + threadIdx.y, a.check, a.err);
+        const Task task = a.tasks[t];
+        const Inst& I = a.insts[task.inst];
+        const GlobalSrc<S, C, N> src{fin + task.f_off, (long long)task.pitch * task.ny, task.pitch, task.ny};
+        fluid_tile<S, C, N>(src, I.G, fin + task.f_off, fout + task.f_off, flb + I.flb_off, a.flags + I.flags_off,
+                            task.tx, task.ty * BYt + threadIdx.y, a.check, a.err, a.keep, NoWait{});
     }
 }
 
@@ -46,9 +50,10 @@ template <class S, class C, int N, int BYt, bool PDL>
 __global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value)
     k_fluid_one(FluidArgs a, Inst I) {
     const S* fin = static_cast<const S*>(a.fin) + I.f_off;
-    fluid_tile<S, C, N, PDL>(global_src<S, C, N>(fin, I.G), I.G, fin, static_cast<S*>(a.fout) + I.f_off,
-                             static_cast<C*>(a.flb) + I.flb_off, a.flags + I.flags_off, blockIdx.x,
-                             blockIdx.y * BYt + threadIdx.y, a.check, a.err);
+    using Wait = typename std::conditional<PDL, PdlWait, NoWait>::type;
+    fluid_tile<S, C, N>(global_src<S, C, N>(fin, I.G), I.G, fin, static_cast<S*>(a.fout) + I.f_off,
+                        static_cast<C*>(a.flb) + I.flb_off, a.flags + I.flags_off, blockIdx.x,
+                        blockIdx.y * BYt + threadIdx.y, a.check, a.err, a.keep, Wait{});
 }
 
 template <class S, class C, int N, int BYt>

@@ -98,7 +98,8 @@ __device__ __forceinline__ void tensor_copy(void* dst, const void* tmap, int x, 
 template <bool ONE>
 __device__ __forceinline__ int4 tile_of(const FluidArgs& a, int t, int ntx) {
     if (ONE) return make_int4(0, t % ntx, t / ntx, 0);
-    return a.tasks[t];
+    const Task& k = a.tasks[t];
+    return make_int4(k.inst, k.tx, k.ty, 0);
 }
 
 // Warp 0: copy the rows tile t needs into stage s and arm its barrier.
@@ -187,18 +188,19 @@ __global__ void __launch_bounds__(STHREADS, 2)
         }
         const int4 tk = slot[s];
         const int x0 = tk.y * Sh::TW, y0 = tk.z * STH;
-        const StageSrc<S, C, N> src{stages + s * Sh::STAGE, Sh::SW, STH, y0, x0 - Sh::H};
+        const int pitch = ONE ? one.G.pitch : sinst[s].G.pitch, ny = ONE ? one.G.ny : sinst[s].G.ny;
+        const StageSrc<S, C, N> src{stages + s * Sh::STAGE, Sh::SW, STH, y0, x0 - Sh::H, pitch, ny};
         if constexpr (ONE) {
             const S* fin = static_cast<const S*>(a.fin) + one.f_off;
-            fluid_tile<S, C, N, false>(src, one.G, fin, static_cast<S*>(a.fout) + one.f_off,
+            fluid_tile<S, C, N>(src, one.G, fin, static_cast<S*>(a.fout) + one.f_off,
                                        static_cast<C*>(a.flb) + one.flb_off, a.flags + one.flags_off, tk.y,
-                                       y0 + warp, a.check, a.err);
+                                       y0 + warp, a.check, a.err, a.keep, NoWait{});
         } else {
             const Inst& I = sinst[s];
             const S* fin = static_cast<const S*>(a.fin) + I.f_off;
-            fluid_tile<S, C, N, false>(src, I.G, fin, static_cast<S*>(a.fout) + I.f_off,
+            fluid_tile<S, C, N>(src, I.G, fin, static_cast<S*>(a.fout) + I.f_off,
                                        static_cast<C*>(a.flb) + I.flb_off, a.flags + I.flags_off, tk.y,
-                                       y0 + warp, a.check, a.err);
+                                       y0 + warp, a.check, a.err, a.keep, NoWait{});
         }
         __syncthreads();  // stage s is free again
         const int tn = t + ST * gridDim.x;

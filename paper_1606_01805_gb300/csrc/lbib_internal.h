@@ -146,8 +146,16 @@ struct SpreadArgs {
     int4 part_inline[INLINE_PARTICLES];  // the first np_inline entries of ptab
 };
 
-// Fluid step over a list of tiles: task t = (instance, tile x, tile y, 0),
-// a tile being 32 * cpt cells of by rows.  One launch covers every tile of
+// One tile of a task list: instance, tile x, tile y (a tile being 32 * cpt
+// cells of by rows), and the instance's population offset and row geometry,
+// so that a kernel can address the tile's populations after one load.
+struct alignas(16) Task {
+    int inst, tx, ty, pitch;
+    long long f_off;
+    int ny, pad_;
+};
+
+// Fluid step over a list of tiles (Task).  One launch covers every tile of
 // every instance; a CTA takes tasks blockIdx.x, blockIdx.x + gridDim.x, ...
 struct FluidArgs {
     const void* fin;
@@ -155,10 +163,11 @@ struct FluidArgs {
     void* flb;
     uint8_t* flags;
     const Inst* insts;
-    const int4* tasks;
+    const Task* tasks;
     int ntasks;
     int check;                // watchdog: flag a non-positive density or a non-finite value
     int stall;                // test hook: the staged kernel's first CTA waits for 16 bytes too many
+    int keep;                 // autotuner: leave the force field and its flags in place
     unsigned* err;
     // staged variants: the tensor maps of the population buffer read, per
     // instance (device array of CUtensorMap), and of a single lattice (host)
@@ -186,6 +195,27 @@ constexpr bool variant_valid(int prec, int v) {
     return v >= 0 && v < N_FLUID_VARIANTS &&
            (prec == LBM_FP32_TANGENT ? v == 2 : (prec == LBM_FP64 ? FLUID_VARIANTS[v].stages == 0 : true));
 }
+
+// The fused step of a batch (one persistent launch per step): its work
+// list and counters.  Item kinds, as int4 (kind, a, b, c):
+//   FI_PROBES  (kind, first marker block, blocks <= 8, particle)
+//   FI_MARKERS (kind, first marker block, blocks <= 8, particle)
+//   FI_SPREAD  (kind, tile, particle, the particle's tile bound)
+//   FI_FLUID   (kind, task of the 2 x 8 task list, instance, spreading
+//               tiles of the instance)
+enum { FI_PROBES = 0, FI_MARKERS = 1, FI_SPREAD = 2, FI_FLUID = 3 };
+struct FusedArgs {
+    FluidArgs fa;             // fluid tiles (the 2 x 8 task list)
+    ParticleArgs pa;          // probes, rigid update, markers
+    SpreadArgs sa;            // spreading tiles
+    const int4* items;
+    int nitems;
+    int np, ninst;
+    int parity;               // counter set of this step (the other one is cleared for the next)
+    unsigned* counters[2];    // two sets of 2 np + ninst + 2 words
+    long long wait_limit;     // clock cycles of a bounded wait
+    int stall, stall_ticket;  // test hook: that fluid item waits for one spreading tile too many
+};
 
 struct FieldArgs {
     const void* f;            // population buffer
@@ -227,6 +257,12 @@ cudaError_t launch_put_pops(int prec, const double* h, const Inst& I, int y0, in
                             cudaStream_t s);
 cudaError_t launch_get_pops(int prec, const void* fbuf, const Inst& I, int y0, int rows, double* h,
                             cudaStream_t s);
+// the fused step (step_fused.cu): one launch for the whole step of a batch;
+// its spreading tiles have fused_spread_rows() rows and its fluid tiles
+// are the task list of variant fused_fluid_variant()
+cudaError_t launch_step_fused(int prec, const FusedArgs& f, int sms, cudaStream_t s);
+int fused_spread_rows();
+int fused_fluid_variant();
 // OR `bits` into the device error word, as a kernel that detects an error does
 cudaError_t launch_raise(unsigned* err, unsigned bits, cudaStream_t s);
 cudaError_t launch_probes(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s);

@@ -28,12 +28,14 @@ LBM_TANGENT_FIELDS = 10     # xc, yc, theta, u[0], u[1], omega, F[0], F[1], M, o
 TANGENT_FIELDS = ("xc", "yc", "theta", "ux", "uy", "omega", "Fx", "Fy", "M", "omega_sum")
 SEED_FIELDS = ("dim0", "dim1", "xc", "yc", "theta", "rho_s")
 LBM_INIT_REST, LBM_INIT_COUETTE, LBM_INIT_TAYLOR_GREEN = 0, 1, 2
+LBM_STEP_SEPARATE, LBM_STEP_FUSED = 0, 1  # step modes of a batch (lbm_set_step_mode)
 LBM_SHAPE_CIRCLE, LBM_SHAPE_ELLIPSE, LBM_SHAPE_RECT, LBM_SHAPE_SQUARE, LBM_SHAPE_TRIANGLE = range(5)
 LBM_W_EXP, LBM_W_CUBIC, LBM_W_QUARTIC, LBM_W_COSINE, LBM_W_POLY = range(5)
 
 # every symbol include/lbib.h declares
 EXPORTS = ["lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "lbm_step_timed",
-           "lbm_sync", "lbm_inject_status", "lbm_inject_stall", "lbm_tile_info", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
+           "lbm_sync", "lbm_inject_status", "lbm_inject_stall", "lbm_tile_info", "lbm_set_step_mode",
+           "lbm_get_step_mode", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
            "lbm_get_particles", "lbm_steps_done", "lbm_last_error", "lbm_destroy",
            "lbm_step_static", "lbm_batch_workspace_bytes", "lbm_init_batch", "lbm_instances",
            "lbm_add_particle_to", "lbm_get_instance_fields", "lbm_get_instance_populations",
@@ -100,6 +102,8 @@ def load(path: os.PathLike | str | None = None):
     L.lbm_inject_status.argtypes = [C.c_void_p, C.c_int32]
     L.lbm_inject_stall.argtypes = [C.c_void_p, C.c_int64]
     L.lbm_tile_info.argtypes = [C.c_int32, C.c_int32] + [C.POINTER(C.c_int32)] * 3
+    L.lbm_set_step_mode.argtypes = [C.c_void_p, C.c_int32]
+    L.lbm_get_step_mode.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
     L.lbm_get_fields.argtypes = [C.c_void_p, _dp, _dp, _dp]
     L.lbm_get_populations.argtypes = [C.c_void_p, _dp]
     L.lbm_set_populations.argtypes = [C.c_void_p, _dp]
@@ -129,7 +133,8 @@ def load(path: os.PathLike | str | None = None):
     L.lbm_get_particle_tangents.argtypes = [C.c_void_p, _dp, C.c_int32, C.POINTER(C.c_int32)]
     L.lbm_get_field_tangents.argtypes = [C.c_void_p, C.c_int32, _dp, _dp, _dp]
     for fn in ("lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "lbm_step_timed",
-               "lbm_sync", "lbm_inject_status", "lbm_inject_stall", "lbm_tile_info", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
+               "lbm_sync", "lbm_inject_status", "lbm_inject_stall", "lbm_tile_info", "lbm_set_step_mode",
+               "lbm_get_step_mode", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
                "lbm_get_particles", "lbm_step_static", "lbm_batch_workspace_bytes",
                "lbm_init_batch", "lbm_add_particle_to", "lbm_get_instance_fields",
                "lbm_get_instance_populations", "lbm_set_instance_populations", "lbm_get_tile",
@@ -355,6 +360,15 @@ class Batch:
 
     def _shape(self, instance):
         return self.shapes[instance]
+
+    def set_step_mode(self, mode):
+        """LBM_STEP_SEPARATE or LBM_STEP_FUSED (one persistent launch per step)."""
+        self._check(load().lbm_set_step_mode(self._h, mode), "lbm_set_step_mode")
+
+    def step_mode(self):
+        m = C.c_int32()
+        self._check(load().lbm_get_step_mode(self._h, C.byref(m)), "lbm_get_step_mode")
+        return m.value
 
     def add_particle(self, instance, shape, dim, xc, yc, theta=0.0, rho_s=1.0, u0=(0.0, 0.0),
                      omega0=0.0, n_markers=0, tangent=None):

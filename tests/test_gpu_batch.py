@@ -108,3 +108,73 @@ def test_full_screening_batch_runs():
     ps = b.particles()
     assert len(ps) == 512
     assert all(np.isfinite([p["xc"], p["yc"], p["theta"], p["omega"]]).all() for p in ps)
+
+
+def _fused_pair(wls, prec, steps):
+    out = []
+    for mode in (lbib.LBM_STEP_SEPARATE, lbib.LBM_STEP_FUSED):
+        b = make_batch(wls, prec)
+        b.set_step_mode(mode)
+        assert b.step_mode() == mode
+        b.step(steps)
+        b.sync()
+        out.append(([b.populations(k) for k in range(len(wls))], b.particles()))
+        b.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64, lbib.LBM_FP16_SHIFTED])
+def test_fused_step_equals_separate_kernels(prec):
+    """One persistent launch per step (probe, marker, spreading and fluid
+    items of all instances in one work list) gives the bits of the separate
+    kernels, through a graph replay and direct steps."""
+    wls = small_batch()
+    (pa, qa), (pb, qb) = _fused_pair(wls, prec, 40)
+    for k in range(len(wls)):
+        np.testing.assert_array_equal(pb[k], pa[k], err_msg=wls[k].name)
+    assert qa == qb
+
+
+def test_fused_step_on_the_screening_batch():
+    """The 512-lattice screening batch, fused against separate kernels."""
+    wls = W.batched_screening(steps=0)
+    res = []
+    for mode in (lbib.LBM_STEP_SEPARATE, lbib.LBM_STEP_FUSED):
+        b = lbib.Batch([dict(W.batch_config(w), precision=FP32) for w in wls], max_particles=512,
+                       max_markers=600000)
+        for k, w in enumerate(wls):
+            b.add_particle(k, **w.particles[0].kwargs())
+        b.set_step_mode(mode)
+        b.step(6)
+        b.sync()
+        res.append(([b.populations(k) for k in (0, 255, 511)], b.particles()))
+        b.close()
+    for a, c in zip(res[0][0], res[1][0]):
+        np.testing.assert_array_equal(a, c)
+    assert res[0][1] == res[1][1]
+
+
+def test_step_modes_switch_between_steps():
+    wls = small_batch(n=4, seed=9)
+    a = make_batch(wls, FP32)
+    a.step(30)
+    b = make_batch(wls, FP32)
+    b.step(10)
+    b.set_step_mode(lbib.LBM_STEP_FUSED)
+    b.step(10)
+    b.set_step_mode(lbib.LBM_STEP_SEPARATE)
+    b.step(5)
+    b.set_step_mode(lbib.LBM_STEP_FUSED)
+    b.step(5)
+    for k in range(len(wls)):
+        np.testing.assert_array_equal(a.populations(k), b.populations(k))
+    assert a.particles() == b.particles()
+
+
+def test_fused_step_needs_a_batch():
+    sim = lbib.Simulation(64, 40, 0.8, precision=FP32)
+    assert lbib.load().lbm_set_step_mode(sim._h, lbib.LBM_STEP_FUSED) == lbib.LBM_EINVAL
+    wls = small_batch(n=2)
+    t = lbib.Batch([dict(W.batch_config(w), precision=lbib.LBM_FP32_TANGENT) for w in wls])
+    with pytest.raises(lbib.LbmError):
+        t.set_step_mode(lbib.LBM_STEP_FUSED)

@@ -185,3 +185,40 @@ def test_inject_stall_needs_a_staged_variant():
     sim.set_tile(7)
     with pytest.raises(lbib.LbmError):
         sim.inject_stall(10)  # below the allowed range
+
+
+def _fused_batch():
+    wls = W.batched_screening(n=3, seed=7, nx_range=(60, 110), ny_range=(40, 70), steps=0)
+    b = lbib.Batch([dict(W.batch_config(w), precision=FP32) for w in wls], max_particles=8)
+    for k, w in enumerate(wls):
+        b.add_particle(k, **w.particles[0].kwargs())
+    b.set_step_mode(lbib.LBM_STEP_FUSED)
+    return b
+
+
+def test_fused_step_wait_runs_out_and_reports_timeout():
+    """lbm_inject_stall in the fused step: one fluid item waits for a
+    spreading tile that does not exist; the bounded wait runs out, the step
+    aborts its other waits and LBM_ETIMEOUT is reported."""
+    b = _fused_batch()
+    b.step(3)
+    b.sync()
+    b.inject_stall(2_000_000)
+    b.step(1)
+    with pytest.raises(lbib.LbmError) as ei:
+        b.sync()
+    assert ei.value.status == lbib.LBM_ETIMEOUT
+    other = _fused_batch()
+    other.step(40)
+    other.sync()
+
+
+def test_fused_step_keeps_the_watchdog():
+    b = _fused_batch()
+    f = b.populations(1)
+    f[2, 10, 10] = np.nan
+    b.set_populations(1, f)
+    b.step(1)
+    with pytest.raises(lbib.LbmError) as ei:
+        b.sync()
+    assert ei.value.status == lbib.LBM_ENONFINITE
