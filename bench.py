@@ -279,6 +279,48 @@ def time_sensitivity(prec, steps, warmup, n=64):
     return sum(w.cells for w in wls), ms / steps, msf / steps
 
 
+def time_adjoint(steps=2000, checkpoint_every=100, n=64):
+    """The sensitivity batch's reverse mode: wall time of one lbm_adjoint
+    call over `steps` steps (forward run, checkpoints, segment recompute and
+    the reverse sweep; both outputs for every instance) beside the wall time
+    of the same `steps` plain FP32 steps."""
+    import numpy as np
+    import torch
+
+    from paper_1606_01805_gb300 import lbib
+    from paper_1606_01805_gb300 import workloads as W
+
+    P, T = W.sensitivity_batch(n=n)
+    wls = [W.sensitivity_ellipse(*P[b], steps=0, theta=float(T[b])) for b in range(n)]
+
+    def make(prec):
+        sim = lbib.Batch([dict(W.batch_config(w), precision=prec) for w in wls], max_particles=n,
+                         max_markers=n * (W.SENS_MARKERS + 8))
+        for b, w in enumerate(wls):
+            sim.add_particle(b, **w.particles[0].kwargs())
+        return sim
+
+    def wall(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3
+
+    out = {}
+    for rep in range(2):  # the first pass warms the code paths and allocations
+        sim = make(lbib.LBM_FP32)
+        ms_plain = wall(lambda: sim.step(steps))
+        sim.close()
+        sim = make(lbib.LBM_FP32)
+        seed = np.tile([1.0, 1.0 / steps], (n, 1))
+        ms_adj = wall(lambda: sim.adjoint(steps, checkpoint_every, seed))
+        sim.close()
+        out = {"steps": steps, "checkpoint_every": checkpoint_every, "ms_plain": ms_plain,
+               "ms_adjoint": ms_adj, "adjoint_over_plain_time": ms_adj / ms_plain}
+    return out
+
+
 def time_per_instance(prec, sweeps):
     """The same 512 lattices as 512 contexts, stepped one after another
     (each replays its own captured 32-step graphs): device time per step."""
@@ -537,6 +579,9 @@ def main():
                               "fluid_GBps": bpc * tc / (tmsf * 1e-3) / 1e9,
                               "bytes_per_cell": bpc}
             tan["tangent_over_plain_time"] = tan["tangent"]["ms_per_step"] / tan["plain_fp32"]["ms_per_step"]
+            tan["adjoint"] = dict(time_adjoint(), method="reverse mode (lbm_adjoint): one forward run, "
+                                  "checkpoints every 100 steps, segment recompute, reverse sweep; "
+                                  "both outputs of every instance; wall time of the call")
             out["tangent"] = tan
         if not args.no_cpu:
             legs = cpu_oracle_rates(wl)

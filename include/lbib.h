@@ -414,6 +414,40 @@ lbm_status lbm_get_particle_tangents(lbm_ctx* ctx, double* out, int32_t cap, int
 lbm_status lbm_get_field_tangents(lbm_ctx* ctx, int32_t instance, double* drho, double* dux,
                                   double* duy);
 
+/*
+ * Reverse-mode differentiation (adjoint) of nsteps steps of the LB-IB map
+ * (Eqs. 2-16, the same discrete map as lbm_step), for two outputs at once
+ * (the paper has no counterpart; it serves the same sensitivity studies as
+ * the tangent mode, with a cost that does not grow with the number of
+ * inputs):
+ *   J_0 = sum_p seed[2p] * yc_p(N),   J_1 = sum_p seed[2p + 1] * omega_sum_p(N)
+ * over the particles p after N = nsteps steps (seed[2p + 1] = 1/N makes J_1
+ * the mean angular velocity).  The call runs the N steps forward (the
+ * context then holds the state after them, as after lbm_step), keeping the
+ * populations and bodies every checkpoint_every steps; it then walks the
+ * steps backwards, recomputing each segment between two checkpoints and
+ * carrying the adjoint of the populations and of the bodies back one step
+ * at a time (collision, streaming with the Zou-He walls, spreading, direct
+ * forcing, MLS interpolation, probe stress, force and torque sums, the
+ * two-level rigid update, all reversed).  Outputs (host, caller-owned):
+ *   dparticle[(p * 2 + o) * 6 + j] = d J_o / d q_j of particle p, for
+ *     q = (dim[0], dim[1], xc, yc, theta, rho_s) of its lbm_particle_desc
+ *     (the marker count held fixed);
+ *   dwall[(i * 2 + o) * 8 + (side * 2 + c)] = d J_o / d wall_u[side][c] of
+ *     instance i (through the Zou-He walls and, for the Couette initial
+ *     field, through the initial profile).
+ * In a batch whose instances hold one particle each, J_o of instance i is
+ * the output of its particle, so its rows are that particle's gradients.
+ * Requirements (else LBM_EINVAL): LBM_FP32, no step done yet, at least one
+ * particle, periodic x sides, the separate step mode; a marker or probe
+ * support must stay off the wall rows (else LBM_EDOMAIN).  The call
+ * allocates its own device memory (checkpoints, one segment of steps, the
+ * adjoint buffers; LBM_ENOMEM if it does not fit) and frees it before it
+ * returns.  Synchronises.
+ */
+lbm_status lbm_adjoint(lbm_ctx* ctx, int32_t nsteps, int32_t checkpoint_every, const double* seed,
+                       double* dparticle, double* dwall);
+
 /* Steps done since lbm_init. */
 int64_t lbm_steps_done(const lbm_ctx* ctx);
 

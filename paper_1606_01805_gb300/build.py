@@ -18,7 +18,7 @@ CSRC = PKG / "csrc"
 OUT = PKG / "_build"
 LIB = PKG / "liblbib.so"
 SOURCES = ["fluid.cu", "fluid_direct_a.cu", "fluid_direct_b.cu", "fluid_staged.cu", "particles.cu",
-           "step_fused.cu", "api.cu", "shapes.cpp"]
+           "step_fused.cu", "adjoint.cu", "api.cu", "shapes.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

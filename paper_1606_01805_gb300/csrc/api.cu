@@ -87,6 +87,12 @@ struct lbm_ctx {
     unsigned* counters = nullptr;
     size_t counter_words = 0;       // per set
     std::vector<double> hrc;        // per particle: circumscribed radius
+    // for the adjoint: body-frame marker geometry in FP64 (rb, nb, S per
+    // marker), each marker's particle, each particle's description
+    std::vector<double> hgeo;
+    std::vector<int> hmpart;
+    std::vector<lbm_particle_desc> hdesc;
+    long long pop_elems = 0, flb_elems = 0;  // elements of one population buffer / force field
     std::string msg;
 };
 
@@ -183,6 +189,7 @@ struct Layout {
     size_t items_cap, counter_words;
     int ntasks[N_FLUID_VARIANTS];
     int scratch_rows, scratch_cols, scratch_planes;
+    long long pop_elems, flb_elems;
 };
 
 Layout layout(const lbm_config* cfgs, int n) {
@@ -251,6 +258,8 @@ Layout layout(const lbm_config* cfgs, int n) {
     L.err = o; o = up(o + 16);
     L.scratch = o; o = up(o + (size_t)L.scratch_planes * L.scratch_rows * max_nx * sizeof(double));
     L.total = o;
+    L.pop_elems = fe;
+    L.flb_elems = fle;
     return L;
 }
 
@@ -669,6 +678,8 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
         ctx->ntasks[v] = L.ntasks[v];
     }
     ctx->tmaps = b + L.tmaps;
+    ctx->pop_elems = L.pop_elems;
+    ctx->flb_elems = L.flb_elems;
     ctx->items = reinterpret_cast<int4*>(b + L.items);
     ctx->items_cap = L.items_cap;
     ctx->counters = reinterpret_cast<unsigned*>(b + L.counters);
@@ -841,6 +852,13 @@ lbm_status add_particle_t(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, co
     ctx->rc_max = std::max(ctx->rc_max, so.rcirc);
     ctx->hrc.push_back(so.rcirc);
     ctx->items_dirty = true;
+    ctx->hdesc.push_back(*d);
+    for (int l = 0; l < n; ++l) {
+        const double g5[5] = {value_of(rb[2 * l]), value_of(rb[2 * l + 1]), value_of(nb[2 * l]),
+                              value_of(nb[2 * l + 1]), value_of(S[l])};
+        ctx->hgeo.insert(ctx->hgeo.end(), g5, g5 + 5);
+        ctx->hmpart.push_back(ctx->np);
+    }
     ctx->hblk.insert(ctx->hblk.end(), blocks.begin(), blocks.end());
     ctx->hpart.push_back(make_int4(P.m0, n, inst, box_tiles(so.rcirc)));
     CK(cudaMemcpyAsync(ctx->ptab + ctx->np, &ctx->hpart.back(), sizeof(int4), cudaMemcpyHostToDevice,
@@ -1274,6 +1292,238 @@ void lbm_destroy(lbm_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// lbm_adjoint: the reverse sweep (see include/lbib.h)
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int ADJ_LP = 13, ADJ_LG = 5, ADJ_LS = 4;  // the accumulators' lengths (adjoint.cu)
+
+// device memory of one adjoint run, carved from one allocation
+struct AdjMem {
+    char* base = nullptr;
+    size_t o = 0;
+    template <class T>
+    T* take(size_t n) {
+        T* p = reinterpret_cast<T*>(base + o);
+        o = up(o + n * sizeof(T));
+        return p;
+    }
+};
+
+lbm_status adjoint_run(lbm_ctx* ctx, int nsteps, int K, const double* seed, double* dpart, double* dwall) {
+    const int np = ctx->np, nm = ctx->nmark, ni = ctx->ninst;
+    const size_t popb = (size_t)ctx->pop_elems * sizeof(float);
+    const size_t partb = (size_t)np * ctx->psz, poseb = (size_t)np * ctx->pcsz;
+    const int nck = (nsteps + K - 1) / K;
+    // sizes first (a null base), then one allocation
+    AdjMem m;
+    auto plan = [&](AdjMem& mm, bool real) {
+        struct Ptrs {
+            char *ckf, *cks, *ckp, *segf, *segs, *segp, *finf, *fins, *finp;
+            float *lam_a, *lam_g, *lam_b, *lam_F;
+            double *lp_a, *lp_b, *lfm, *lsh, *lmg, *lwall, *mgeo;
+            int* mpart;
+        } q;
+        q.ckf = mm.take<char>(nck * popb);
+        q.cks = mm.take<char>(nck * partb);
+        q.ckp = mm.take<char>(nck * poseb);
+        q.segf = mm.take<char>(K * popb);
+        q.segs = mm.take<char>((K + 1) * partb);
+        q.segp = mm.take<char>((K + 1) * poseb);
+        q.finf = mm.take<char>(popb);
+        q.fins = mm.take<char>(partb);
+        q.finp = mm.take<char>(poseb);
+        q.lam_a = mm.take<float>(2 * ctx->pop_elems);
+        q.lam_g = mm.take<float>(2 * ctx->pop_elems);
+        q.lam_b = mm.take<float>(2 * ctx->pop_elems);
+        q.lam_F = mm.take<float>(4 * ctx->flb_elems);
+        q.lp_a = mm.take<double>((size_t)np * 2 * ADJ_LP);
+        q.lp_b = mm.take<double>((size_t)np * 2 * ADJ_LP);
+        q.lfm = mm.take<double>((size_t)np * 2 * 3);
+        q.lsh = mm.take<double>((size_t)np * 2 * ADJ_LS);
+        q.lmg = mm.take<double>((size_t)nm * 2 * ADJ_LG);
+        q.lwall = mm.take<double>((size_t)ni * 2 * 8);
+        q.mgeo = mm.take<double>((size_t)nm * 5);
+        q.mpart = mm.take<int>(nm);
+        (void)real;
+        return q;
+    };
+    plan(m, false);
+    const size_t total = m.o;
+    m.o = 0;
+    if (cudaMalloc(&m.base, total) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, LBM_ENOMEM, "the adjoint's checkpoints and buffers do not fit on the device");
+    }
+    struct Free {
+        char* p;
+        ~Free() { cudaFree(p); }
+    } guard{m.base};
+    auto q = plan(m, true);
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemsetAsync(m.base, 0, total, st));
+    CK(cudaMemcpyAsync(q.mgeo, ctx->hgeo.data(), ctx->hgeo.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(q.mpart, ctx->hmpart.data(), ctx->hmpart.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    auto save = [&](char* f, char* sp, char* pp) -> lbm_status {
+        CK(cudaMemcpyAsync(f, ctx->f[ctx->cur], popb, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(sp, state(ctx, ctx->cur), partb, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(pp, pose(ctx, ctx->cur), poseb, cudaMemcpyDeviceToDevice, st));
+        return LBM_OK;
+    };
+    auto load = [&](const char* f, const char* sp, const char* pp) -> lbm_status {
+        ctx->cur = 0;
+        CK(cudaMemcpyAsync(ctx->f[0], f, popb, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(state(ctx, 0), sp, partb, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(pose(ctx, 0), pp, poseb, cudaMemcpyDeviceToDevice, st));
+        return LBM_OK;
+    };
+    lbm_status s = LBM_OK;
+    // forward, with a checkpoint every K steps
+    for (int c = 0; c < nck; ++c) {
+        if ((s = save(q.ckf + c * popb, q.cks + c * partb, q.ckp + c * poseb)) != LBM_OK) return s;
+        if ((s = lbm_step(ctx, std::min(K, nsteps - c * K))) != LBM_OK) return s;
+    }
+    const int fin_cur = ctx->cur;
+    const int64_t fin_steps = ctx->steps;
+    if ((s = save(q.finf, q.fins, q.finp)) != LBM_OK) return s;
+    // the outputs' seeds: lambda of y_c (output 0) and of the omega sum (output 1)
+    std::vector<double> lp0((size_t)np * 2 * ADJ_LP, 0.0);
+    for (int p = 0; p < np; ++p) {
+        lp0[((size_t)p * 2 + 0) * ADJ_LP + 1] = seed[2 * p];           // LY0
+        lp0[((size_t)p * 2 + 1) * ADJ_LP + ADJ_LP - 1] = seed[2 * p + 1];  // LWS
+    }
+    CK(cudaMemcpyAsync(q.lp_a, lp0.data(), lp0.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    float *lam_in = q.lam_a, *lam_out = q.lam_b;
+    double *lp_new = q.lp_a, *lp_old = q.lp_b;
+    AdjArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.flb = static_cast<float*>(ctx->flb);
+    a.flags = ctx->flags;
+    a.insts = ctx->insts;
+    a.mgeo = q.mgeo;
+    a.marker_particle = q.mpart;
+    a.ptab = ctx->ptab;
+    a.np = np;
+    a.nmark = nm;
+    a.weight = ctx->cfg.weight;
+    a.pop_elems = ctx->pop_elems;
+    a.flb_elems = ctx->flb_elems;
+    a.lam_g = q.lam_g;
+    a.lam_F = q.lam_F;
+    a.lamFM = q.lfm;
+    a.lam_shape = q.lsh;
+    a.lam_mgeo = q.lmg;
+    a.lam_wall = q.lwall;
+    a.err = ctx->err;
+    for (int c = nck - 1; c >= 0; --c) {
+        const int n0 = c * K, mseg = std::min(K, nsteps - n0);
+        if ((s = load(q.ckf + c * popb, q.cks + c * partb, q.ckp + c * poseb)) != LBM_OK) return s;
+        for (int j = 0; j < mseg; ++j) {  // recompute the segment, keeping every level
+            if ((s = save(q.segf + j * popb, q.segs + j * partb, q.segp + j * poseb)) != LBM_OK) return s;
+            if ((s = enqueue_step(ctx, st, ctx->cur, n0 + j, nullptr)) != LBM_OK) return s;
+            ctx->cur ^= 1;
+        }
+        // the bodies of level n0 + mseg (the last step's P(n+1))
+        CK(cudaMemcpyAsync(q.segs + mseg * partb, state(ctx, ctx->cur), partb, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(q.segp + mseg * poseb, pose(ctx, ctx->cur), poseb, cudaMemcpyDeviceToDevice, st));
+        for (int j = mseg - 1; j >= 0; --j) {
+            // level n = n0 + j: its f* and bodies in buffer 0; the step's IB
+            // kernels leave f_lb(n), its flags and P(n+1) in buffer 1
+            if ((s = load(q.segf + j * popb, q.segs + j * partb, q.segp + j * poseb)) != LBM_OK) return s;
+            if ((s = enqueue_step_part(ctx, st, 0, n0 + j, true)) != LBM_OK) return s;
+            a.f = static_cast<const float*>(ctx->f[0]);
+            a.Pn = reinterpret_cast<const DParticle*>(state(ctx, 0));
+            a.Pn1 = reinterpret_cast<const DParticle*>(state(ctx, 1));
+            a.lam_in = lam_in;
+            a.lam_out = lam_out;
+            a.lamP_new = lp_new;
+            a.lamP_old = lp_old;
+            CK(launch_adjoint_step(a, ctx->hinst, st));
+            std::swap(lam_in, lam_out);
+            std::swap(lp_new, lp_old);
+            CK(cudaMemsetAsync(lp_old, 0, (size_t)np * 2 * ADJ_LP * sizeof(double), st));
+        }
+    }
+    // lambda(f*(0)) is lam_in, lambda(P(0)) is lp_new: the initial field's share
+    a.lam_in = lam_in;
+    std::vector<int> couette(ni);
+    for (int i = 0; i < ni; ++i) couette[i] = ctx->icfg[i].init == LBM_INIT_COUETTE;
+    CK(launch_adjoint_init(a, ctx->hinst, couette, st));
+    std::vector<double> lp((size_t)np * 2 * ADJ_LP), lsh((size_t)np * 2 * ADJ_LS), lmg((size_t)nm * 2 * ADJ_LG),
+        lw((size_t)ni * 2 * 8);
+    CK(cudaMemcpyAsync(lp.data(), lp_new, lp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(lsh.data(), q.lsh, lsh.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(lmg.data(), q.lmg, lmg.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(lw.data(), q.lwall, lw.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // back to the forward run's final state
+    ctx->cur = fin_cur;
+    CK(cudaMemcpyAsync(ctx->f[fin_cur], q.finf, popb, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(state(ctx, fin_cur), q.fins, partb, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(pose(ctx, fin_cur), q.finp, poseb, cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->steps = fin_steps;
+    drop_graphs(ctx);
+    if ((s = device_error(ctx)) != LBM_OK) return s;
+    // the particles' inputs: the pose from both stored levels, the shape
+    // through its markers and mass properties (dual numbers over the two
+    // dimensions), the density through the mass properties
+    for (int p = 0; p < np; ++p) {
+        const lbm_particle_desc& d = ctx->hdesc[p];
+        const int m0 = ctx->hpart[p].x, n = ctx->hpart[p].y;
+        std::vector<TD> rb(2 * n + 2), nb(2 * n + 2), S(n + 1);
+        TD dim[2] = {TD(d.dim[0]), TD(d.dim[1])};
+        dim[0].d[0] = 1.0;
+        dim[1].d[1] = 1.0;
+        ShapeOutT<TD> so;
+        if (make_shape_t<TD>(d, dim, ctx->icfg[ctx->hpart[p].z].marker_spacing, rb.data(), nb.data(), S.data(), n,
+                             &so) != n)
+            return fail(ctx, LBM_EINTERNAL, "adjoint: the particle's markers could not be rebuilt");
+        const double area = value_of(so.area), ipm = value_of(so.inertia_per_mass), rs = d.rho_s;
+        const double mass = rs * area, inertia = mass * ipm;
+        for (int o = 0; o < 2; ++o) {
+            const double* l = lp.data() + ((size_t)p * 2 + o) * ADJ_LP;
+            const double* sh = lsh.data() + ((size_t)p * 2 + o) * ADJ_LS;
+            double ldim[2] = {0.0, 0.0};
+            for (int k = 0; k < n; ++k) {
+                const double* g = lmg.data() + ((size_t)(m0 + k) * 2 + o) * ADJ_LG;
+                for (int j = 0; j < 2; ++j)
+                    ldim[j] += g[0] * rb[2 * k].d[j] + g[1] * rb[2 * k + 1].d[j] + g[2] * nb[2 * k].d[j] +
+                               g[3] * nb[2 * k + 1].d[j] + g[4] * S[k].d[j];
+            }
+            // 1/m, 1/I -> m, I -> area, inertia per mass, rho_s
+            const double lI = -sh[1] / (inertia * inertia);
+            const double lm = -sh[0] / (mass * mass) + lI * ipm;
+            const double lipm = lI * mass;
+            const double larea = sh[2] + lm * rs, lrho = sh[3] + lm * area;
+            for (int j = 0; j < 2; ++j) ldim[j] += larea * so.area.d[j] + lipm * so.inertia_per_mass.d[j];
+            double* out = dpart + ((size_t)p * 2 + o) * 6;
+            out[0] = ldim[0];
+            out[1] = ldim[1];
+            out[2] = l[0] + l[6];   // xc: both stored levels
+            out[3] = l[1] + l[7];   // yc
+            out[4] = l[2] + l[8];   // theta
+            out[5] = lrho;
+        }
+    }
+    for (size_t k = 0; k < lw.size(); ++k) dwall[k] = lw[k];
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_adjoint(lbm_ctx* ctx, int32_t nsteps, int32_t checkpoint_every, const double* seed,
+                                  double* dparticle, double* dwall) {
+    if (!ctx || !seed || !dparticle || !dwall || nsteps < 1 || checkpoint_every < 1) return LBM_EINVAL;
+    if (ctx->prec != LBM_FP32) return fail(ctx, LBM_EINVAL, "the adjoint runs on LBM_FP32 contexts");
+    if (ctx->steps != 0) return fail(ctx, LBM_EINVAL, "the adjoint starts from a context with no steps done");
+    if (ctx->np < 1) return fail(ctx, LBM_EINVAL, "the adjoint needs a particle");
+    if (ctx->step_mode != LBM_STEP_SEPARATE) return fail(ctx, LBM_EINVAL, "the adjoint needs the separate step mode");
+    for (const Inst& I : ctx->hinst)
+        if (!I.G.px) return fail(ctx, LBM_EINVAL, "the adjoint needs periodic x sides (no x walls)");
+    return adjoint_run(ctx, nsteps, checkpoint_every, seed, dparticle, dwall);
+}
 
 // ---------------------------------------------------------------------------
 // lbm_step_static: the step with the immersed-boundary scratch in a static

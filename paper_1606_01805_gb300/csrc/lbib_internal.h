@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -217,6 +218,36 @@ struct FusedArgs {
     int stall, stall_ticket;  // test hook: that fluid item waits for one spreading tile too many
 };
 
+// The reverse (adjoint) step of FP32 contexts, two outputs at once
+// (adjoint.cu).  Adjoint buffers of populations have the layout of a
+// population buffer (FP32), one per output, pop_elems apart; lam_F holds
+// the force adjoint of flagged cells, [output][component] blocks of
+// flb_elems, indexed like the force field.
+struct AdjArgs {
+    const float* f;            // f*(n) (stored shifted populations of level n)
+    float* flb;                // the step's force field (recomputed), cleared at the end
+    uint8_t* flags;            // its flags, cleared at the end
+    const Inst* insts;
+    const DParticle* Pn;       // P(n)
+    const DParticle* Pn1;      // P(n+1) (recomputed)
+    const double* mgeo;        // per marker: body-frame position (2), normal (2), arc length (FP64)
+    const int* marker_particle;
+    const int4* ptab;          // per particle: (first marker, markers, instance, -)
+    int np, nmark, weight;
+    long long pop_elems, flb_elems;
+    const float* lam_in;       // lambda(f*(n+1)) per output
+    float* lam_g;              // lambda of the streamed populations of level n
+    float* lam_out;            // lambda(f*(n))
+    float* lam_F;
+    double* lamP_new;          // per particle and output: lambda(P(n+1)) (see adjoint.cu)
+    double* lamP_old;          // lambda(P(n)), accumulated
+    double* lamFM;             // per particle and output: lambda of F_x, F_y, M
+    double* lam_shape;         // per particle and output: lambda of 1/m, 1/I, area, rho_s
+    double* lam_mgeo;          // per marker and output: lambda of rb (2), nb (2), S
+    double* lam_wall;          // per instance and output: lambda of wall_u[4][2]
+    unsigned* err;
+};
+
 struct FieldArgs {
     const void* f;            // population buffer
     Inst I;
@@ -263,6 +294,12 @@ cudaError_t launch_get_pops(int prec, const void* fbuf, const Inst& I, int y0, i
 cudaError_t launch_step_fused(int prec, const FusedArgs& f, int sms, cudaStream_t s);
 int fused_spread_rows();
 int fused_fluid_variant();
+// the reverse step (adjoint.cu): the kernels of one step in order, and the
+// initial Couette profile's share of the wall-speed adjoint (instances
+// whose init_couette entry is nonzero)
+cudaError_t launch_adjoint_step(const AdjArgs& a, const std::vector<Inst>& insts, cudaStream_t s);
+cudaError_t launch_adjoint_init(const AdjArgs& a, const std::vector<Inst>& insts, const std::vector<int>& init_couette,
+                                cudaStream_t s);
 // OR `bits` into the device error word, as a kernel that detects an error does
 cudaError_t launch_raise(unsigned* err, unsigned bits, cudaStream_t s);
 cudaError_t launch_probes(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s);

@@ -35,7 +35,7 @@ LBM_W_EXP, LBM_W_CUBIC, LBM_W_QUARTIC, LBM_W_COSINE, LBM_W_POLY = range(5)
 # every symbol include/lbib.h declares
 EXPORTS = ["lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "lbm_step_timed",
            "lbm_sync", "lbm_inject_status", "lbm_inject_stall", "lbm_tile_info", "lbm_set_step_mode",
-           "lbm_get_step_mode", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
+           "lbm_get_step_mode", "lbm_adjoint", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
            "lbm_get_particles", "lbm_steps_done", "lbm_last_error", "lbm_destroy",
            "lbm_step_static", "lbm_batch_workspace_bytes", "lbm_init_batch", "lbm_instances",
            "lbm_add_particle_to", "lbm_get_instance_fields", "lbm_get_instance_populations",
@@ -103,6 +103,7 @@ def load(path: os.PathLike | str | None = None):
     L.lbm_inject_stall.argtypes = [C.c_void_p, C.c_int64]
     L.lbm_tile_info.argtypes = [C.c_int32, C.c_int32] + [C.POINTER(C.c_int32)] * 3
     L.lbm_set_step_mode.argtypes = [C.c_void_p, C.c_int32]
+    L.lbm_adjoint.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _dp, _dp, _dp]
     L.lbm_get_step_mode.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
     L.lbm_get_fields.argtypes = [C.c_void_p, _dp, _dp, _dp]
     L.lbm_get_populations.argtypes = [C.c_void_p, _dp]
@@ -134,7 +135,7 @@ def load(path: os.PathLike | str | None = None):
     L.lbm_get_field_tangents.argtypes = [C.c_void_p, C.c_int32, _dp, _dp, _dp]
     for fn in ("lbm_workspace_bytes", "lbm_init", "lbm_add_particle", "lbm_step", "lbm_step_timed",
                "lbm_sync", "lbm_inject_status", "lbm_inject_stall", "lbm_tile_info", "lbm_set_step_mode",
-               "lbm_get_step_mode", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
+               "lbm_get_step_mode", "lbm_adjoint", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
                "lbm_get_particles", "lbm_step_static", "lbm_batch_workspace_bytes",
                "lbm_init_batch", "lbm_add_particle_to", "lbm_get_instance_fields",
                "lbm_get_instance_populations", "lbm_set_instance_populations", "lbm_get_tile",
@@ -298,6 +299,19 @@ class Simulation:
     def _shape(self, instance):
         return (self.ny, self.nx)
 
+    def adjoint(self, nsteps, checkpoint_every, seed):
+        """Reverse-mode gradients (lbm_adjoint): runs nsteps forward, then
+        back; seed [np][2] weights the particles' final y and omega sum in
+        the two outputs.  Returns (dparticle [np][2][6] over (dim0, dim1,
+        xc, yc, theta, rho_s), dwall [instances][2][8] over wall_u[4][2])."""
+        n = max(self.np, 1)
+        seed = np.ascontiguousarray(seed, np.float64).reshape(n, 2)
+        dp = np.zeros((n, 2, 6))
+        dw = np.zeros((len(self) if isinstance(self, Batch) else 1, 2, 8))
+        self._check(load().lbm_adjoint(self._h, nsteps, checkpoint_every, _ptr(seed), _ptr(dp), _ptr(dw)),
+                    "lbm_adjoint")
+        return dp, dw
+
 
 class Batch:
     """Many independent lattices advanced together (lbm_init_batch).
@@ -355,6 +369,7 @@ class Batch:
         return load().lbm_instances(self._h)
 
     particle_tangents = Simulation.particle_tangents
+    adjoint = Simulation.adjoint
     set_wall_tangents = Simulation.set_wall_tangents
     field_tangents = Simulation.field_tangents
 
