@@ -62,6 +62,38 @@ def ncu_traffic(workload, prec, variant):
     return None
 
 
+def record_traffic(csv_path, workload, prec, variant, source):
+    """Add (or replace) the traffic record of the fluid kernel for this
+    workload, precision and tile variant from an ncu CSV log of
+    dram__bytes_read.sum and dram__bytes_write.sum (per launch, averaged over
+    the captured launches), keyed by the current kernel sources."""
+    import csv
+
+    rows = list(csv.reader(Path(csv_path).read_text().splitlines()))
+    hdr = next(r for r in rows if "Metric Name" in r)
+    ki, mi, vi = hdr.index("Kernel Name"), hdr.index("Metric Name"), hdr.index("Metric Value")
+    sums, counts = {}, {}
+    for r in rows[rows.index(hdr) + 1:]:
+        if len(r) != len(hdr) or "k_fluid" not in r[ki]:
+            continue
+        v = float(r[vi].replace(",", ""))
+        sums[r[mi]] = sums.get(r[mi], 0.0) + v
+        counts[r[mi]] = counts.get(r[mi], 0) + 1
+    rd = sums["dram__bytes_read.sum"] / counts["dram__bytes_read.sum"]
+    wr = sums["dram__bytes_write.sum"] / counts["dram__bytes_write.sum"]
+    try:
+        recs = json.loads(TRAFFIC_FILE.read_text())
+    except (OSError, ValueError):
+        recs = []
+    key = (kernel_hash(), workload, prec, variant)
+    recs = [r for r in recs if (r.get("kernel_hash"), r.get("workload"), r.get("precision"), r.get("tile")) != key]
+    recs.append({"kernel_hash": key[0], "workload": workload, "precision": prec, "tile": variant,
+                 "dram_read_bytes": rd, "dram_write_bytes": wr, "launches": counts["dram__bytes_read.sum"],
+                 "source": source})
+    TRAFFIC_FILE.write_text(json.dumps(recs, indent=1) + "\n")
+    return recs[-1]
+
+
 def kernel_hash():
     """hash of the sources that define the direct fluid kernels"""
     h = hashlib.sha256()
@@ -462,10 +494,21 @@ def main():
                     help="force this fluid tile variant (lbm_set_tile) instead of the tuned one")
     ap.add_argument("--instances", type=int, default=512,
                     help="screening workload: first N lattices of the batch (profiling subsets)")
+    ap.add_argument("--record-traffic", metavar="CSV", default=None,
+                    help="record the fluid kernel's DRAM traffic from this ncu CSV log for --workload, "
+                         "--precision and --tile, then exit")
     args = ap.parse_args()
     prec = {"fp64": 0, "fp32": 1, "fp16s": 2}[args.precision]
     ws, rank, local = dist_env()
     wl = make_workload(args.workload, steps=20000)
+    if args.record_traffic:
+        assert wl is not None and args.tile is not None, "--record-traffic needs a lattice workload and --tile"
+        cmd = (f"ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+               f"--clock-control none -k regex:k_fluid_one -s 3 -c 3 --csv python bench.py --workload "
+               f"{args.workload} --precision {args.precision} --tile {args.tile} --steps 3 --warmup 3 "
+               f"--no-side --no-cpu --no-batched")
+        print(json.dumps(record_traffic(args.record_traffic, wl.name, prec, args.tile, cmd)))
+        return
     if wl is None:
         return main_screening(args)
 

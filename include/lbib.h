@@ -323,12 +323,14 @@ lbm_status lbm_get_instance_populations(lbm_ctx* ctx, int32_t instance, double* 
 lbm_status lbm_set_instance_populations(lbm_ctx* ctx, int32_t instance, const double* f);
 
 /*
- * Tile variant of the fused fluid kernel.  lbm_init / lbm_init_batch time
- * every variant the precision has on the context's own lattices and keep
- * the fastest (all variants give bit-identical results); lbm_get_tile
- * reports the choice (index, cells per thread, rows per tile) and
- * lbm_set_tile forces variant `variant` (LBM_EINVAL for an index out of
- * 0 .. LBM_TILE_VARIANTS - 1 or one the precision does not have).
+ * Tile variant of the fused fluid kernel.  The first step of a context
+ * (lbm_step or lbm_step_timed) runs its immersed-boundary kernels once, times
+ * every variant the precision has on the context's own lattices with those
+ * forces and keeps the fastest (all variants give bit-identical results);
+ * lbm_get_tile reports the choice (index, cells per thread, rows per tile)
+ * and lbm_set_tile forces variant `variant` and skips the timing
+ * (LBM_EINVAL for an index out of 0 .. LBM_TILE_VARIANTS - 1 or one the
+ * precision does not have).
  * lbm_tile_info describes any variant: cells per thread (the tile is 32
  * times as wide), rows per tile, and the stages of a staged variant (0 for
  * a direct one), and whether `precision` has it (returns LBM_OK) or not
@@ -352,21 +354,33 @@ lbm_status lbm_set_tile(lbm_ctx* ctx, int32_t variant);
  * Step mode of a batch.  LBM_STEP_SEPARATE (the default): each step is the
  * immersed-boundary kernels (probes and rigid update, markers, spreading)
  * and then the fluid kernel, each one launch over all instances.
+ * LBM_STEP_OVERLAP: the instances are split into two halves of about equal
+ * cell count, and lbm_step's captured runs of steps advance each half with
+ * its own chain of the same kernels on a stream of its own, the
+ * immersed-boundary kernels at the device's most urgent scheduling
+ * priority: the particle work of one half runs beside the fluid kernel of
+ * the other, step after step.  Steps launched one by one (lbm_step_timed,
+ * the remainder of a run that is not a multiple of 32 steps) run both
+ * halves as in LBM_STEP_SEPARATE.  The split needs the particles numbered
+ * in instance order across it; otherwise the mode runs as
+ * LBM_STEP_SEPARATE.  It needs a batch of two or more instances (else
+ * LBM_EINVAL).
  * LBM_STEP_FUSED: each step is one persistent launch whose CTAs take the
  * step's work items in a fixed order -- probe blocks, marker blocks,
  * spreading tiles and fluid tiles of every instance, the stages of one
  * instance a few instances apart, so that the particle work of some
  * instances runs beside the fluid work of others.  Within an instance an
  * item waits (bounded; LBM_ETIMEOUT on expiry) for the items it needs.
- * Both modes give the same results, bit for bit.  The fused mode needs a
- * batch of two or more instances (lbm_init_batch) in LBM_FP64, LBM_FP32 or
- * LBM_FP16_SHIFTED (else LBM_EINVAL); it uses its own fluid tile (2 cells
- * per thread, 8 rows: lbm_get_tile reports variant 3) and lbm_step_timed
- * then reports the fused launch as the fluid time.  Set it before or
+ * The fused mode needs a batch of two or more instances (lbm_init_batch) in
+ * LBM_FP64, LBM_FP32 or LBM_FP16_SHIFTED (else LBM_EINVAL); it uses its own
+ * fluid tile (4 cells per thread, 8 rows: lbm_get_tile reports variant 0)
+ * and lbm_step_timed then reports the fused launch as the fluid time.
+ * All modes give the same results, bit for bit.  Set the mode before or
  * between steps.
  */
 #define LBM_STEP_SEPARATE 0
 #define LBM_STEP_FUSED 1
+#define LBM_STEP_OVERLAP 2
 lbm_status lbm_set_step_mode(lbm_ctx* ctx, int32_t mode);
 lbm_status lbm_get_step_mode(const lbm_ctx* ctx, int32_t* mode);
 
@@ -439,7 +453,7 @@ lbm_status lbm_get_field_tangents(lbm_ctx* ctx, int32_t instance, double* drho, 
  * In a batch whose instances hold one particle each, J_o of instance i is
  * the output of its particle, so its rows are that particle's gradients.
  * Requirements (else LBM_EINVAL): LBM_FP32, no step done yet, at least one
- * particle, periodic x sides, the separate step mode; a marker or probe
+ * particle, periodic x sides, not the fused step mode; a marker or probe
  * support must stay off the wall rows (else LBM_EDOMAIN).  The call
  * allocates its own device memory (checkpoints, one segment of steps, the
  * adjoint buffers; LBM_ENOMEM if it does not fit) and frees it before it

@@ -86,6 +86,16 @@ struct lbm_ctx {
     bool items_dirty = true;
     unsigned* counters = nullptr;
     size_t counter_words = 0;       // per set
+    // overlapped step of a batch (LBM_STEP_OVERLAP): two halves of the
+    // instances, each a range of the marker blocks, the particles and every
+    // variant's task list; empty when the batch cannot be split that way
+    struct Half {
+        int b0, b1, p0, p1;
+        int t0[N_FLUID_VARIANTS], t1[N_FLUID_VARIANTS];
+    };
+    std::vector<Half> halves;
+    bool halves_dirty = true;
+    int prio_hi = 0;                // the most urgent scheduling priority (the IB kernels')
     std::vector<double> hrc;        // per particle: circumscribed radius
     // for the adjoint: body-frame marker geometry in FP64 (rb, nb, S per
     // marker), each marker's particle, each particle's description
@@ -315,6 +325,7 @@ ParticleArgs particle_args(lbm_ctx* ctx, int cur) {
     pa.boxes = ctx->boxes;
     pa.err = ctx->err;
     pa.weight = ctx->cfg.weight;
+    pa.blk_base = 0;
     pa.single = ctx->ninst == 1;
     pa.one = ctx->hinst[0];
     pa.nblk_inline = ctx->nblk <= INLINE_BLOCKS ? ctx->nblk : 0;
@@ -326,6 +337,7 @@ SpreadArgs spread_args(lbm_ctx* ctx, const ParticleArgs& pa) {
     SpreadArgs sa;
     sa.insts = ctx->insts;
     sa.ptab = ctx->ptab;
+    sa.p_base = 0;
     sa.recs = pa.recs;
     sa.boxes = pa.boxes;
     sa.flb = ctx->flb;
@@ -362,15 +374,16 @@ bool watched(const lbm_ctx* ctx, int64_t step) { return (step + 1) % ctx->check_
 // stall: the test hook of lbm_inject_stall; keep: leave the forces and
 // their flags in place (the autotuner's repeated launches of one step)
 lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v, bool pdl = false,
-                             bool check = false, bool stall = false, bool keep = false) {
+                             bool check = false, bool stall = false, bool keep = false, int t0 = 0,
+                             int tn = -1) {
     FluidArgs fa;
     fa.fin = ctx->f[cur];
     fa.fout = ctx->f[cur ^ 1];
     fa.flb = ctx->flb;
     fa.flags = ctx->flags;
     fa.insts = ctx->insts;
-    fa.tasks = ctx->tasks[v];
-    fa.ntasks = ctx->ntasks[v];
+    fa.tasks = ctx->tasks[v] + t0;  // tasks t0 .. t0 + tn - 1 (all by default)
+    fa.ntasks = tn < 0 ? ctx->ntasks[v] : tn;
     fa.err = ctx->err;
     fa.check = check ? 1 : 0;
     fa.stall = stall ? 1 : 0;
@@ -474,6 +487,74 @@ lbm_status launch_fused_step(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t ste
 
 bool fused(const lbm_ctx* ctx) { return ctx->step_mode == LBM_STEP_FUSED; }
 
+// The overlapped step's halves: the instances split where the first half's
+// cells reach half the total, if that boundary also splits the particles
+// and the marker blocks (particles numbered in instance order).
+void plan_halves(lbm_ctx* ctx) {
+    ctx->halves.clear();
+    ctx->halves_dirty = false;
+    const int n = ctx->ninst;
+    if (n < 2) return;
+    long long tot = 0;
+    for (const Inst& I : ctx->hinst) tot += (long long)I.G.nx * I.G.ny;
+    int k = 1;
+    long long acc = (long long)ctx->hinst[0].G.nx * ctx->hinst[0].G.ny;
+    while (k < n - 1 && 2 * acc < tot) {
+        acc += (long long)ctx->hinst[k].G.nx * ctx->hinst[k].G.ny;
+        ++k;
+    }
+    // the first particle / block / task of instance k or later; every one
+    // after it must belong to the second half too
+    auto split = [k](int count, auto inst_of) {
+        int first = count;
+        for (int i = 0; i < count; ++i)
+            if (inst_of(i) >= k) {
+                first = i;
+                break;
+            }
+        for (int i = first; i < count; ++i)
+            if (inst_of(i) < k) return -1;
+        return first;
+    };
+    const int ps = split(ctx->np, [&](int p) { return ctx->hpart[p].z; });
+    const int bs = split(ctx->nblk, [&](int b) { return ctx->hblk[b].w; });
+    if (ps < 0 || bs < 0) return;
+    lbm_ctx::Half h0{0, bs, 0, ps, {}, {}}, h1{bs, ctx->nblk, ps, ctx->np, {}, {}};
+    for (int v = 0; v < N_FLUID_VARIANTS; ++v) {
+        const std::vector<Task> t = make_tasks(ctx->hinst, v);
+        const int ts = split((int)t.size(), [&](int i) { return t[i].inst; });
+        if (ts < 0) return;
+        h0.t0[v] = 0;
+        h0.t1[v] = ts;
+        h1.t0[v] = ts;
+        h1.t1[v] = (int)t.size();
+    }
+    ctx->halves = {h0, h1};
+}
+
+bool overlapped(const lbm_ctx* ctx) { return ctx->step_mode == LBM_STEP_OVERLAP && ctx->halves.size() == 2; }
+
+// time step number `step` of one half of the instances from buffer `cur`
+// on stream `st`: its IB kernels (at the context's most urgent priority, so
+// that their CTAs go ahead of the other half's fluid CTAs), then its fluid
+// tasks
+lbm_status enqueue_half(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t step, const lbm_ctx::Half& h) {
+    const bool ib = h.p1 > h.p0;
+    if (ib) {
+        LaunchPriority urgent(ctx->prio_hi);
+        ParticleArgs pa = particle_args(ctx, cur);
+        pa.blk_base = h.b0;
+        CK(launch_probes(ctx->prec, pa, h.b1 - h.b0, st));
+        CK(launch_markers(ctx->prec, pa, h.b1 - h.b0, st));
+        SpreadArgs sa = spread_args(ctx, pa);
+        sa.p_base = h.p0;
+        CK(launch_spread(ctx->prec, sa, h.p1 - h.p0, spread_tiles(ctx), st));
+    }
+    const int v = ctx->variant;
+    if (h.t1[v] <= h.t0[v]) return LBM_OK;
+    return launch_fluid_step(ctx, st, cur, v, ib, watched(ctx, step), false, false, h.t0[v], h.t1[v] - h.t0[v]);
+}
+
 // Part of time step number `step` (steps done before it) from buffer `cur`
 // on stream `st`: the immersed-boundary kernels (ib = true: probes / rigid
 // update / markers, spreading) or the fused fluid kernel over every
@@ -512,17 +593,46 @@ bool capture_graph(lbm_ctx* ctx, int cur, int64_t step) {
     cudaGraphExec_t& ge = ctx->graph[cur][step % ctx->check_every];
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return false;
+    // the overlapped step: the second half on a stream of its own, forked
+    // from the capture and joined back at its end
+    cudaStream_t cs2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    const bool two = overlapped(ctx);
+    if (two && (cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess)) {
+        if (cs2) cudaStreamDestroy(cs2);
+        if (fork) cudaEventDestroy(fork);
+        cudaStreamDestroy(cs);
+        cudaGetLastError();
+        return false;
+    }
     bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
         int c = cur;
-        for (int k = 0; k < GRAPH_STEPS && ok; ++k, c ^= 1)
-            ok = enqueue_step(ctx, cs, c, step + k, nullptr) == LBM_OK;
+        if (two) {
+            ok = cudaEventRecord(fork, cs) == cudaSuccess && cudaStreamWaitEvent(cs2, fork, 0) == cudaSuccess;
+            for (int k = 0; k < GRAPH_STEPS && ok; ++k, c ^= 1)
+                ok = enqueue_half(ctx, cs, c, step + k, ctx->halves[0]) == LBM_OK &&
+                     enqueue_half(ctx, cs2, c, step + k, ctx->halves[1]) == LBM_OK;
+            // the join, whatever happened, so that the capture can end
+            const bool joined = cudaEventRecord(join, cs2) == cudaSuccess && cudaStreamWaitEvent(cs, join, 0) == cudaSuccess;
+            ok = ok && joined;
+        } else {
+            for (int k = 0; k < GRAPH_STEPS && ok; ++k, c ^= 1)
+                ok = enqueue_step(ctx, cs, c, step + k, nullptr) == LBM_OK;
+        }
         cudaGraph_t g = nullptr;
         const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
         ok = ok && ended && g && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
         if (g) cudaGraphDestroy(g);
     }
     cudaStreamDestroy(cs);
+    if (two) {
+        cudaStreamDestroy(cs2);
+        cudaEventDestroy(fork);
+        cudaEventDestroy(join);
+    }
     cudaGetLastError();  // a failed capture leaves no sticky error
     if (!ok) ge = nullptr;
     return ok;
@@ -861,6 +971,7 @@ lbm_status add_particle_t(lbm_ctx* ctx, int inst, const lbm_particle_desc* d, co
     }
     ctx->hblk.insert(ctx->hblk.end(), blocks.begin(), blocks.end());
     ctx->hpart.push_back(make_int4(P.m0, n, inst, box_tiles(so.rcirc)));
+    ctx->halves_dirty = true;
     CK(cudaMemcpyAsync(ctx->ptab + ctx->np, &ctx->hpart.back(), sizeof(int4), cudaMemcpyHostToDevice,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1066,6 +1177,10 @@ lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps) {
         lbm_status s = build_items(ctx);
         if (s != LBM_OK) return s;
     }
+    if (ctx->step_mode == LBM_STEP_OVERLAP && ctx->halves_dirty) {  // before any capture
+        drop_graphs(ctx);
+        plan_halves(ctx);
+    }
     if (!ctx->tuned && nsteps > 0) {  // the first step picks the tile variant
         bool stepped = false;
         lbm_status s = tune_step(ctx, &stepped);
@@ -1254,7 +1369,10 @@ lbm_status lbm_set_tile(lbm_ctx* ctx, int32_t variant) {
 
 lbm_status lbm_set_step_mode(lbm_ctx* ctx, int32_t mode) {
     if (!ctx) return LBM_EINVAL;
-    if (mode != LBM_STEP_SEPARATE && mode != LBM_STEP_FUSED) return fail(ctx, LBM_EINVAL, "no such step mode");
+    if (mode != LBM_STEP_SEPARATE && mode != LBM_STEP_FUSED && mode != LBM_STEP_OVERLAP)
+        return fail(ctx, LBM_EINVAL, "no such step mode");
+    if (mode == LBM_STEP_OVERLAP && ctx->ninst < 2)
+        return fail(ctx, LBM_EINVAL, "the overlapped step is for batches of two or more instances");
     if (mode == LBM_STEP_FUSED && ctx->prec == LBM_FP32_TANGENT)
         return fail(ctx, LBM_EINVAL, "the fused step has no tangent mode");
     if (mode == LBM_STEP_FUSED && ctx->items_cap == 0)
@@ -1262,6 +1380,12 @@ lbm_status lbm_set_step_mode(lbm_ctx* ctx, int32_t mode) {
     if (mode == ctx->step_mode) return LBM_OK;
     drop_graphs(ctx);
     ctx->step_mode = mode;
+    if (mode == LBM_STEP_OVERLAP) {
+        ctx->halves_dirty = true;
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        ctx->prio_hi = greatest;
+    }
     if (mode == LBM_STEP_FUSED) {
         ctx->items_dirty = true;
         ctx->variant = fused_fluid_variant();
@@ -1319,12 +1443,23 @@ lbm_status adjoint_run(lbm_ctx* ctx, int nsteps, int K, const double* seed, doub
     const int nck = (nsteps + K - 1) / K;
     // sizes first (a null base), then one allocation
     AdjMem m;
-    auto plan = [&](AdjMem& mm, bool real) {
+    // the cell kernels' blocks over all instances
+    std::vector<int4> cblk;
+    const int ab = adjoint_block_rows();
+    for (int i = 0; i < ni; ++i) {
+        const Geo& G = ctx->hinst[i].G;
+        const int fl = ctx->icfg[i].init == LBM_INIT_COUETTE ? 1 : 0;
+        for (int by = 0; by < (G.ny + ab - 1) / ab; ++by)
+            for (int bx = 0; bx < (G.nx + 31) / 32; ++bx) cblk.push_back(make_int4(i, bx, by, fl));
+    }
+    auto plan = [&](AdjMem& mm) {
         struct Ptrs {
             char *ckf, *cks, *ckp, *segf, *segs, *segp, *finf, *fins, *finp;
-            float *lam_a, *lam_g, *lam_b, *lam_F;
+            float *lam_a, *lam_b, *lam_F;
             double *lp_a, *lp_b, *lfm, *lsh, *lmg, *lwall, *mgeo;
             int* mpart;
+            float* zh;
+            int4* cblk;
         } q;
         q.ckf = mm.take<char>(nck * popb);
         q.cks = mm.take<char>(nck * partb);
@@ -1336,7 +1471,6 @@ lbm_status adjoint_run(lbm_ctx* ctx, int nsteps, int K, const double* seed, doub
         q.fins = mm.take<char>(partb);
         q.finp = mm.take<char>(poseb);
         q.lam_a = mm.take<float>(2 * ctx->pop_elems);
-        q.lam_g = mm.take<float>(2 * ctx->pop_elems);
         q.lam_b = mm.take<float>(2 * ctx->pop_elems);
         q.lam_F = mm.take<float>(4 * ctx->flb_elems);
         q.lp_a = mm.take<double>((size_t)np * 2 * ADJ_LP);
@@ -1347,10 +1481,11 @@ lbm_status adjoint_run(lbm_ctx* ctx, int nsteps, int K, const double* seed, doub
         q.lwall = mm.take<double>((size_t)ni * 2 * 8);
         q.mgeo = mm.take<double>((size_t)nm * 5);
         q.mpart = mm.take<int>(nm);
-        (void)real;
+        q.zh = mm.take<float>((size_t)ni * 2 * 81);
+        q.cblk = mm.take<int4>(cblk.size());
         return q;
     };
-    plan(m, false);
+    plan(m);
     const size_t total = m.o;
     m.o = 0;
     if (cudaMalloc(&m.base, total) != cudaSuccess) {
@@ -1361,11 +1496,12 @@ lbm_status adjoint_run(lbm_ctx* ctx, int nsteps, int K, const double* seed, doub
         char* p;
         ~Free() { cudaFree(p); }
     } guard{m.base};
-    auto q = plan(m, true);
+    auto q = plan(m);
     cudaStream_t st = ctx->stream;
     CK(cudaMemsetAsync(m.base, 0, total, st));
     CK(cudaMemcpyAsync(q.mgeo, ctx->hgeo.data(), ctx->hgeo.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(q.mpart, ctx->hmpart.data(), ctx->hmpart.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(q.cblk, cblk.data(), cblk.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
     auto save = [&](char* f, char* sp, char* pp) -> lbm_status {
         CK(cudaMemcpyAsync(f, ctx->f[ctx->cur], popb, cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(sp, state(ctx, ctx->cur), partb, cudaMemcpyDeviceToDevice, st));
@@ -1395,7 +1531,9 @@ lbm_status adjoint_run(lbm_ctx* ctx, int nsteps, int K, const double* seed, doub
         lp0[((size_t)p * 2 + 1) * ADJ_LP + ADJ_LP - 1] = seed[2 * p + 1];  // LWS
     }
     CK(cudaMemcpyAsync(q.lp_a, lp0.data(), lp0.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    float *lam_in = q.lam_a, *lam_out = q.lam_b;
+    // lambda(g) of level n + 1 (zero above the last level: the outputs do
+    // not depend on the final populations) and of level n
+    float *lam_gp = q.lam_a, *lam_g = q.lam_b;
     double *lp_new = q.lp_a, *lp_old = q.lp_b;
     AdjArgs a;
     std::memset(&a, 0, sizeof a);
@@ -1410,13 +1548,16 @@ lbm_status adjoint_run(lbm_ctx* ctx, int nsteps, int K, const double* seed, doub
     a.weight = ctx->cfg.weight;
     a.pop_elems = ctx->pop_elems;
     a.flb_elems = ctx->flb_elems;
-    a.lam_g = q.lam_g;
     a.lam_F = q.lam_F;
     a.lamFM = q.lfm;
     a.lam_shape = q.lsh;
     a.lam_mgeo = q.lmg;
     a.lam_wall = q.lwall;
+    a.zh = q.zh;
+    a.cblk = q.cblk;
+    a.ncblk = (int)cblk.size();
     a.err = ctx->err;
+    CK(launch_adjoint_setup(a, ni, st));
     for (int c = nck - 1; c >= 0; --c) {
         const int n0 = c * K, mseg = std::min(K, nsteps - n0);
         if ((s = load(q.ckf + c * popb, q.cks + c * partb, q.ckp + c * poseb)) != LBM_OK) return s;
@@ -1429,28 +1570,34 @@ lbm_status adjoint_run(lbm_ctx* ctx, int nsteps, int K, const double* seed, doub
         CK(cudaMemcpyAsync(q.segs + mseg * partb, state(ctx, ctx->cur), partb, cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(q.segp + mseg * poseb, pose(ctx, ctx->cur), poseb, cudaMemcpyDeviceToDevice, st));
         for (int j = mseg - 1; j >= 0; --j) {
-            // level n = n0 + j: its f* and bodies in buffer 0; the step's IB
-            // kernels leave f_lb(n), its flags and P(n+1) in buffer 1
-            if ((s = load(q.segf + j * popb, q.segs + j * partb, q.segp + j * poseb)) != LBM_OK) return s;
-            if ((s = enqueue_step_part(ctx, st, 0, n0 + j, true)) != LBM_OK) return s;
-            a.f = static_cast<const float*>(ctx->f[0]);
+            // level n = n0 + j: its bodies in buffer 0, its f* read where it
+            // was kept (population buffer 0 points there while the step's IB
+            // kernels are launched); those kernels leave f_lb(n), its flags
+            // and P(n+1) in buffer 1
+            ctx->cur = 0;
+            CK(cudaMemcpyAsync(state(ctx, 0), q.segs + j * partb, partb, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(pose(ctx, 0), q.segp + j * poseb, poseb, cudaMemcpyDeviceToDevice, st));
+            void* const f0 = ctx->f[0];
+            ctx->f[0] = q.segf + j * popb;
+            s = enqueue_step_part(ctx, st, 0, n0 + j, true);
+            ctx->f[0] = f0;
+            if (s != LBM_OK) return s;
+            a.f = reinterpret_cast<const float*>(q.segf + j * popb);
             a.Pn = reinterpret_cast<const DParticle*>(state(ctx, 0));
             a.Pn1 = reinterpret_cast<const DParticle*>(state(ctx, 1));
-            a.lam_in = lam_in;
-            a.lam_out = lam_out;
+            a.lam_gp = lam_gp;
+            a.lam_g = lam_g;
             a.lamP_new = lp_new;
             a.lamP_old = lp_old;
-            CK(launch_adjoint_step(a, ctx->hinst, st));
-            std::swap(lam_in, lam_out);
+            CK(launch_adjoint_step(a, st));
+            std::swap(lam_gp, lam_g);
             std::swap(lp_new, lp_old);
             CK(cudaMemsetAsync(lp_old, 0, (size_t)np * 2 * ADJ_LP * sizeof(double), st));
         }
     }
-    // lambda(f*(0)) is lam_in, lambda(P(0)) is lp_new: the initial field's share
-    a.lam_in = lam_in;
-    std::vector<int> couette(ni);
-    for (int i = 0; i < ni; ++i) couette[i] = ctx->icfg[i].init == LBM_INIT_COUETTE;
-    CK(launch_adjoint_init(a, ctx->hinst, couette, st));
+    // lambda(g(0)) is lam_gp, lambda(P(0)) is lp_new: the initial field's share
+    a.lam_gp = lam_gp;
+    CK(launch_adjoint_init(a, st));
     std::vector<double> lp((size_t)np * 2 * ADJ_LP), lsh((size_t)np * 2 * ADJ_LS), lmg((size_t)nm * 2 * ADJ_LG),
         lw((size_t)ni * 2 * 8);
     CK(cudaMemcpyAsync(lp.data(), lp_new, lp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1519,7 +1666,7 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* ctx, int32_t nsteps, int32_t checkpoi
     if (ctx->prec != LBM_FP32) return fail(ctx, LBM_EINVAL, "the adjoint runs on LBM_FP32 contexts");
     if (ctx->steps != 0) return fail(ctx, LBM_EINVAL, "the adjoint starts from a context with no steps done");
     if (ctx->np < 1) return fail(ctx, LBM_EINVAL, "the adjoint needs a particle");
-    if (ctx->step_mode != LBM_STEP_SEPARATE) return fail(ctx, LBM_EINVAL, "the adjoint needs the separate step mode");
+    if (ctx->step_mode == LBM_STEP_FUSED) return fail(ctx, LBM_EINVAL, "the adjoint does not run the fused step");
     for (const Inst& I : ctx->hinst)
         if (!I.G.px) return fail(ctx, LBM_EINVAL, "the adjoint needs periodic x sides (no x walls)");
     return adjoint_run(ctx, nsteps, checkpoint_every, seed, dparticle, dwall);

@@ -125,6 +125,7 @@ struct ParticleArgs {
     int4* boxes;              // per particle: support box (x0, y0, x1, y1)
     unsigned* err;
     int weight;
+    int blk_base;             // marker block of the kernels' first CTA (a range of the table)
     int single;               // the context holds one lattice: `one` is its descriptor
     Inst one;
     // a context of at most INLINE_BLOCKS marker blocks also passes the block
@@ -143,8 +144,19 @@ struct SpreadArgs {
     int single;               // as in ParticleArgs
     Inst one;
     const int4* ptab;         // per particle: (first marker, markers, instance, tiles of its box)
+    int p_base;               // particle of the kernel's first CTA row (a range of the particles)
     int np_inline;            // 0 or the particle count (at most INLINE_PARTICLES)
     int4 part_inline[INLINE_PARTICLES];  // the first np_inline entries of ptab
+};
+
+// Scheduling priority of the kernels this host thread launches through
+// launch_k (lbib_device.cuh) (0: the stream's own; lower is more urgent, as for streams), set
+// for a group of launches by a LaunchPriority guard.
+inline thread_local int tl_launch_priority = 0;
+struct LaunchPriority {
+    int old;
+    explicit LaunchPriority(int p) : old(tl_launch_priority) { tl_launch_priority = p; }
+    ~LaunchPriority() { tl_launch_priority = old; }
 };
 
 // One tile of a task list: instance, tile x, tile y (a tile being 32 * cpt
@@ -235,9 +247,8 @@ struct AdjArgs {
     const int4* ptab;          // per particle: (first marker, markers, instance, -)
     int np, nmark, weight;
     long long pop_elems, flb_elems;
-    const float* lam_in;       // lambda(f*(n+1)) per output
-    float* lam_g;              // lambda of the streamed populations of level n
-    float* lam_out;            // lambda(f*(n))
+    const float* lam_gp;       // lambda of the streamed populations of level n + 1, per output
+    float* lam_g;              // the same of level n
     float* lam_F;
     double* lamP_new;          // per particle and output: lambda(P(n+1)) (see adjoint.cu)
     double* lamP_old;          // lambda(P(n)), accumulated
@@ -245,6 +256,9 @@ struct AdjArgs {
     double* lam_shape;         // per particle and output: lambda of 1/m, 1/I, area, rho_s
     double* lam_mgeo;          // per marker and output: lambda of rb (2), nb (2), S
     double* lam_wall;          // per instance and output: lambda of wall_u[4][2]
+    float* zh;                 // per instance and y wall: the Zou-He transpose (9 x 9)
+    const int4* cblk;          // blocks of the cell kernels: (instance, bx, by, flags)
+    int ncblk;
     unsigned* err;
 };
 
@@ -294,12 +308,15 @@ cudaError_t launch_get_pops(int prec, const void* fbuf, const Inst& I, int y0, i
 cudaError_t launch_step_fused(int prec, const FusedArgs& f, int sms, cudaStream_t s);
 int fused_spread_rows();
 int fused_fluid_variant();
-// the reverse step (adjoint.cu): the kernels of one step in order, and the
-// initial Couette profile's share of the wall-speed adjoint (instances
-// whose init_couette entry is nonzero)
-cudaError_t launch_adjoint_step(const AdjArgs& a, const std::vector<Inst>& insts, cudaStream_t s);
-cudaError_t launch_adjoint_init(const AdjArgs& a, const std::vector<Inst>& insts, const std::vector<int>& init_couette,
-                                cudaStream_t s);
+// the reverse step (adjoint.cu): setup (the Zou-He transposes), the kernels
+// of one step in order, and the initial Couette profile's share of the
+// wall-speed adjoint.  The cell kernels' block list has blocks of 32 x
+// adjoint_block_rows() cells; flags bit 0: the instance starts from the
+// Couette profile
+int adjoint_block_rows();
+cudaError_t launch_adjoint_setup(const AdjArgs& a, int ninst, cudaStream_t s);
+cudaError_t launch_adjoint_step(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint_init(const AdjArgs& a, cudaStream_t s);
 // OR `bits` into the device error word, as a kernel that detects an error does
 cudaError_t launch_raise(unsigned* err, unsigned bits, cudaStream_t s);
 cudaError_t launch_probes(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s);

@@ -12,19 +12,20 @@ constexpr int SPREAD_TY = 16;  // rows of a spreading tile of the separate kerne
 
 template <class S, class C, class R, bool ONE>
 __global__ void __launch_bounds__(32) k_probes(ParticleArgs a) {
-    probe_block<S, C, R, ONE, false>(a, blockIdx.x, nullptr);
+    probe_block<S, C, R, ONE, false>(a, a.blk_base + blockIdx.x, nullptr);
 }
 
 template <class S, class C, class R, bool ONE>
 __global__ void __launch_bounds__(32) k_markers(ParticleArgs a) {
-    marker_block<S, C, R, ONE, false>(a, blockIdx.x, nullptr);
+    marker_block<S, C, R, ONE, false>(a, a.blk_base + blockIdx.x, nullptr);
 }
 
 template <class C, class R, bool ONE>
 __global__ void __launch_bounds__(TX * SPREAD_TY, sizeof(C) == 4 ? 2 : 1) k_spread(SpreadArgs a) {
     __shared__ SpreadSmem<C, SPREAD_TY> sm;
-    const int4 pr = a.np_inline ? a.part_inline[blockIdx.y] : a.ptab[blockIdx.y];
-    spread_tile<C, R, ONE, false, SPREAD_TY>(a, blockIdx.x, blockIdx.y, pr.w, sm);
+    const int p = a.p_base + blockIdx.y;
+    const int4 pr = a.np_inline ? a.part_inline[p] : a.ptab[p];
+    spread_tile<C, R, ONE, false, SPREAD_TY>(a, blockIdx.x, p, pr.w, sm);
 }
 
 }  // namespace

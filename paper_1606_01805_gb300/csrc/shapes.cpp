@@ -41,25 +41,53 @@ struct GaussLegendre {
     }
 };
 
-// arc length of (a cos t, b sin t) over [0, t]: composite 20-point Gauss-Legendre
+// Arc length along (a cos t, b sin t), t in [0, 2 pi]: a table of the
+// cumulative length at NT equal steps of t (one 20-point Gauss-Legendre
+// panel per step), and within a step one more panel from the step's start
+struct ArcRule {
+    static constexpr int NT = 256;
+    static constexpr double DT = 2.0 * M_PI / NT;
+};
+
 template <class T>
-T ellipse_arc(const T& a, const T& b, const T& t) {
+T arc_panel(const T& a, const T& b, double t0, const T& t1) {
     using std::cos;
     using std::hypot;
     using std::sin;
     static const GaussLegendre gl(20);
-    const int panels = 64;
-    const T h = t / (double)panels;
+    const T h = t1 - t0, mid = t0 + 0.5 * h;
     T acc = T(0.0);
-    for (int p = 0; p < panels; ++p) {
-        const T mid = (p + 0.5) * h;
-        for (size_t i = 0; i < gl.x.size(); ++i) {
-            const T s = mid + (0.5 * gl.x[i]) * h;
-            acc += gl.w[i] * hypot(a * sin(s), b * cos(s));
-        }
+    for (size_t i = 0; i < gl.x.size(); ++i) {
+        const T s = mid + (0.5 * gl.x[i]) * h;
+        acc += gl.w[i] * hypot(a * sin(s), b * cos(s));
     }
     return 0.5 * h * acc;
 }
+
+template <class T>
+struct EllipseArc {
+    T a, b;
+    std::vector<T> cum;
+    EllipseArc(const T& a_, const T& b_) : a(a_), b(b_), cum(ArcRule::NT + 1) {
+        cum[0] = T(0.0);
+        for (int j = 0; j < ArcRule::NT; ++j)
+            cum[j + 1] = cum[j] + arc_panel<T>(a, b, j * ArcRule::DT, T((j + 1) * ArcRule::DT));
+    }
+    T perimeter() const { return cum[ArcRule::NT]; }
+    int step_of(double t) const { return std::min(std::max((int)std::floor(t / ArcRule::DT), 0), ArcRule::NT - 1); }
+    T operator()(const T& t) const {  // length over [0, t]
+        const int j = step_of(value_of(t));
+        return cum[j] + arc_panel<T>(a, b, j * ArcRule::DT, t);
+    }
+    // the parameter where the length reaches s (values only): linear in the
+    // table's step, the start of the Newton iteration
+    double guess(double s) const {
+        int j = 0;
+        while (j < ArcRule::NT - 1 && value_of(cum[j + 1]) <= s) ++j;
+        const double c0 = value_of(cum[j]), c1 = value_of(cum[j + 1]);
+        return (j + (s - c0) / (c1 - c0)) * ArcRule::DT;
+    }
+};
 
 }  // namespace
 
@@ -80,7 +108,9 @@ int make_shape_t(const lbm_particle_desc& d, const T dim[2], double spacing, T* 
         case LBM_SHAPE_CIRCLE:
         case LBM_SHAPE_ELLIPSE: {
             const T a = 0.5 * D0, b = d.shape == LBM_SHAPE_CIRCLE ? 0.5 * D0 : 0.5 * D1;
-            const T P = d.shape == LBM_SHAPE_CIRCLE ? M_PI * D0 : ellipse_arc<T>(a, b, T(2.0 * M_PI));
+            std::vector<EllipseArc<T>> arc;
+            if (d.shape == LBM_SHAPE_ELLIPSE) arc.emplace_back(a, b);
+            const T P = d.shape == LBM_SHAPE_CIRCLE ? M_PI * D0 : arc[0].perimeter();
             n = d.n_markers > 0 ? d.n_markers : (int)std::lround(value_of(P) / h0);
             if (n < 8) n = 8;
             if (n > cap) return -1;
@@ -88,14 +118,15 @@ int make_shape_t(const lbm_particle_desc& d, const T dim[2], double spacing, T* 
                 T t = T(2.0 * M_PI * (l + 0.5) / n);
                 if (d.shape == LBM_SHAPE_ELLIPSE) {  // invert the arc length by Newton
                     const T target = ((l + 0.5) / n) * P;
+                    t = T(arc[0].guess(value_of(target)));
                     for (int it = 0; it < 60; ++it) {
-                        const T g = ellipse_arc<T>(a, b, t) - target;
+                        const T g = arc[0](t) - target;
                         const T dt = g / hypot(a * sin(t), b * cos(t));
                         t -= dt;
                         // one more pass after the value has converged lets the
                         // derivatives converge too (Newton on the dual part)
                         if (std::fabs(value_of(dt)) < 1e-15) {
-                            const T g2 = ellipse_arc<T>(a, b, t) - target;
+                            const T g2 = arc[0](t) - target;
                             t -= g2 / hypot(a * sin(t), b * cos(t));
                             break;
                         }

@@ -28,7 +28,7 @@ LBM_TANGENT_FIELDS = 10     # xc, yc, theta, u[0], u[1], omega, F[0], F[1], M, o
 TANGENT_FIELDS = ("xc", "yc", "theta", "ux", "uy", "omega", "Fx", "Fy", "M", "omega_sum")
 SEED_FIELDS = ("dim0", "dim1", "xc", "yc", "theta", "rho_s")
 LBM_INIT_REST, LBM_INIT_COUETTE, LBM_INIT_TAYLOR_GREEN = 0, 1, 2
-LBM_STEP_SEPARATE, LBM_STEP_FUSED = 0, 1  # step modes of a batch (lbm_set_step_mode)
+LBM_STEP_SEPARATE, LBM_STEP_FUSED, LBM_STEP_OVERLAP = 0, 1, 2  # step modes of a batch (lbm_set_step_mode)
 LBM_SHAPE_CIRCLE, LBM_SHAPE_ELLIPSE, LBM_SHAPE_RECT, LBM_SHAPE_SQUARE, LBM_SHAPE_TRIANGLE = range(5)
 LBM_W_EXP, LBM_W_CUBIC, LBM_W_QUARTIC, LBM_W_COSINE, LBM_W_POLY = range(5)
 
@@ -377,7 +377,8 @@ class Batch:
         return self.shapes[instance]
 
     def set_step_mode(self, mode):
-        """LBM_STEP_SEPARATE or LBM_STEP_FUSED (one persistent launch per step)."""
+        """LBM_STEP_SEPARATE, LBM_STEP_OVERLAP (two halves of the instances on two
+        streams) or LBM_STEP_FUSED (one persistent launch per step)."""
         self._check(load().lbm_set_step_mode(self._h, mode), "lbm_set_step_mode")
 
     def step_mode(self):

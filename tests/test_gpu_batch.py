@@ -178,3 +178,71 @@ def test_fused_step_needs_a_batch():
     t = lbib.Batch([dict(W.batch_config(w), precision=lbib.LBM_FP32_TANGENT) for w in wls])
     with pytest.raises(lbib.LbmError):
         t.set_step_mode(lbib.LBM_STEP_FUSED)
+
+
+def _mode_pair(wls, prec, steps, mode):
+    out = []
+    for m in (lbib.LBM_STEP_SEPARATE, mode):
+        b = make_batch(wls, prec)
+        b.set_step_mode(m)
+        assert b.step_mode() == m
+        b.step(steps)
+        b.sync()
+        out.append(([b.populations(k) for k in range(len(wls))], b.particles()))
+        b.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64, lbib.LBM_FP16_SHIFTED, lbib.LBM_FP32_TANGENT])
+def test_overlapped_step_equals_separate_kernels(prec):
+    """Two halves of the instances on two streams (two graph replays of 32
+    steps, then direct steps) give the bits of the separate kernels."""
+    wls = small_batch(n=8, seed=5)
+    (pa, qa), (pb, qb) = _mode_pair(wls, prec, 70, lbib.LBM_STEP_OVERLAP)
+    for k in range(len(wls)):
+        np.testing.assert_array_equal(pb[k], pa[k], err_msg=wls[k].name)
+    assert qa == qb
+
+
+def test_overlapped_step_with_particles_out_of_instance_order():
+    """Particles not numbered in instance order: the mode runs one chain,
+    with the same bits."""
+    wls = small_batch(n=4, seed=9)
+    res = []
+    for m in (lbib.LBM_STEP_SEPARATE, lbib.LBM_STEP_OVERLAP):
+        b = lbib.Batch([dict(W.batch_config(w), precision=FP32) for w in wls], max_particles=64,
+                       max_markers=65536)
+        for k in reversed(range(len(wls))):
+            b.add_particle(k, **wls[k].particles[0].kwargs())
+        b.set_step_mode(m)
+        b.step(40)
+        res.append(([b.populations(k) for k in range(len(wls))], b.particles()))
+        b.close()
+    for a, c in zip(res[0][0], res[1][0]):
+        np.testing.assert_array_equal(a, c)
+    assert res[0][1] == res[1][1]
+
+
+def test_overlapped_step_on_the_screening_batch():
+    """The 512-lattice screening batch, overlapped halves against separate
+    kernels, through a graph replay."""
+    wls = W.batched_screening(steps=0)
+    res = []
+    for mode in (lbib.LBM_STEP_SEPARATE, lbib.LBM_STEP_OVERLAP):
+        b = lbib.Batch([dict(W.batch_config(w), precision=FP32) for w in wls], max_particles=512,
+                       max_markers=600000)
+        for k, w in enumerate(wls):
+            b.add_particle(k, **w.particles[0].kwargs())
+        b.set_step_mode(mode)
+        b.step(33)
+        b.sync()
+        res.append(([b.populations(k) for k in (0, 200, 300, 511)], b.particles()))
+        b.close()
+    for a, c in zip(res[0][0], res[1][0]):
+        np.testing.assert_array_equal(a, c)
+    assert res[0][1] == res[1][1]
+
+
+def test_overlapped_step_needs_a_batch():
+    sim = lbib.Simulation(64, 40, 0.8, precision=FP32)
+    assert lbib.load().lbm_set_step_mode(sim._h, lbib.LBM_STEP_OVERLAP) == lbib.LBM_EINVAL
