@@ -267,48 +267,35 @@ def screening_batch(prec, wls):
     return b
 
 
-def time_batched(prec, steps, warmup, instances=512, mode=0):
+def time_batched(prec, steps, warmup, instances=512, mode=None):
     """The screening batch (512 uneven lattices, 63 M cells, beyond L2) as
-    one context, in step mode `mode` (separate kernels or the fused
-    persistent launch): device time per step from the library's events."""
+    one context, in step mode `mode` (None: the library's default for
+    batches): device time per step over a run of graph-replayed steps (CUDA
+    events on the context's stream around lbm_step, as a long run steps),
+    and the fluid kernel's own time from timed single steps."""
+    import torch
+
     from paper_1606_01805_gb300 import workloads as W
 
     wls = W.batched_screening(steps=0)[:instances]
     b = screening_batch(prec, wls)
-    b.set_step_mode(mode)
-    b.step_timed(warmup, fluid=False)
-    ms_step = b.step_timed(steps, fluid=False)[0]
-    ms_fluid = b.step_timed(steps)[1]
-    tile = b.tile()
+    if mode is not None:
+        b.set_step_mode(mode)
+    b.step(max(warmup, 1))  # the first step picks the fluid tile
+    b.sync()
+    run = max(32, steps // 32 * 32)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.step(run)
+    e1.record()
+    e1.synchronize()
+    ms_step = e0.elapsed_time(e1) / run
+    nf = min(steps, 10)
+    ms_fluid = b.step_timed(nf)[1] / nf
+    tile, used = b.tile(), b.step_mode()
     b.close()
     cells = sum(w.cells for w in wls)
-    return cells, ms_step / steps, ms_fluid / steps, tile
-
-
-def time_sensitivity(prec, steps, warmup, n=64):
-    """The sensitivity batch (64 Couette channels 400 x 100 with an ellipse
-    each, inputs (aspect ratio, y0, wall speed) from seed 4) as one context,
-    in the tangent mode (values and the 3 derivative directions) or plain
-    FP32: device time per step from the library's events."""
-    from paper_1606_01805_gb300 import lbib
-    from paper_1606_01805_gb300 import sensitivity as S
-    from paper_1606_01805_gb300 import workloads as W
-
-    P, T = W.sensitivity_batch(n=n)
-    wls = [W.sensitivity_ellipse(*P[b], steps=0, theta=float(T[b])) for b in range(n)]
-    sim = lbib.Batch([dict(W.batch_config(w), precision=prec) for w in wls], max_particles=n,
-                     max_markers=n * (W.SENS_MARKERS + 8))
-    tangent = prec == lbib.LBM_FP32_TANGENT
-    for b, w in enumerate(wls):
-        seed, dwall = S.seeds(P[b, 0])
-        if tangent:
-            sim.set_wall_tangents(dwall, b)
-        sim.add_particle(b, **w.particles[0].kwargs(), tangent=seed if tangent else None)
-    sim.step_timed(warmup, fluid=False)
-    ms = sim.step_timed(steps, fluid=False)[0]
-    msf = sim.step_timed(steps)[1]
-    sim.close()
-    return sum(w.cells for w in wls), ms / steps, msf / steps
+    return cells, ms_step, ms_fluid, tile, used
 
 
 def time_adjoint(steps=2000, checkpoint_every=100, n=64):
@@ -598,13 +585,21 @@ def main():
         if not args.no_batched:
             batched = {"workload": "screening batch, 512 Couette lattices 256-1024 x 128-256, "
                                    "one random particle each (seed 3)"}
+            from paper_1606_01805_gb300 import lbib as _lb
+
+            mode_names = {_lb.LBM_STEP_SEPARATE: "separate", _lb.LBM_STEP_OVERLAP: "overlap",
+                          _lb.LBM_STEP_FUSED: "fused"}
             for pname, pv in (("fp32", 1), ("fp16s", 2)):
-                bc, bms, bmsf, btile = time_batched(pv, 20, 3)
+                bc, bms, bmsf, btile, bmode = time_batched(pv, 64, 3)
                 bpc = BYTES_PER_CELL[pv]
                 batched[pname] = {"MLUPS": bc / (bms * 1e-3) / 1e6, "ms_per_step": bms,
                                   "fluid_GBps": bpc * bc / (bmsf * 1e-3) / 1e9,
                                   "frac_of_roofline_mlups": bc / (bms * 1e-3) / (peak * 1e9 / bpc),
-                                  "tile": btile}
+                                  "tile": btile, "step_mode": mode_names.get(bmode, bmode)}
+            # the other step modes of the same batch (FP32)
+            batched["fp32_step_modes_ms_per_step"] = {
+                mode_names[m]: time_batched(1, 64, 3, mode=m)[1]
+                for m in (_lb.LBM_STEP_SEPARATE, _lb.LBM_STEP_OVERLAP, _lb.LBM_STEP_FUSED)}
             bc, ms_pi = time_per_instance(1, 2)
             batched["fp32_per_instance_contexts"] = {"MLUPS": bc / (ms_pi * 1e-3) / 1e6,
                                                      "ms_per_step": ms_pi}
@@ -657,7 +652,7 @@ def main_screening(args):
     torch.cuda.set_device(0)
     build.build()
     with ClockSampler(0) as clk:
-        cells, ms, msf, tile = time_batched(prec, args.steps, args.warmup, args.instances)
+        cells, ms, msf, tile, _ = time_batched(prec, args.steps, args.warmup, args.instances)
     peak, peak_kind = hbm_peak()
     bpc = BYTES_PER_CELL[prec]
     achieved = bpc * cells / (msf * 1e-3) / 1e9

@@ -351,10 +351,12 @@ lbm_status lbm_tile_info(int32_t variant, int32_t precision, int32_t* cells_per_
 lbm_status lbm_set_tile(lbm_ctx* ctx, int32_t variant);
 
 /*
- * Step mode of a batch.  LBM_STEP_SEPARATE (the default): each step is the
- * immersed-boundary kernels (probes and rigid update, markers, spreading)
- * and then the fluid kernel, each one launch over all instances.
- * LBM_STEP_OVERLAP: the instances are split into two halves of about equal
+ * Step mode of a batch.  LBM_STEP_SEPARATE (the mode of a single lattice):
+ * each step is the immersed-boundary kernels (probes and rigid update,
+ * markers, spreading) and then the fluid kernel, each one launch over all
+ * instances.
+ * LBM_STEP_OVERLAP (the default of a batch of two or more instances): the
+ * instances are split into two halves of about equal
  * cell count, and lbm_step's captured runs of steps advance each half with
  * its own chain of the same kernels on a stream of its own, the
  * immersed-boundary kernels at the device's most urgent scheduling

@@ -86,9 +86,9 @@ struct lbm_ctx {
     bool items_dirty = true;
     unsigned* counters = nullptr;
     size_t counter_words = 0;       // per set
-    // overlapped step of a batch (LBM_STEP_OVERLAP): two halves of the
-    // instances, each a range of the marker blocks, the particles and every
-    // variant's task list; empty when the batch cannot be split that way
+    // overlapped step of a batch (LBM_STEP_OVERLAP): runs of the instances,
+    // each a range of the marker blocks, the particles and every variant's
+    // task list; empty when the batch cannot be split that way
     struct Half {
         int b0, b1, p0, p1;
         int t0[N_FLUID_VARIANTS], t1[N_FLUID_VARIANTS];
@@ -487,56 +487,61 @@ lbm_status launch_fused_step(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t ste
 
 bool fused(const lbm_ctx* ctx) { return ctx->step_mode == LBM_STEP_FUSED; }
 
-// The overlapped step's halves: the instances split where the first half's
-// cells reach half the total, if that boundary also splits the particles
-// and the marker blocks (particles numbered in instance order).
+// The overlapped step's parts: OVERLAP_PARTS runs of instances of about
+// equal cell count, each also a run of the particles and of the marker
+// blocks (particles numbered in instance order); none when that fails.
+constexpr int OVERLAP_PARTS = 2;
+
 void plan_halves(lbm_ctx* ctx) {
     ctx->halves.clear();
     ctx->halves_dirty = false;
-    const int n = ctx->ninst;
-    if (n < 2) return;
+    const int n = ctx->ninst, P = std::min(OVERLAP_PARTS, n);
+    if (P < 2) return;
     long long tot = 0;
     for (const Inst& I : ctx->hinst) tot += (long long)I.G.nx * I.G.ny;
-    int k = 1;
-    long long acc = (long long)ctx->hinst[0].G.nx * ctx->hinst[0].G.ny;
-    while (k < n - 1 && 2 * acc < tot) {
-        acc += (long long)ctx->hinst[k].G.nx * ctx->hinst[k].G.ny;
-        ++k;
+    // first instance of each part
+    std::vector<int> cut(P + 1, n);
+    cut[0] = 0;
+    long long acc = 0;
+    int part = 1;
+    for (int i = 0; i < n && part < P; ++i) {
+        acc += (long long)ctx->hinst[i].G.nx * ctx->hinst[i].G.ny;
+        if (acc * P >= tot * part && i + 1 < n) cut[part++] = i + 1;
     }
-    // the first particle / block / task of instance k or later; every one
-    // after it must belong to the second half too
-    auto split = [k](int count, auto inst_of) {
-        int first = count;
-        for (int i = 0; i < count; ++i)
-            if (inst_of(i) >= k) {
-                first = i;
-                break;
-            }
-        for (int i = first; i < count; ++i)
-            if (inst_of(i) < k) return -1;
-        return first;
+    if (part < P) return;
+    // the same runs over particles, blocks and tasks (instance never decreasing)
+    auto runs = [&](int count, auto inst_of, std::vector<int>& at) {
+        at.assign(P + 1, count);
+        at[0] = 0;
+        int q = 1;
+        for (int i = 0; i < count; ++i) {
+            if (i > 0 && inst_of(i) < inst_of(i - 1)) return false;
+            while (q < P && inst_of(i) >= cut[q]) at[q++] = i;
+        }
+        return true;
     };
-    const int ps = split(ctx->np, [&](int p) { return ctx->hpart[p].z; });
-    const int bs = split(ctx->nblk, [&](int b) { return ctx->hblk[b].w; });
-    if (ps < 0 || bs < 0) return;
-    lbm_ctx::Half h0{0, bs, 0, ps, {}, {}}, h1{bs, ctx->nblk, ps, ctx->np, {}, {}};
+    std::vector<int> pa, ba;
+    if (!runs(ctx->np, [&](int p) { return ctx->hpart[p].z; }, pa)) return;
+    if (!runs(ctx->nblk, [&](int b) { return ctx->hblk[b].w; }, ba)) return;
+    std::vector<lbm_ctx::Half> parts(P);
+    for (int q = 0; q < P; ++q) parts[q] = lbm_ctx::Half{ba[q], ba[q + 1], pa[q], pa[q + 1], {}, {}};
     for (int v = 0; v < N_FLUID_VARIANTS; ++v) {
         const std::vector<Task> t = make_tasks(ctx->hinst, v);
-        const int ts = split((int)t.size(), [&](int i) { return t[i].inst; });
-        if (ts < 0) return;
-        h0.t0[v] = 0;
-        h0.t1[v] = ts;
-        h1.t0[v] = ts;
-        h1.t1[v] = (int)t.size();
+        std::vector<int> ta;
+        if (!runs((int)t.size(), [&](int i) { return t[i].inst; }, ta)) return;
+        for (int q = 0; q < P; ++q) {
+            parts[q].t0[v] = ta[q];
+            parts[q].t1[v] = ta[q + 1];
+        }
     }
-    ctx->halves = {h0, h1};
+    ctx->halves = parts;
 }
 
-bool overlapped(const lbm_ctx* ctx) { return ctx->step_mode == LBM_STEP_OVERLAP && ctx->halves.size() == 2; }
+bool overlapped(const lbm_ctx* ctx) { return ctx->step_mode == LBM_STEP_OVERLAP && ctx->halves.size() >= 2; }
 
-// time step number `step` of one half of the instances from buffer `cur`
+// time step number `step` of one part of the instances from buffer `cur`
 // on stream `st`: its IB kernels (at the context's most urgent priority, so
-// that their CTAs go ahead of the other half's fluid CTAs), then its fluid
+// that their CTAs go ahead of the other parts' fluid CTAs), then its fluid
 // tasks
 lbm_status enqueue_half(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t step, const lbm_ctx::Half& h) {
     const bool ib = h.p1 > h.p0;
@@ -593,16 +598,24 @@ bool capture_graph(lbm_ctx* ctx, int cur, int64_t step) {
     cudaGraphExec_t& ge = ctx->graph[cur][step % ctx->check_every];
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return false;
-    // the overlapped step: the second half on a stream of its own, forked
-    // from the capture and joined back at its end
-    cudaStream_t cs2 = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    // the overlapped step: every part after the first on a stream of its
+    // own, forked from the capture and joined back at its end
     const bool two = overlapped(ctx);
-    if (two && (cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess)) {
-        if (cs2) cudaStreamDestroy(cs2);
-        if (fork) cudaEventDestroy(fork);
+    const int P = two ? (int)ctx->halves.size() : 1;
+    std::vector<cudaStream_t> side(P > 1 ? P - 1 : 0, nullptr);
+    std::vector<cudaEvent_t> evs(P, nullptr);  // fork, then one join per side stream
+    bool made = true;
+    for (auto& x : side) made = made && cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) == cudaSuccess;
+    if (two)
+        for (auto& e : evs) made = made && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    auto release = [&] {
+        for (auto x : side)
+            if (x) cudaStreamDestroy(x);
+        for (auto e : evs)
+            if (e) cudaEventDestroy(e);
+    };
+    if (!made) {
+        release();
         cudaStreamDestroy(cs);
         cudaGetLastError();
         return false;
@@ -611,12 +624,16 @@ bool capture_graph(lbm_ctx* ctx, int cur, int64_t step) {
     if (ok) {
         int c = cur;
         if (two) {
-            ok = cudaEventRecord(fork, cs) == cudaSuccess && cudaStreamWaitEvent(cs2, fork, 0) == cudaSuccess;
+            ok = cudaEventRecord(evs[0], cs) == cudaSuccess;
+            for (auto x : side) ok = ok && cudaStreamWaitEvent(x, evs[0], 0) == cudaSuccess;
             for (int k = 0; k < GRAPH_STEPS && ok; ++k, c ^= 1)
-                ok = enqueue_half(ctx, cs, c, step + k, ctx->halves[0]) == LBM_OK &&
-                     enqueue_half(ctx, cs2, c, step + k, ctx->halves[1]) == LBM_OK;
-            // the join, whatever happened, so that the capture can end
-            const bool joined = cudaEventRecord(join, cs2) == cudaSuccess && cudaStreamWaitEvent(cs, join, 0) == cudaSuccess;
+                for (int q = 0; q < P && ok; ++q)
+                    ok = enqueue_half(ctx, q ? side[q - 1] : cs, c, step + k, ctx->halves[q]) == LBM_OK;
+            // the joins, whatever happened, so that the capture can end
+            bool joined = true;
+            for (int q = 1; q < P; ++q)
+                joined = cudaEventRecord(evs[q], side[q - 1]) == cudaSuccess &&
+                         cudaStreamWaitEvent(cs, evs[q], 0) == cudaSuccess && joined;
             ok = ok && joined;
         } else {
             for (int k = 0; k < GRAPH_STEPS && ok; ++k, c ^= 1)
@@ -628,11 +645,7 @@ bool capture_graph(lbm_ctx* ctx, int cur, int64_t step) {
         if (g) cudaGraphDestroy(g);
     }
     cudaStreamDestroy(cs);
-    if (two) {
-        cudaStreamDestroy(cs2);
-        cudaEventDestroy(fork);
-        cudaEventDestroy(join);
-    }
+    release();
     cudaGetLastError();  // a failed capture leaves no sticky error
     if (!ok) ge = nullptr;
     return ok;
@@ -815,6 +828,13 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
+    // a batch steps its instances in overlapped parts by default
+    if (n >= 2) {
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        ctx->prio_hi = greatest;
+        ctx->step_mode = LBM_STEP_OVERLAP;
+    }
     if (ctx->sms < 1) ctx->sms = 1;
     std::vector<std::vector<Task>> tasks(N_FLUID_VARIANTS);
     for (int v = 0; v < N_FLUID_VARIANTS; ++v) tasks[v] = make_tasks(L.insts, v);

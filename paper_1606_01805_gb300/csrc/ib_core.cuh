@@ -594,9 +594,11 @@ __device__ __forceinline__ void spread_tile(const SpreadArgs& a, int tile, int p
         for (int h = 0; h < 2; ++h) {
             const int k = h * TX * TY + t, l = base + k;
             if (k < CAP && l < nm) {
-                r[h] = recs[m0 + l];
-                rel[h] = r[h].i0 <= x0 + TX - 1 && r[h].i0 + 2 >= x0 && r[h].j0 <= y0 + TY - 1 &&
-                         r[h].j0 + 2 >= y0;
+                // the support origin first (one 16-byte load, the record's
+                // first sector); the whole record only if it is relevant
+                const int4 head = *reinterpret_cast<const int4*>(recs + m0 + l);
+                rel[h] = head.x <= x0 + TX - 1 && head.x + 2 >= x0 && head.y <= y0 + TY - 1 && head.y + 2 >= y0;
+                if (rel[h]) r[h] = recs[m0 + l];
             }
         }
         const unsigned bal0 = __ballot_sync(0xffffffffu, rel[0]), bal1 = __ballot_sync(0xffffffffu, rel[1]);
