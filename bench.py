@@ -180,7 +180,9 @@ def make_workload(name, steps):
         return W.large_couette(steps=steps)
     if name == "couette2k":  # 2048 x 2048, 4 particles: beyond L2, small enough to profile
         return W.large_couette(nx=2048, ny=2048, n_particles=4, steps=steps)
-    if name == "screening":  # the 512-lattice batch, timed as one context
+    if name.startswith("shape") and name[5:].isdigit():  # one lattice of the 1024 x 256 shape set
+        return W.couette_shapes(steps=steps)[int(name[5:])]
+    if name in ("screening", "adjoint"):  # batches, timed as one context each
         return None
     raise SystemExit(f"unknown workload {name}")
 
@@ -296,6 +298,32 @@ def time_batched(prec, steps, warmup, instances=512, mode=None):
     b.close()
     cells = sum(w.cells for w in wls)
     return cells, ms_step, ms_fluid, tile, used
+
+
+def time_sensitivity(prec, steps, warmup, n=64):
+    """The sensitivity batch (64 Couette channels 400 x 100 with an ellipse
+    each, inputs (aspect ratio, y0, wall speed) from seed 4) as one context,
+    in the tangent mode (values and the 3 derivative directions) or plain
+    FP32: device time per step from the library's events."""
+    from paper_1606_01805_gb300 import lbib
+    from paper_1606_01805_gb300 import sensitivity as S
+    from paper_1606_01805_gb300 import workloads as W
+
+    P, T = W.sensitivity_batch(n=n)
+    wls = [W.sensitivity_ellipse(*P[b], steps=0, theta=float(T[b])) for b in range(n)]
+    sim = lbib.Batch([dict(W.batch_config(w), precision=prec) for w in wls], max_particles=n,
+                     max_markers=n * (W.SENS_MARKERS + 8))
+    tangent = prec == lbib.LBM_FP32_TANGENT
+    for b, w in enumerate(wls):
+        seed, dwall = S.seeds(P[b, 0])
+        if tangent:
+            sim.set_wall_tangents(dwall, b)
+        sim.add_particle(b, **w.particles[0].kwargs(), tangent=seed if tangent else None)
+    sim.step_timed(warmup, fluid=False)
+    ms = sim.step_timed(steps, fluid=False)[0]
+    msf = sim.step_timed(steps)[1]
+    sim.close()
+    return sum(w.cells for w in wls), ms / steps, msf / steps
 
 
 def time_adjoint(steps=2000, checkpoint_every=100, n=64):
@@ -481,6 +509,8 @@ def main():
                     help="force this fluid tile variant (lbm_set_tile) instead of the tuned one")
     ap.add_argument("--instances", type=int, default=512,
                     help="screening workload: first N lattices of the batch (profiling subsets)")
+    ap.add_argument("--threads", type=int, default=None,
+                    help="reference arm: host threads of the oracle (default: all cores)")
     ap.add_argument("--record-traffic", metavar="CSV", default=None,
                     help="record the fluid kernel's DRAM traffic from this ncu CSV log for --workload, "
                          "--precision and --tile, then exit")
@@ -497,7 +527,7 @@ def main():
         print(json.dumps(record_traffic(args.record_traffic, wl.name, prec, args.tile, cmd)))
         return
     if wl is None:
-        return main_screening(args)
+        return main_adjoint(args) if args.workload == "adjoint" else main_screening(args)
 
     if args.impl == "reference":
         if rank != 0:
@@ -506,7 +536,7 @@ def main():
         from oracle import oracle as o
         from paper_1606_01805_gb300 import workloads as W
 
-        cores = o.set_threads(os.cpu_count() or 1)
+        cores = o.set_threads(args.threads or os.cpu_count() or 1)
         sim = W.run_with(lambda nx, ny, tau, **kw: o.Sim(nx, ny, tau, **kw), wl, steps=0)
         for _ in range(args.warmup):
             sim.step(1)
@@ -667,6 +697,27 @@ def main_screening(args):
                      "frac": achieved / peak, "traffic": None, "kernel": "k_fluid (task list)",
                      "peak_source": f"{peak_kind} (burst copy)"},
         "gpu_launches": 4 * args.steps, "clocks": clk.summary()}))
+
+
+def main_adjoint(args):
+    """`--workload adjoint`: the sensitivity batch (64 channels 400 x 100,
+    one ellipse each) through lbm_adjoint over --steps steps with a
+    checkpoint every 100 steps (every half of them for shorter runs),
+    beside the same plain FP32 steps (wall time of each call)."""
+    import torch
+
+    from paper_1606_01805_gb300 import build
+
+    if args.impl == "reference":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle has no adjoint; its finite "
+                          "differences are the adjoint's parity check (tests/test_gpu_adjoint.py)"}))
+        return
+    torch.cuda.set_device(0)
+    build.build()
+    steps = max(2, args.steps)
+    r = time_adjoint(steps=steps, checkpoint_every=max(1, min(100, steps // 2)))
+    print(json.dumps(dict(r, workload="sensitivity batch: 64 Couette channels 400 x 100, one ellipse each",
+                          unit="ms")))
 
 
 if __name__ == "__main__":

@@ -358,10 +358,9 @@ lbm_status lbm_set_tile(lbm_ctx* ctx, int32_t variant);
  * LBM_STEP_OVERLAP (the default of a batch of two or more instances): the
  * instances are split into two halves of about equal
  * cell count, and lbm_step's captured runs of steps advance each half with
- * its own chain of the same kernels on a stream of its own, the
- * immersed-boundary kernels at the device's most urgent scheduling
- * priority: the particle work of one half runs beside the fluid kernel of
- * the other, step after step.  Steps launched one by one (lbm_step_timed,
+ * its own chain of the same kernels on a stream of its own: the particle
+ * work of one half can run beside the fluid kernel of the other, step
+ * after step.  Steps launched one by one (lbm_step_timed,
  * the remainder of a run that is not a multiple of 32 steps) run both
  * halves as in LBM_STEP_SEPARATE.  The split needs the particles numbered
  * in instance order across it; otherwise the mode runs as
@@ -455,7 +454,8 @@ lbm_status lbm_get_field_tangents(lbm_ctx* ctx, int32_t instance, double* drho, 
  * In a batch whose instances hold one particle each, J_o of instance i is
  * the output of its particle, so its rows are that particle's gradients.
  * Requirements (else LBM_EINVAL): LBM_FP32, no step done yet, at least one
- * particle, periodic x sides, not the fused step mode; a marker or probe
+ * particle, periodic x sides, fewer than 2^31 / 9 nodes per lattice, not
+ * the fused step mode; a marker or probe
  * support must stay off the wall rows (else LBM_EDOMAIN).  The call
  * allocates its own device memory (checkpoints, one segment of steps, the
  * adjoint buffers; LBM_ENOMEM if it does not fit) and frees it before it

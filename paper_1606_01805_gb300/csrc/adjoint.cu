@@ -219,39 +219,77 @@ __device__ __forceinline__ double warp_sum(double v) {
 __global__ void __launch_bounds__(32 * AB, 3) k_adj_cells(AdjArgs a) {
     const CellPos q = cell_pos(a);
     const Inst& I = *q.I;
+    // the lattice's geometry in registers; element offsets within one
+    // instance fit 32 bits (lbm_adjoint checks)
+    const int nx = I.G.nx, ny = I.G.ny, pitch = I.G.pitch, plane = (int)I.G.plane;
+    const bool px = I.G.px != 0, py = I.G.py != 0;
     const int x = q.x, y = q.y;
-    const bool in = x < I.G.nx && y < I.G.ny;
+    const bool in = x < nx && y < ny;
     const int seg = y * I.G.nseg + (x >> 5);
-    const long long c = (long long)y * I.G.pitch + x;
-    const bool wall = !I.G.py && y < I.G.ny && (y == 0 || y == I.G.ny - 1);  // the same for the whole warp
+    const int c = y * pitch + x;
+    const bool wall = !py && y < ny && (y == 0 || y == ny - 1);  // the same for the whole warp
     const int side = y == 0 ? 2 : 3;
+    const float* __restrict__ f = a.f + I.f_off;
+    const float* __restrict__ lp0 = a.lam_gp + I.f_off;
+    const float* __restrict__ lp1 = lp0 + a.pop_elems;
     bool forced = false;
     float lg[2][9], g0[9];
     if (in) {
-        // every load first: the populations, the force, both outputs' lambdas
-        pull_general<float, float>(a.f + I.f_off, I.G, x, y, g0);
+        // neighbour columns and rows (periodic wrap; -1 across a wall)
+        const int xm = x > 0 ? x - 1 : (px ? nx - 1 : -1), xp = x < nx - 1 ? x + 1 : (px ? 0 : -1);
+        const int ym = y > 0 ? y - 1 : (py ? ny - 1 : -1), yp = y < ny - 1 ? y + 1 : (py ? 0 : -1);
+        // every load first: the streamed populations (pull from x - e_i),
+        // the force, both outputs' lambda(g) of the next level at x + e_i
+        int ts[9];
+        float lam[2][9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int sx = cx(i) == 0 ? x : (cx(i) > 0 ? xm : xp), sy = cy(i) == 0 ? y : (cy(i) > 0 ? ym : yp);
+            g0[i] = sx >= 0 && sy >= 0 ? f[i * plane + sy * pitch + sx] : 0.f;
+            const int tx = cx(i) == 0 ? x : (cx(i) > 0 ? xp : xm), ty = cy(i) == 0 ? y : (cy(i) > 0 ? yp : ym);
+            ts[i] = tx >= 0 && ty >= 0 ? ty * pitch + tx : -1;
+            lam[0][i] = ts[i] >= 0 ? lp0[i * plane + ts[i]] : 0.f;
+            lam[1][i] = ts[i] >= 0 ? lp1[i * plane + ts[i]] : 0.f;
+        }
         forced = a.flags[I.flags_off + seg] != 0;
         float Fx = I.G.gf[0], Fy = I.G.gf[1];
         if (forced) {
             Fx += a.flb[I.flb_off + c];
-            Fy += a.flb[I.flb_off + I.G.plane + c];
+            Fy += a.flb[I.flb_off + plane + c];
         }
-        float lam[2][9];
-        lam_post(a, I, q.inst, x, y, lam);
+        // at a y wall node x + e_i, what the Zou-He unknowns owe the known
+        // populations (the transposes of k_adj_zh)
+        if (!py && (y <= 1 || y >= ny - 2)) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                if (ts[i] < 0) continue;
+                const int ty = cy(i) == 0 ? y : (cy(i) > 0 ? yp : ym);
+                if (ty != 0 && ty != ny - 1) continue;
+                const float* A = a.zh + ((long long)q.inst * 2 + (ty == 0 ? 0 : 1)) * 81;
+                for (int u = 0; u < 9; ++u) {
+                    const float w = A[u * 9 + i];
+                    if (w != 0.f) {
+                        lam[0][i] += w * lp0[u * plane + ts[i]];
+                        lam[1][i] += w * lp1[u * plane + ts[i]];
+                    }
+                }
+            }
+        }
         float g[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = g0[i];
-        complete_walls<float, float>(a.f + I.f_off, I.G, x, y, g);
+        complete_walls<float, float>(f, I.G, x, y, g);
         const CellState cs = cell_state(g, Fx, Fy);
+        const float omega = I.G.omegaf;
 #pragma unroll
         for (int o = 0; o < 2; ++o) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) lg[o][i] = 0.f;
             float lFx, lFy;
-            collide_adjoint(cs, I.G.omegaf, lam[o], lg[o], lFx, lFy);
-            float* __restrict__ lgo = a.lam_g + o * a.pop_elems;
+            collide_adjoint(cs, omega, lam[o], lg[o], lFx, lFy);
+            float* __restrict__ lgo = a.lam_g + o * a.pop_elems + I.f_off;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) lgo[cell_index(I, i, x, y)] = lg[o][i];
+            for (int i = 0; i < 9; ++i) lgo[i * plane + c] = lg[o][i];
             if (forced) {
                 a.lam_F[(2 * o) * a.flb_elems + I.flb_off + c] = lFx;
                 a.lam_F[(2 * o + 1) * a.flb_elems + I.flb_off + c] = lFy;
@@ -290,7 +328,7 @@ __global__ void __launch_bounds__(32 * AB, 3) k_adj_cells(AdjArgs a) {
     }
     if (forced) {
         a.flb[I.flb_off + c] = 0.f;
-        a.flb[I.flb_off + I.G.plane + c] = 0.f;
+        a.flb[I.flb_off + plane + c] = 0.f;
     }
     __syncwarp();  // every lane has read the segment's flag
     if (forced && (x & 31) == 0) a.flags[I.flags_off + seg] = 0;

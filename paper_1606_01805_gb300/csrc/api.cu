@@ -3,6 +3,7 @@
 // particle set-up, the fluid-tile autotuner and the per-step launch sequence
 // (probes -> markers -> spreading -> fused fluid step).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -95,7 +96,6 @@ struct lbm_ctx {
     };
     std::vector<Half> halves;
     bool halves_dirty = true;
-    int prio_hi = 0;                // the most urgent scheduling priority (the IB kernels')
     std::vector<double> hrc;        // per particle: circumscribed radius
     // for the adjoint: body-frame marker geometry in FP64 (rb, nb, S per
     // marker), each marker's particle, each particle's description
@@ -540,13 +540,10 @@ void plan_halves(lbm_ctx* ctx) {
 bool overlapped(const lbm_ctx* ctx) { return ctx->step_mode == LBM_STEP_OVERLAP && ctx->halves.size() >= 2; }
 
 // time step number `step` of one part of the instances from buffer `cur`
-// on stream `st`: its IB kernels (at the context's most urgent priority, so
-// that their CTAs go ahead of the other parts' fluid CTAs), then its fluid
-// tasks
+// on stream `st`: its IB kernels, then its fluid tasks
 lbm_status enqueue_half(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t step, const lbm_ctx::Half& h) {
     const bool ib = h.p1 > h.p0;
     if (ib) {
-        LaunchPriority urgent(ctx->prio_hi);
         ParticleArgs pa = particle_args(ctx, cur);
         pa.blk_base = h.b0;
         CK(launch_probes(ctx->prec, pa, h.b1 - h.b0, st));
@@ -829,12 +826,7 @@ lbm_status init_contexts(const lbm_config* cfgs, int n, lbm_ctx** out) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
     // a batch steps its instances in overlapped parts by default
-    if (n >= 2) {
-        int least = 0, greatest = 0;
-        cudaDeviceGetStreamPriorityRange(&least, &greatest);
-        ctx->prio_hi = greatest;
-        ctx->step_mode = LBM_STEP_OVERLAP;
-    }
+    if (n >= 2) ctx->step_mode = LBM_STEP_OVERLAP;
     if (ctx->sms < 1) ctx->sms = 1;
     std::vector<std::vector<Task>> tasks(N_FLUID_VARIANTS);
     for (int v = 0; v < N_FLUID_VARIANTS; ++v) tasks[v] = make_tasks(L.insts, v);
@@ -1400,12 +1392,7 @@ lbm_status lbm_set_step_mode(lbm_ctx* ctx, int32_t mode) {
     if (mode == ctx->step_mode) return LBM_OK;
     drop_graphs(ctx);
     ctx->step_mode = mode;
-    if (mode == LBM_STEP_OVERLAP) {
-        ctx->halves_dirty = true;
-        int least = 0, greatest = 0;
-        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-        ctx->prio_hi = greatest;
-    }
+    if (mode == LBM_STEP_OVERLAP) ctx->halves_dirty = true;
     if (mode == LBM_STEP_FUSED) {
         ctx->items_dirty = true;
         ctx->variant = fused_fluid_variant();
@@ -1689,6 +1676,9 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* ctx, int32_t nsteps, int32_t checkpoi
     if (ctx->step_mode == LBM_STEP_FUSED) return fail(ctx, LBM_EINVAL, "the adjoint does not run the fused step");
     for (const Inst& I : ctx->hinst)
         if (!I.G.px) return fail(ctx, LBM_EINVAL, "the adjoint needs periodic x sides (no x walls)");
+    for (const Inst& I : ctx->hinst)
+        if (9 * I.G.plane >= (long long)INT_MAX)
+            return fail(ctx, LBM_EINVAL, "the adjoint's lattices must hold fewer than 2^31 / 9 nodes each");
     return adjoint_run(ctx, nsteps, checkpoint_every, seed, dparticle, dwall);
 }
 

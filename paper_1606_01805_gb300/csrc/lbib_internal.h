@@ -149,16 +149,6 @@ struct SpreadArgs {
     int4 part_inline[INLINE_PARTICLES];  // the first np_inline entries of ptab
 };
 
-// Scheduling priority of the kernels this host thread launches through
-// launch_k (lbib_device.cuh) (0: the stream's own; lower is more urgent, as for streams), set
-// for a group of launches by a LaunchPriority guard.
-inline thread_local int tl_launch_priority = 0;
-struct LaunchPriority {
-    int old;
-    explicit LaunchPriority(int p) : old(tl_launch_priority) { tl_launch_priority = p; }
-    ~LaunchPriority() { tl_launch_priority = old; }
-};
-
 // One tile of a task list: instance, tile x, tile y (a tile being 32 * cpt
 // cells of by rows), and the instance's population offset and row geometry,
 // so that a kernel can address the tile's populations after one load.

@@ -169,7 +169,8 @@ def test_sensitivities_match_oracle_finite_differences():
         print(f"instance {idx[b]} p={P[b].tolist()}\n  tangent      {J[b].tolist()}\n"
               f"  FD switch-free {Jf[b].tolist()} steps {used[b].tolist()} switches {sw[b].tolist()}\n"
               f"  FD h=1e-4    {Jc[b].tolist()} switches {swc[b].tolist()}\n"
-              f"  scaled row error vs the switch-free differences: {err.tolist()}")
+              f"  scaled row error vs the switch-free differences: {err.tolist()}\n"
+              f"  per-entry relative error: {(np.abs(J[b] - Jf[b]) / np.maximum(np.abs(Jf[b]), 1e-300)).tolist()}")
         # values: the FP32 path against the FP64 oracle
         assert abs(vals[b, 0] - base[b, 0]) < 1e-3
         assert abs(vals[b, 1] - base[b, 1]) <= 1e-3 * abs(base[b, 1])
