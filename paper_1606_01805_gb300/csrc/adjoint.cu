@@ -710,9 +710,11 @@ __global__ void k_adj_zh(AdjArgs a, int ninst) {
 
 // the initial field f* = f^eq(1, u(y)) of the planar Couette profile
 // u(y) = ub + (ut - ub) y / H reversed: lambda of the two wall speeds
-// (instances whose blocks carry the Couette flag; summed per warp), with
-// lambda(f*(0)) from level 0's lambda(g) (streaming reversed)
+// (instances whose blocks carry the Couette flag), with lambda(f*(0)) from
+// level 0's lambda(g) (streaming reversed); summed per warp, then per
+// block, one atomic per block and value
 __global__ void k_adj_init(AdjArgs a) {
+    __shared__ double part[AB][4];
     const CellPos q = cell_pos(a);
     if (!(q.flags & 1)) return;  // the same for the whole block
     const Inst& I = *q.I;
@@ -734,10 +736,16 @@ __global__ void k_adj_init(AdjArgs a) {
         }
         const double db = warp_sum(d * (1.0 - t)), dt = warp_sum(d * t);
         if (threadIdx.x == 0) {
-            double* lw = a.lam_wall + ((long long)q.inst * 2 + o) * 8;
-            atomicAdd(lw + 2 * 2 + 0, db);
-            atomicAdd(lw + 3 * 2 + 0, dt);
+            part[threadIdx.y][2 * o] = db;
+            part[threadIdx.y][2 * o + 1] = dt;
         }
+    }
+    __syncthreads();
+    if (threadIdx.y == 0 && threadIdx.x < 4) {
+        double v = 0.0;
+        for (int w = 0; w < AB; ++w) v += part[w][threadIdx.x];
+        const int o = threadIdx.x >> 1, side = (threadIdx.x & 1) ? 3 : 2;
+        atomicAdd(a.lam_wall + ((long long)q.inst * 2 + o) * 8 + side * 2 + 0, v);
     }
 }
 
