@@ -507,8 +507,8 @@ __global__ void __launch_bounds__(64) k_adj_markers(AdjArgs a) {
         lgm[LG_S] += L.d[8];
         // node velocities: d L / d u_j = -S phi_j s_x (and s_y)
         float* lg = a.lam_g + o * a.pop_elems;
-#pragma unroll
-        for (int j = 0; j < 9; ++j) {
+#pragma unroll 1
+        for (int j = 0; j < 9; ++j) {  // (atomics: nothing to wait for; a loop keeps the code small)
             const float cj = -S.v * phi[j].v;
             scatter_moments(lg, I, nxk[j], nyk[j], 0.f, cj * sx.v, cj * sy.v, nr[j], nu[j], nv[j]);
         }
@@ -669,8 +669,8 @@ __global__ void __launch_bounds__(64) k_adj_probes(AdjArgs a) {
 #pragma unroll
         for (int q = 0; q < 5; ++q) lf[q] = f0 * Gx.d[q] + f1 * Gy.d[q] + f2 * GM.d[q];
         float* lg = a.lam_g + o * a.pop_elems;
-#pragma unroll
-        for (int kk = 0; kk < 9; ++kk) {
+#pragma unroll 1
+        for (int kk = 0; kk < 9; ++kk) {  // (atomics: nothing to wait for; a loop keeps the code small)
             const float ldr = phi[kk].v * lf[0];
             const float lu = dpx[kk].v * lf[1] + dpy[kk].v * lf[2];
             const float lv = dpx[kk].v * lf[3] + dpy[kk].v * lf[4];
@@ -720,21 +720,23 @@ __global__ void k_adj_init(AdjArgs a) {
     const Inst& I = *q.I;
     const int x = q.x, y = q.y;
     const bool in = x < I.G.nx && y < I.G.ny;
-    const double ub = I.G.uw[2][0], ut = I.G.uw[3][0], t = (double)y / (double)(I.G.ny - 1);
-    const double ux = ub + (ut - ub) * t;
+    // per cell in FP32 (this part's FP64 rate is a small fraction of its
+    // FP32 rate); the sums over cells in FP64
+    const float ub = I.G.uwf[2][0], ut = I.G.uwf[3][0], t = (float)y / (float)(I.G.ny - 1);
+    const float ux = ub + (ut - ub) * t;
     float lam[2][9];
     if (in) lam_post(a, I, q.inst, x, y, lam);
 #pragma unroll
     for (int o = 0; o < 2; ++o) {
-        double d = 0.0;  // sum_i lambda_i d feq_i / d ux at rho = 1, uy = 0
+        float d = 0.f;  // sum_i lambda_i d feq_i / d ux at rho = 1, uy = 0
         if (in) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const double ex = cx(i);
-                d += lam[o][i] * wt(i) * (3.0 * ex + 9.0 * ex * ex * ux - 3.0 * ux);
+                const float ex = (float)cx(i);
+                d += lam[o][i] * (float)wt(i) * (3.f * ex + 9.f * ex * ex * ux - 3.f * ux);
             }
         }
-        const double db = warp_sum(d * (1.0 - t)), dt = warp_sum(d * t);
+        const double db = warp_sum((double)(d * (1.f - t))), dt = warp_sum((double)(d * t));
         if (threadIdx.x == 0) {
             part[threadIdx.y][2 * o] = db;
             part[threadIdx.y][2 * o + 1] = dt;
