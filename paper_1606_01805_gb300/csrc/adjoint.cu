@@ -254,8 +254,8 @@ __global__ void __launch_bounds__(32 * AB, 3) k_adj_cells(AdjArgs a) {
         forced = a.flags[I.flags_off + seg] != 0;
         float Fx = I.G.gf[0], Fy = I.G.gf[1];
         if (forced) {
-            Fx += a.flb[I.flb_off + c];
-            Fy += a.flb[I.flb_off + plane + c];
+            Fx += ForceField<float>::get(a.flb[I.flb_off + c]);
+            Fy += ForceField<float>::get(a.flb[I.flb_off + plane + c]);
         }
         // at a y wall node x + e_i, what the Zou-He unknowns owe the known
         // populations (the transposes of k_adj_zh)
@@ -327,8 +327,8 @@ __global__ void __launch_bounds__(32 * AB, 3) k_adj_cells(AdjArgs a) {
         }
     }
     if (forced) {
-        a.flb[I.flb_off + c] = 0.f;
-        a.flb[I.flb_off + plane + c] = 0.f;
+        a.flb[I.flb_off + c] = 0;
+        a.flb[I.flb_off + plane + c] = 0;
     }
     __syncwarp();  // every lane has read the segment's flag
     if (forced && (x & 31) == 0) a.flags[I.flags_off + seg] = 0;

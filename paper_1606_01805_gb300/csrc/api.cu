@@ -232,7 +232,7 @@ Layout layout(const lbm_config* cfgs, int n) {
     size_t o = 0;
     L.f0 = o; o = up(o + fe * storage_bytes(prec));
     L.f1 = o; o = up(o + fe * storage_bytes(prec));
-    L.flb = o; o = up(o + fle * compute_bytes(prec));
+    L.flb = o; o = up(o + fle * force_bytes(prec));
     L.flags = o; o = up(o + fge);
     L.insts_off = o; o = up(o + n * sizeof(Inst));
     for (int v = 0; v < N_FLUID_VARIANTS; ++v) {
@@ -323,6 +323,8 @@ ParticleArgs particle_args(lbm_ctx* ctx, int cur) {
     pa.S = ctx->S;
     pa.recs = ctx->recs;
     pa.boxes = ctx->boxes;
+    pa.flb = ctx->flb;
+    pa.flags = ctx->flags;
     pa.err = ctx->err;
     pa.weight = ctx->cfg.weight;
     pa.blk_base = 0;
@@ -548,9 +550,11 @@ lbm_status enqueue_half(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t step, co
         pa.blk_base = h.b0;
         CK(launch_probes(ctx->prec, pa, h.b1 - h.b0, st));
         CK(launch_markers(ctx->prec, pa, h.b1 - h.b0, st));
-        SpreadArgs sa = spread_args(ctx, pa);
-        sa.p_base = h.p0;
-        CK(launch_spread(ctx->prec, sa, h.p1 - h.p0, spread_tiles(ctx), st));
+        if (!markers_spread(ctx->prec)) {
+            SpreadArgs sa = spread_args(ctx, pa);
+            sa.p_base = h.p0;
+            CK(launch_spread(ctx->prec, sa, h.p1 - h.p0, spread_tiles(ctx), st));
+        }
     }
     const int v = ctx->variant;
     if (h.t1[v] <= h.t0[v]) return LBM_OK;
@@ -570,7 +574,8 @@ lbm_status enqueue_step_part(lbm_ctx* ctx, cudaStream_t st, int cur, int64_t ste
     const ParticleArgs pa = particle_args(ctx, cur);
     CK(launch_probes(ctx->prec, pa, ctx->nblk, st));
     CK(launch_markers(ctx->prec, pa, ctx->nblk, st));
-    CK(launch_spread(ctx->prec, spread_args(ctx, pa), ctx->np, spread_tiles(ctx), st));
+    if (!markers_spread(ctx->prec))
+        CK(launch_spread(ctx->prec, spread_args(ctx, pa), ctx->np, spread_tiles(ctx), st));
     return LBM_OK;
 }
 
@@ -1544,7 +1549,7 @@ lbm_status adjoint_run(lbm_ctx* ctx, int nsteps, int K, const double* seed, doub
     double *lp_new = q.lp_a, *lp_old = q.lp_b;
     AdjArgs a;
     std::memset(&a, 0, sizeof a);
-    a.flb = static_cast<float*>(ctx->flb);
+    a.flb = static_cast<long long*>(ctx->flb);
     a.flags = ctx->flags;
     a.insts = ctx->insts;
     a.mgeo = q.mgeo;
@@ -1756,7 +1761,8 @@ extern "C" lbm_status lbm_step_static(lbm_ctx* ctx, int32_t nsteps) {
             pa.boxes = reinterpret_cast<int4*>(sb + o_boxes);
             CK(launch_probes(ctx->prec, pa, ctx->nblk, ctx->stream));
             CK(launch_markers(ctx->prec, pa, ctx->nblk, ctx->stream));
-            CK(launch_spread(ctx->prec, spread_args(ctx, pa), ctx->np, spread_tiles(ctx), ctx->stream));
+            if (!markers_spread(ctx->prec))
+                CK(launch_spread(ctx->prec, spread_args(ctx, pa), ctx->np, spread_tiles(ctx), ctx->stream));
         }
         lbm_status s = launch_fluid_step(ctx, ctx->stream, ctx->cur, ctx->variant, ctx->np > 0,
                                          watched(ctx, ctx->steps));

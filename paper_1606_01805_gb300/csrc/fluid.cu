@@ -97,6 +97,14 @@ size_t storage_bytes(int prec) {
         default: return sizeof(TF);
     }
 }
+// bytes of one force-field value (the fixed point of ForceField for the
+// FP32 compute type)
+size_t force_bytes(int prec) {
+    return prec == LBM_FP32 || prec == LBM_FP16_SHIFTED ? sizeof(long long) : compute_bytes(prec);
+}
+
+bool markers_spread(int prec) { return prec == LBM_FP32 || prec == LBM_FP16_SHIFTED; }
+
 size_t compute_bytes(int prec) {
     return prec == LBM_FP64 ? sizeof(double) : (prec == LBM_FP32_TANGENT ? sizeof(TF) : sizeof(float));
 }

@@ -230,14 +230,14 @@ struct PdlWait {
 // The forces of this thread's cells when its segment is flagged (zero
 // otherwise); the field is cleared for the next step after the tile.
 template <class C, int N>
-__device__ __forceinline__ void load_forces(bool forced, const C* flb, long long row, long long plane, int x0,
-                                            int nx, C fx[N], C fy[N]) {
+__device__ __forceinline__ void load_forces(bool forced, const ForceT<C>* flb, long long row, long long plane,
+                                            int x0, int nx, C fx[N], C fy[N]) {
     if (!forced) return;
 #pragma unroll
     for (int k = 0; k < N; ++k)
         if (x0 + k < nx) {
-            fx[k] = flb[row + x0 + k];
-            fy[k] = flb[plane + row + x0 + k];
+            fx[k] = ForceField<C>::get(flb[row + x0 + k]);
+            fy[k] = ForceField<C>::get(flb[plane + row + x0 + k]);
         }
 }
 
@@ -292,7 +292,7 @@ __device__ __forceinline__ void pulled_plane(int i, const C q[N], C bnd, C wl, i
 // the periodic patch and the per-cell general path read fin itself.
 template <class S, class C, int N, class Src, class Wait>
 __device__ __forceinline__ void fluid_tile(const Src& src, const Geo& G, const S* __restrict__ fin,
-                                           S* __restrict__ fout, C* __restrict__ flb,
+                                           S* __restrict__ fout, ForceT<C>* __restrict__ flb,
                                            uint8_t* __restrict__ flags, int tx, int y, int check,
                                            unsigned* err, int keep, const Wait& wait) {
     constexpr bool PDL = Wait::LATE;
@@ -464,8 +464,8 @@ __device__ __forceinline__ void fluid_tile(const Src& src, const Geo& G, const S
 #pragma unroll
         for (int k = 0; k < N; ++k)
             if (x0 + k < G.nx) {
-                flb[row + x0 + k] = C(0);
-                flb[G.plane + row + x0 + k] = C(0);
+                flb[row + x0 + k] = ForceT<C>(0);
+                flb[G.plane + row + x0 + k] = ForceT<C>(0);
             }
     }
     __syncwarp();

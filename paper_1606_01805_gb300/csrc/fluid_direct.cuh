@@ -32,7 +32,7 @@ template <class S, class C, int N, int BYt>
 __global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value) k_fluid(FluidArgs a) {
     const S* fin = static_cast<const S*>(a.fin);
     S* fout = static_cast<S*>(a.fout);
-    C* flb = static_cast<C*>(a.flb);
+    ForceT<C>* flb = static_cast<ForceT<C>*>(a.flb);
     for (int t0 = blockIdx.x * TASKS_PER_CTA; t0 < a.ntasks; t0 += gridDim.x * TASKS_PER_CTA)
     for (int t = t0; t < min(t0 + TASKS_PER_CTA, a.ntasks); ++t) {
         const Task task = a.tasks[t];
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(32 * BYt, FluidOccupancy<S, N, BYt>::value)
     const S* fin = static_cast<const S*>(a.fin) + I.f_off;
     using Wait = typename std::conditional<PDL, PdlWait, NoWait>::type;
     fluid_tile<S, C, N>(global_src<S, C, N>(fin, I.G), I.G, fin, static_cast<S*>(a.fout) + I.f_off,
-                        static_cast<C*>(a.flb) + I.flb_off, a.flags + I.flags_off, blockIdx.x,
+                        static_cast<ForceT<C>*>(a.flb) + I.flb_off, a.flags + I.flags_off, blockIdx.x,
                         blockIdx.y * BYt + threadIdx.y, a.check, a.err, a.keep, Wait{});
 }
 

@@ -193,13 +193,13 @@ __global__ void __launch_bounds__(STHREADS, 2)
         if constexpr (ONE) {
             const S* fin = static_cast<const S*>(a.fin) + one.f_off;
             fluid_tile<S, C, N>(src, one.G, fin, static_cast<S*>(a.fout) + one.f_off,
-                                       static_cast<C*>(a.flb) + one.flb_off, a.flags + one.flags_off, tk.y,
+                                       static_cast<ForceT<C>*>(a.flb) + one.flb_off, a.flags + one.flags_off, tk.y,
                                        y0 + warp, a.check, a.err, a.keep, NoWait{});
         } else {
             const Inst& I = sinst[s];
             const S* fin = static_cast<const S*>(a.fin) + I.f_off;
             fluid_tile<S, C, N>(src, I.G, fin, static_cast<S*>(a.fout) + I.f_off,
-                                       static_cast<C*>(a.flb) + I.flb_off, a.flags + I.flags_off, tk.y,
+                                       static_cast<ForceT<C>*>(a.flb) + I.flb_off, a.flags + I.flags_off, tk.y,
                                        y0 + warp, a.check, a.err, a.keep, NoWait{});
         }
         __syncthreads();  // stage s is free again

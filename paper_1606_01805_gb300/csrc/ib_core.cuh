@@ -497,16 +497,47 @@ __device__ __forceinline__ void marker_block(const ParticleArgs& a, int blk, uns
         const C Sl = static_cast<const C*>(a.S)[m];
         const C sx = Sl * ((BU - BW * ry) - ux);
         const C sy = Sl * ((BV + BW * rx) - uy);
-        Rec<C>* rc = recs + m;
+        if constexpr (!FUSED && ForceField<C>::FIXED) {
+            // Eq. 12 added straight into the fixed-point force field: each
+            // lane its support nodes (no records, no spreading kernel)
+            using FF = ForceField<C>;
+            ForceT<C>* flb = static_cast<ForceT<C>*>(a.flb) + I.flb_off;
+            uint8_t* flags = a.flags + I.flags_off;
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
-            if (j < M.nk) {
-                rc->cx[M.kk[j]] = M.phi[j] * sx;
-                rc->cy[M.kk[j]] = M.phi[j] * sy;
+            for (int j = 0; j < 3; ++j)
+                if (j < M.nk) {
+                    const int k = M.kk[j];
+                    int gx = M.i0 + k % 3, gy = M.j0 + k / 3;
+                    bool in = true;
+                    if (gx < 0 || gx >= G.nx) {
+                        if (G.px) gx = ((gx % G.nx) + G.nx) % G.nx;
+                        else in = false;
+                    }
+                    if (gy < 0 || gy >= G.ny) {
+                        if (G.py) gy = ((gy % G.ny) + G.ny) % G.ny;
+                        else in = false;
+                    }
+                    if (in) {
+                        const long long c = (long long)gy * G.pitch + gx;
+                        FF::add(flb + c, FF::fix(M.phi[j] * sx));
+                        FF::add(flb + G.plane + c, FF::fix(M.phi[j] * sy));
+                        flags[gy * G.nseg + (gx >> 5)] = 1;
+                    }
+                }
+        } else {
+            Rec<C>* rc = recs + m;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (j < M.nk) {
+                    rc->cx[M.kk[j]] = M.phi[j] * sx;
+                    rc->cy[M.kk[j]] = M.phi[j] * sy;
+                }
+            if (q == 0) {
+                rc->i0 = M.i0;
+                rc->j0 = M.j0;
             }
+        }
         if (q == 0) {
-            rc->i0 = M.i0;
-            rc->j0 = M.j0;
             bx0 = M.i0;
             by0 = M.j0;
             bx1 = M.i0 + 2;
@@ -565,7 +596,8 @@ __device__ __forceinline__ void spread_tile(const SpreadArgs& a, int tile, int p
     const Inst& I = inst_of<ONE>(a, pr.z);
     const Geo& G = I.G;
     const Rec<C>* recs = static_cast<const Rec<C>*>(a.recs);
-    C* flb = static_cast<C*>(a.flb) + I.flb_off;
+    using FF = ForceField<C>;
+    ForceT<C>* flb = static_cast<ForceT<C>*>(a.flb) + I.flb_off;
     uint8_t* flags = a.flags + I.flags_off;
     constexpr int NW = TX * TY / 32;
     Rec<C>* list = sm.list;
@@ -582,7 +614,7 @@ __device__ __forceinline__ void spread_tile(const SpreadArgs& a, int tile, int p
     const int x0 = box.x + (tile % ntx) * TX, y0 = box.y + (tile / ntx) * TY;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int cxl = x0 + t % TX, cyl = y0 + t / TX;  // this thread's (unwrapped) cell
-    C ax = C(0), ay = C(0);
+    ForceT<C> ax = ForceT<C>(0), ay = ForceT<C>(0);  // (fixed point: each contribution rounded, then summed)
     bool touched = false;
     for (int base = 0; base < nm; base += CAP) {
         // thread t examines records base + t (slot 0) and base + TX TY + t
@@ -635,8 +667,13 @@ __device__ __forceinline__ void spread_tile(const SpreadArgs& a, int tile, int p
                 bits &= bits - 1u;
                 const int da = cxl - rc.i0, db = cyl - rc.j0;
                 if (da >= 0 && da < 3) {
-                    ax += rc.cx[db * 3 + da];
-                    ay += rc.cy[db * 3 + da];
+                    if constexpr (FF::FIXED) {
+                        ax += FF::fix(rc.cx[db * 3 + da]);
+                        ay += FF::fix(rc.cy[db * 3 + da]);
+                    } else {
+                        ax += rc.cx[db * 3 + da];
+                        ay += rc.cy[db * 3 + da];
+                    }
                     touched = true;
                 }
             }
@@ -654,8 +691,13 @@ __device__ __forceinline__ void spread_tile(const SpreadArgs& a, int tile, int p
         gy = ((gy % G.ny) + G.ny) % G.ny;
     }
     const long long c = (long long)gy * G.pitch + gx;
-    atomicAdd(flb + c, ax);
-    atomicAdd(flb + G.plane + c, ay);
+    if constexpr (FF::FIXED) {
+        FF::add(flb + c, ax);
+        FF::add(flb + G.plane + c, ay);
+    } else {
+        atomicAdd(flb + c, ax);
+        atomicAdd(flb + G.plane + c, ay);
+    }
     flags[gy * G.nseg + (gx >> 5)] = 1;
 }
 

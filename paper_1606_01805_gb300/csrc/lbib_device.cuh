@@ -37,6 +37,31 @@ cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, 
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// ------------------------------------------------------------ force field ----
+// The IB force field of Eq. 12.  With the FP32 compute type (FP32 and
+// FP16-shifted storage) it is held in fixed point, units of 2^-40 in a
+// 64-bit integer: every marker's contribution is rounded to that grid once
+// and added with an integer atomic, so the sum is the same bits whatever
+// the order of the additions (and whether markers add directly or a
+// spreading tile gathers them first).  The other compute types keep the
+// field in that type (their spreading tiles gather per cell in marker
+// order and add one sum per cell and particle).
+template <class C> struct ForceField {
+    using T = C;
+    static constexpr bool FIXED = false;
+    __device__ __forceinline__ static C get(const T& v) { return v; }
+};
+template <> struct ForceField<float> {
+    using T = long long;
+    static constexpr bool FIXED = true;
+    __device__ __forceinline__ static float get(long long v) { return (float)v * 0x1p-40f; }
+    __device__ __forceinline__ static long long fix(float v) { return __float2ll_rn(v * 0x1p40f); }
+    __device__ __forceinline__ static void add(long long* p, long long v) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+    }
+};
+template <class C> using ForceT = typename ForceField<C>::T;
+
 // ---------------------------------------------------------------- D2Q9 ----
 // Velocities of Eq. 3: e_0 rest, e_1..e_4 axes at angles (i-1) pi/2,
 // e_5..e_8 diagonals at (2i-9) pi/4; weights 4/9, 1/9, 1/36.

@@ -123,6 +123,8 @@ struct ParticleArgs {
     const void* S;            // C: marker arc lengths
     void* recs;               // Rec<C>[max_markers]
     int4* boxes;              // per particle: support box (x0, y0, x1, y1)
+    void* flb;                // force field and its flags: the marker kernel spreads into them
+    uint8_t* flags;           // directly when the field is fixed point (ForceField)
     unsigned* err;
     int weight;
     int blk_base;             // marker block of the kernels' first CTA (a range of the table)
@@ -227,7 +229,7 @@ struct FusedArgs {
 // flb_elems, indexed like the force field.
 struct AdjArgs {
     const float* f;            // f*(n) (stored shifted populations of level n)
-    float* flb;                // the step's force field (recomputed), cleared at the end
+    long long* flb;            // the step's force field (recomputed; fixed point), cleared at the end
     uint8_t* flags;            // its flags, cleared at the end
     const Inst* insts;
     const DParticle* Pn;       // P(n)
@@ -314,6 +316,11 @@ cudaError_t launch_markers(int prec, const ParticleArgs& a, int nblocks, cudaStr
 cudaError_t launch_spread(int prec, const SpreadArgs& a, int np, int tiles, cudaStream_t s);
 size_t storage_bytes(int prec);
 size_t compute_bytes(int prec);
+size_t force_bytes(int prec);
+// the precisions whose marker kernel adds the spreading (Eq. 12) straight
+// into the fixed-point force field, with no spreading kernel in the
+// separate step (the fused step still gathers by tiles, to the same bits)
+bool markers_spread(int prec);
 size_t rec_bytes(int prec);
 size_t real_bytes(int prec);      // the particle real type R
 size_t particle_bytes(int prec);  // sizeof(DParticleT<R>)

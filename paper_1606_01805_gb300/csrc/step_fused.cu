@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_step_fused(FusedArgs f) {
                 const GlobalSrc<S, C, FUSED_CPT> src{fin, (long long)task.pitch * task.ny, task.pitch, task.ny};
                 const SpreadWait w{k.sdone + it.z, target, f.wait_limit, f.fa.err, k.abort};
                 fluid_tile<S, C, FUSED_CPT>(src, I.G, fin, static_cast<S*>(f.fa.fout) + task.f_off,
-                                            static_cast<C*>(f.fa.flb) + I.flb_off, f.fa.flags + I.flags_off,
+                                            static_cast<ForceT<C>*>(f.fa.flb) + I.flb_off, f.fa.flags + I.flags_off,
                                             task.tx, task.ty * FUSED_TY + warp, f.fa.check, f.fa.err, 0, w);
                 break;
             }
