@@ -15,6 +15,12 @@
  *      (Eqs. 8-10), direct-forcing marker force (Eq. 11), spreading of the
  *      marker forces to the lattice (Eq. 12);
  *   5. BGK collision with the Guo forcing term (Eqs. 2, 4, 5).
+ * With the FP32 compute type (LBM_FP32, LBM_FP16_SHIFTED) the force field
+ * of step 4 is held in fixed point (units of 2^-40 in 64-bit integers):
+ * each marker adds its contributions straight into it with integer atomics,
+ * so the result does not depend on the order of the additions.  LBM_FP64
+ * and the tangent mode gather the contributions per cell in marker order
+ * (a spreading kernel) and keep the field in their compute type.
  *
  * Conventions shared by every call:
  *  - Lattice units: dx = dt = 1.  Nodes (x, y), 0 <= x < nx, 0 <= y < ny.
@@ -177,8 +183,8 @@ lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps);
  * the steps (ms) to *ms_step and of the stream-collide launches to
  * *ms_fluid (either may be NULL).  With ms_fluid NULL no event sits before
  * the stream-collide launch, which may then start its population loads
- * while the spreading kernel finishes, as in lbm_step; with ms_fluid it
- * starts after the spreading kernel, so that its time is its own.
+ * while the immersed-boundary kernel before it finishes, as in lbm_step;
+ * with ms_fluid it starts after that kernel, so that its time is its own.
  */
 lbm_status lbm_step_timed(lbm_ctx* ctx, int32_t nsteps, double* ms_step, double* ms_fluid);
 
@@ -353,8 +359,8 @@ lbm_status lbm_set_tile(lbm_ctx* ctx, int32_t variant);
 /*
  * Step mode of a batch.  LBM_STEP_SEPARATE (the mode of a single lattice):
  * each step is the immersed-boundary kernels (probes and rigid update,
- * markers, spreading) and then the fluid kernel, each one launch over all
- * instances.
+ * markers, and the spreading kernel in LBM_FP64 and the tangent mode) and
+ * then the fluid kernel, each one launch over all instances.
  * LBM_STEP_OVERLAP (the default of a batch of two or more instances): the
  * instances are split into two halves of about equal
  * cell count, and lbm_step's captured runs of steps advance each half with
