@@ -298,10 +298,10 @@ __device__ __forceinline__ void fluid_tile(const Src& src, const Geo& G, const S
     constexpr bool PDL = Wait::LATE;
     const int lane = threadIdx.x & 31;
     const int x0 = (tx * 32 + lane) * N;
-    // (FP32 vector tiles take the row count and pitch from the source, so
-    // that their loads need no descriptor load; the others from G, which
-    // measured faster for them on GB300)
-    constexpr bool HOIST = sizeof(S) == 4 && N >= 2;
+    // (FP32 and FP16 vector tiles take the row count and pitch from the
+    // source, so that their loads need no descriptor load; the others from
+    // G, which measured faster for them on GB300)
+    constexpr bool HOIST = (sizeof(S) == 4 || sizeof(S) == 2) && N >= 2;
     if (y >= (HOIST ? src.ny : G.ny)) return;  // whole warp (one row)
     const long long row = (long long)y * G.pitch;
     // the vector values of cell x0 + k are its pulled populations whenever
@@ -320,11 +320,12 @@ __device__ __forceinline__ void fluid_tile(const Src& src, const Geo& G, const S
     const int ke = G.nx - 1 - x0;  // position of x = nx - 1 in this thread's cells
     const bool wrap_l = wrap && x0 == 0, wrap_r = wrap && ke >= 0 && ke < N;
     // Two load orders, chosen per storage type and width by measurement on
-    // GB300: FP32 vectors of two or four cells issue every population load
-    // and the force loads of a flagged segment before consuming any (the
-    // flag -> force chain then overlaps the population loads); FP16, FP64
-    // and one-cell tiles load and shuffle plane by plane and read the forces
-    // after the populations (fewer live registers).
+    // GB300: FP32 and FP16 vectors of two or four cells issue every
+    // population load and the force loads of a flagged segment before
+    // consuming any (the flag -> force chain then overlaps the population
+    // loads; the 512-lattice batch in FP16 storage 0.946 -> 0.902 ms per
+    // step); FP64 and one-cell tiles load and shuffle plane by plane and
+    // read the forces after the populations (fewer live registers).
     if constexpr (HOIST) {
         C q[9][N], bnd[9], wl[9];
 #pragma unroll
