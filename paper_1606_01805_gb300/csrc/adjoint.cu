@@ -21,10 +21,13 @@
 //                marker geometry;
 //  k_adj_rigid   per particle: the two-level update of Eqs. 15-16 reversed
 //                -> lambda of the old state, of F and M;
-//  k_adj_probes  per marker: the probe stress and surface integrals of
-//                Eqs. 13-14 reversed -> lambda of the node density and
-//                velocities at the probe supports, of the old pose and of
-//                the marker geometry;
+//  k_adj_probes_pre / _fin  per marker: the probe stress and surface
+//                integrals of Eqs. 13-14 reversed -> lambda of the node
+//                density and velocities at the probe supports, of the old
+//                pose and of the marker geometry.  Their Jacobians do not
+//                depend on any adjoint: _pre forms them (on a second stream,
+//                beside the kernels above), _fin contracts them with the
+//                force and torque adjoint of k_adj_rigid;
 // The markers' and probes' shares of lambda(g(n)) are added before the
 // next (earlier) level's k_adj_cells reads it.  The cell kernels walk one
 // list of blocks over all instances of a batch.
@@ -575,12 +578,12 @@ __device__ __forceinline__ void traction(const T& dr, const T& uxx, const T& uxy
     M = (rx * ty - ry * tx) * S;
 }
 
-// k_adj_probes: one thread per marker; the probes of the step (the body at
+// k_adj_probes_pre: one thread per marker; the probes of the step (the body at
 // level n with its previous level, the fluid at level n).  Positions are
 // relative to the node at or below the centre; duals over (X0, Y0, th0,
 // th1, U0, V0, U1, V1, W0, W1, rbx, rby, nbx, nby, S) in FP32, the MLS fits
 // through their gradients in the probe position.
-__global__ void __launch_bounds__(64) k_adj_probes(AdjArgs a) {
+__global__ void __launch_bounds__(64) k_adj_probes_pre(AdjArgs a) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= a.nmark) return;
     const int p = a.marker_particle[l];
@@ -622,6 +625,8 @@ __global__ void __launch_bounds__(64) k_adj_probes(AdjArgs a) {
         nu[k] = ux;
         nv[k] = uy;
     }
+    ProbePre& pp = a.ppre[l];
+    pp.ok = ok ? 1 : 0;
     if (!ok) {
         atomicOr(a.err, ERR_DOMAIN);
         return;
@@ -642,39 +647,79 @@ __global__ void __launch_bounds__(64) k_adj_probes(AdjArgs a) {
     F5 Gx, Gy, GM;
     traction<F5>(f5[0], f5[1], f5[2], f5[3], f5[4], F5(nx.v), F5(ny.v), F5(rx.v), F5(ry.v), F5(dvx.v), F5(dvy.v),
                  F5(S.v), tau, Gx, Gy, GM);
+    // what the finishing kernel needs, none of it depending on the adjoint
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+        pp.jF[0][k] = Fx.d[k];
+        pp.jF[1][k] = Fy.d[k];
+        pp.jF[2][k] = M.d[k];
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        pp.jG[0][q] = Gx.d[q];
+        pp.jG[1][q] = Gy.d[q];
+        pp.jG[2][q] = GM.d[q];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        pp.w[0][k] = phi[k].v;
+        pp.w[1][k] = dpx[k].v;
+        pp.w[2][k] = dpy[k].v;
+        pp.nf[0][k] = nd[k];
+        pp.nf[1][k] = nu[k];
+        pp.nf[2][k] = nv[k];
+        pp.node[0][k] = nxk[k];
+        pp.node[1][k] = nyk[k];
+    }
+}
+
+// k_adj_probes_fin: one thread per marker, after k_adj_rigid: the probe
+// Jacobians of k_adj_probes_pre contracted with the adjoint of the force
+// and torque -> lambda of the old pose, of the marker geometry and, through
+// the fits, of the node density and velocities
+__global__ void __launch_bounds__(64) k_adj_probes_fin(AdjArgs a) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= a.nmark) return;
+    const ProbePre& pp = a.ppre[l];
+    if (!pp.ok) return;
+    const int p = a.marker_particle[l];
+    const Inst& I = a.insts[a.ptab[p].z];
 #pragma unroll
     for (int o = 0; o < 2; ++o) {
         const double* fm = a.lamFM + ((long long)p * 2 + o) * 3;
         const float f0 = (float)fm[0], f1 = (float)fm[1], f2 = (float)fm[2];
-        const F15 L = f0 * Fx + f1 * Fy + f2 * M;
+        float L[15];
+#pragma unroll
+        for (int k = 0; k < 15; ++k) L[k] = f0 * pp.jF[0][k] + f1 * pp.jF[1][k] + f2 * pp.jF[2][k];
         double* lp = a.lamP_old + ((long long)p * 2 + o) * LP_N;
-        atomicAdd(lp + LX0, (double)L.d[0]);
-        atomicAdd(lp + LY0, (double)L.d[1]);
-        atomicAdd(lp + LT0, (double)L.d[2]);
-        atomicAdd(lp + LT1, (double)L.d[3]);
-        atomicAdd(lp + LU0, (double)L.d[4]);
-        atomicAdd(lp + LV0, (double)L.d[5]);
-        atomicAdd(lp + LU1, (double)L.d[6]);
-        atomicAdd(lp + LV1, (double)L.d[7]);
-        atomicAdd(lp + LW0, (double)L.d[8]);
-        atomicAdd(lp + LW1, (double)L.d[9]);
+        atomicAdd(lp + LX0, (double)L[0]);
+        atomicAdd(lp + LY0, (double)L[1]);
+        atomicAdd(lp + LT0, (double)L[2]);
+        atomicAdd(lp + LT1, (double)L[3]);
+        atomicAdd(lp + LU0, (double)L[4]);
+        atomicAdd(lp + LV0, (double)L[5]);
+        atomicAdd(lp + LU1, (double)L[6]);
+        atomicAdd(lp + LV1, (double)L[7]);
+        atomicAdd(lp + LW0, (double)L[8]);
+        atomicAdd(lp + LW1, (double)L[9]);
         double* lgm = a.lam_mgeo + ((long long)l * 2 + o) * LG_N;
-        lgm[LG_RX] += L.d[10];
-        lgm[LG_RY] += L.d[11];
-        lgm[LG_NX] += L.d[12];
-        lgm[LG_NY] += L.d[13];
-        lgm[LG_S] += L.d[14];
+        lgm[LG_RX] += L[10];
+        lgm[LG_RY] += L[11];
+        lgm[LG_NX] += L[12];
+        lgm[LG_NY] += L[13];
+        lgm[LG_S] += L[14];
         // the node values through the fits (linear in them)
         float lf[5];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) lf[q] = f0 * Gx.d[q] + f1 * Gy.d[q] + f2 * GM.d[q];
+        for (int q = 0; q < 5; ++q) lf[q] = f0 * pp.jG[0][q] + f1 * pp.jG[1][q] + f2 * pp.jG[2][q];
         float* lg = a.lam_g + o * a.pop_elems;
 #pragma unroll 1
         for (int kk = 0; kk < 9; ++kk) {  // (atomics: nothing to wait for; a loop keeps the code small)
-            const float ldr = phi[kk].v * lf[0];
-            const float lu = dpx[kk].v * lf[1] + dpy[kk].v * lf[2];
-            const float lv = dpx[kk].v * lf[3] + dpy[kk].v * lf[4];
-            scatter_moments(lg, I, nxk[kk], nyk[kk], ldr, lu, lv, 1.f + nd[kk], nu[kk], nv[kk]);
+            const float ldr = pp.w[0][kk] * lf[0];
+            const float lu = pp.w[1][kk] * lf[1] + pp.w[2][kk] * lf[2];
+            const float lv = pp.w[1][kk] * lf[3] + pp.w[2][kk] * lf[4];
+            scatter_moments(lg, I, pp.node[0][kk], pp.node[1][kk], ldr, lu, lv, 1.f + pp.nf[0][kk], pp.nf[1][kk],
+                            pp.nf[2][kk]);
         }
     }
 }
@@ -764,7 +809,16 @@ cudaError_t launch_adjoint_step(const AdjArgs& a, cudaStream_t s) {
     k_adj_cells<<<a.ncblk, dim3(32, AB), 0, s>>>(a);
     if (a.nmark > 0) k_adj_markers<<<(a.nmark + 63) / 64, 64, 0, s>>>(a);
     if (a.np > 0) k_adj_rigid<<<(a.np + 63) / 64, 64, 0, s>>>(a);
-    if (a.nmark > 0) k_adj_probes<<<(a.nmark + 63) / 64, 64, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_probes_pre(const AdjArgs& a, cudaStream_t s) {
+    if (a.nmark > 0) k_adj_probes_pre<<<(a.nmark + 63) / 64, 64, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_probes_fin(const AdjArgs& a, cudaStream_t s) {
+    if (a.nmark > 0) k_adj_probes_fin<<<(a.nmark + 63) / 64, 64, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -1471,6 +1471,7 @@ lbm_status adjoint_run(lbm_ctx* ctx, int nsteps, int K, const double* seed, doub
             double *lp_a, *lp_b, *lfm, *lsh, *lmg, *lwall, *mgeo;
             int* mpart;
             float* zh;
+            ProbePre* ppre;
             int4* cblk;
         } q;
         q.ckf = mm.take<char>(nck * popb);
@@ -1494,6 +1495,7 @@ lbm_status adjoint_run(lbm_ctx* ctx, int nsteps, int K, const double* seed, doub
         q.mgeo = mm.take<double>((size_t)nm * 5);
         q.mpart = mm.take<int>(nm);
         q.zh = mm.take<float>((size_t)ni * 2 * 81);
+        q.ppre = mm.take<ProbePre>(nm);
         q.cblk = mm.take<int4>(cblk.size());
         return q;
     };
@@ -1566,10 +1568,27 @@ lbm_status adjoint_run(lbm_ctx* ctx, int nsteps, int K, const double* seed, doub
     a.lam_mgeo = q.lmg;
     a.lam_wall = q.lwall;
     a.zh = q.zh;
+    a.ppre = q.ppre;
     a.cblk = q.cblk;
     a.ncblk = (int)cblk.size();
     a.err = ctx->err;
     CK(launch_adjoint_setup(a, ni, st));
+    // a side stream for the probe Jacobians of each reverse level
+    struct Side {
+        cudaStream_t s = nullptr;
+        cudaEvent_t fork = nullptr, join = nullptr;
+        ~Side() {
+            if (s) {
+                cudaStreamSynchronize(s);
+                cudaStreamDestroy(s);
+            }
+            if (fork) cudaEventDestroy(fork);
+            if (join) cudaEventDestroy(join);
+        }
+    } side;
+    CK(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&side.fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&side.join, cudaEventDisableTiming));
     for (int c = nck - 1; c >= 0; --c) {
         const int n0 = c * K, mseg = std::min(K, nsteps - n0);
         if ((s = load(q.ckf + c * popb, q.cks + c * partb, q.ckp + c * poseb)) != LBM_OK) return s;
@@ -1601,7 +1620,15 @@ lbm_status adjoint_run(lbm_ctx* ctx, int nsteps, int K, const double* seed, doub
             a.lam_g = lam_g;
             a.lamP_new = lp_new;
             a.lamP_old = lp_old;
+            // the probe Jacobians on the side stream, beside the cell, marker
+            // and rigid-update kernels; joined before the probes finish
+            CK(cudaEventRecord(side.fork, st));
+            CK(cudaStreamWaitEvent(side.s, side.fork, 0));
+            CK(launch_adjoint_probes_pre(a, side.s));
+            CK(cudaEventRecord(side.join, side.s));
             CK(launch_adjoint_step(a, st));
+            CK(cudaStreamWaitEvent(st, side.join, 0));
+            CK(launch_adjoint_probes_fin(a, st));
             std::swap(lam_gp, lam_g);
             std::swap(lp_new, lp_old);
             CK(cudaMemsetAsync(lp_old, 0, (size_t)np * 2 * ADJ_LP * sizeof(double), st));

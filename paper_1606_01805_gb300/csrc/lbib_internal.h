@@ -227,6 +227,16 @@ struct FusedArgs {
 // population buffer (FP32), one per output, pop_elems apart; lam_F holds
 // the force adjoint of flagged cells, [output][component] blocks of
 // flb_elems, indexed like the force field.
+// per marker, the probe Jacobians of one reverse level (adjoint.cu):
+// d(F_x, F_y, M)/d(the 15 pose and geometry inputs) and d/d(the 5 MLS fits),
+// the fits' weights (phi, dphi/dx, dphi/dy) at the 9 support nodes, the
+// nodes' density deviation and velocity, and the nodes themselves
+struct ProbePre {
+    float jF[3][15], jG[3][5], w[3][9], nf[3][9];
+    int node[2][9];
+    int ok;
+};
+
 struct AdjArgs {
     const float* f;            // f*(n) (stored shifted populations of level n)
     long long* flb;            // the step's force field (recomputed; fixed point), cleared at the end
@@ -249,6 +259,7 @@ struct AdjArgs {
     double* lam_mgeo;          // per marker and output: lambda of rb (2), nb (2), S
     double* lam_wall;          // per instance and output: lambda of wall_u[4][2]
     float* zh;                 // per instance and y wall: the Zou-He transpose (9 x 9)
+    ProbePre* ppre;            // per marker: the probe Jacobians of the level
     const int4* cblk;          // blocks of the cell kernels: (instance, bx, by, flags)
     int ncblk;
     unsigned* err;
@@ -309,6 +320,8 @@ int adjoint_block_rows();
 cudaError_t launch_adjoint_setup(const AdjArgs& a, int ninst, cudaStream_t s);
 cudaError_t launch_adjoint_step(const AdjArgs& a, cudaStream_t s);
 cudaError_t launch_adjoint_init(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint_probes_pre(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint_probes_fin(const AdjArgs& a, cudaStream_t s);
 // OR `bits` into the device error word, as a kernel that detects an error does
 cudaError_t launch_raise(unsigned* err, unsigned bits, cudaStream_t s);
 cudaError_t launch_probes(int prec, const ParticleArgs& a, int nblocks, cudaStream_t s);
