@@ -219,7 +219,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // the next recompute (the forward fluid kernel's job in a normal step; this
 // kernel is their last reader).  A warp is one 32-cell row segment; no lane
 // leaves early.
-__global__ void __launch_bounds__(32 * AB, 3) k_adj_cells(AdjArgs a) {
+__global__ void __launch_bounds__(32 * AB, 4) k_adj_cells(AdjArgs a) {
     const CellPos q = cell_pos(a);
     const Inst& I = *q.I;
     // the lattice's geometry in registers; element offsets within one
