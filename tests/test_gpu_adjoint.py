@@ -61,6 +61,7 @@ def test_adjoint_matches_oracle_finite_differences():
         assert abs(vals[b, 0] - base[b, 0]) < 1e-3
         assert np.all(sw[b] == 0), "a switch-free difference is needed for the check"
         assert np.all(err <= 1e-3), err
+        assert np.all(swc[b] > 0), swc[b]  # h = 1e-4 crosses support switches (see the tangent test)
     print(f"worst scaled row error over {len(idx)} instances: {worst:.3e}")
 
 

@@ -159,7 +159,7 @@ def _fd(P, T, steps, hs):
 
 def test_sensitivities_match_oracle_finite_differences():
     steps = 2000
-    idx = [0, 1, 2]
+    idx = [0, 1, 2, 9, 27, 45, 61, 63]
     P, T = PARAMS[idx], THETAS[idx]
     vals, J = sens.transport_jacobian(P, T, steps=steps)
     Jf, sw, used, base = _fd(P, T, steps, [1e-8, 1e-9, 1e-10])
@@ -176,6 +176,9 @@ def test_sensitivities_match_oracle_finite_differences():
         assert abs(vals[b, 1] - base[b, 1]) <= 1e-3 * abs(base[b, 1])
         assert np.all(sw[b] == 0), "a switch-free difference is needed for the check"
         assert np.all(err <= 1e-3), err
+        # the premise of the switch-free step: at h = 1e-4 every pair of runs
+        # crosses MLS support switches, so its quotients measure the jumps
+        assert np.all(swc[b] > 0), swc[b]
 
 
 def test_autograd_backward_is_the_vector_jacobian_product():
