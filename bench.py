@@ -38,6 +38,18 @@ FALLBACK_HBM_GBS = 6800.0
 BYTES_PER_CELL = {0: 144, 1: 72, 2: 36, 3: 288}
 PREC_NAMES = {0: "f64", 1: "f32", 2: "f16-storage/f32", 3: "f32+3 tangents"}
 
+
+def kernels_per_step(prec, particles, mode=0):
+    """Kernel launches of one lbm_step: the fluid kernel, and with particles
+    the probe and marker kernels, plus the spreading kernel where the marker
+    kernel does not spread into the fixed-point field itself (FP64 and the
+    tangent mode).  A batch in the overlapped mode runs that chain once per
+    part (two); the fused mode is one persistent launch."""
+    if mode == 1:
+        return 1
+    k = 1 + ((2 if prec in (1, 2) else 3) if particles else 0)
+    return k * (2 if mode == 2 else 1)
+
 # DRAM bytes per fluid-kernel launch from ncu captures, recorded beside the
 # profile summaries: a list of records keyed by the hash of the kernel
 # sources the capture ran, the workload, the precision and the tile shape
@@ -251,7 +263,7 @@ def time_device(wl, prec, steps, warmup, flush, pick_tile=False, tile=None):
         do_flush()
         ms_fluid += sim.step_timed(1)[1]
     sim.sync()
-    launches = steps * (4 if wl.particles else 1)
+    launches = steps * kernels_per_step(prec, bool(wl.particles))
     tile = sim.tile()
     sim.close()
     return ms_step, ms_fluid, launches, tile
@@ -269,17 +281,21 @@ def screening_batch(prec, wls):
     return b
 
 
-def time_batched(prec, steps, warmup, instances=512, mode=None):
+def time_batched(prec, steps, warmup, instances=512, mode=None, indices=None):
     """The screening batch (512 uneven lattices, 63 M cells, beyond L2) as
     one context, in step mode `mode` (None: the library's default for
     batches): device time per step over a run of graph-replayed steps (CUDA
     events on the context's stream around lbm_step, as a long run steps),
-    and the fluid kernel's own time from timed single steps."""
+    and the fluid kernel's own time from timed single steps.  `indices`
+    (this rank's share of a split batch) selects lattices of the first
+    `instances`."""
     import torch
 
     from paper_1606_01805_gb300 import workloads as W
 
     wls = W.batched_screening(steps=0)[:instances]
+    if indices is not None:
+        wls = [wls[k] for k in indices]
     b = screening_batch(prec, wls)
     if mode is not None:
         b.set_step_mode(mode)
@@ -297,7 +313,7 @@ def time_batched(prec, steps, warmup, instances=512, mode=None):
     tile, used = b.tile(), b.step_mode()
     b.close()
     cells = sum(w.cells for w in wls)
-    return cells, ms_step, ms_fluid, tile, used
+    return cells, ms_step, ms_fluid, tile, used, run * kernels_per_step(prec, True, used)
 
 
 def time_sensitivity(prec, steps, warmup, n=64):
@@ -464,6 +480,26 @@ def replica_throughput(ms_local, cells, steps, world):
     return world * cells * steps / (ms[0] * 1e-3) / 1e6, ms
 
 
+def sharded_throughput(cells_local, ms_local, world):
+    """Whole-job rate of a batch split over `world` ranks: every rank's cell
+    updates per step (summed over ranks) over the slowest rank's time per
+    step (max over ranks); the two reductions are the run's only
+    collectives.  Returns (MLUPS, total cells, [max ms per step, ...])."""
+    import torch
+
+    c = torch.tensor([float(cells_local)], dtype=torch.float64)
+    t = torch.tensor([float(m) for m in ms_local], dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+
+        if dist.get_backend() == "nccl":
+            c, t = c.cuda(), t.cuda()
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    cells, ms = c.cpu().item(), t.cpu().tolist()
+    return cells / (ms[0] * 1e-3) / 1e6, cells, ms
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -620,7 +656,7 @@ def main():
             mode_names = {_lb.LBM_STEP_SEPARATE: "separate", _lb.LBM_STEP_OVERLAP: "overlap",
                           _lb.LBM_STEP_FUSED: "fused"}
             for pname, pv in (("fp32", 1), ("fp16s", 2)):
-                bc, bms, bmsf, btile, bmode = time_batched(pv, 64, 3)
+                bc, bms, bmsf, btile, bmode, _ = time_batched(pv, 64, 3)
                 bpc = BYTES_PER_CELL[pv]
                 batched[pname] = {"MLUPS": bc / (bms * 1e-3) / 1e6, "ms_per_step": bms,
                                   "fluid_GBps": bpc * bc / (bmsf * 1e-3) / 1e9,
@@ -667,15 +703,22 @@ def main():
 
 def main_screening(args):
     """`--workload screening`: the 512-lattice batch is the timed workload
-    (63 M cells, beyond L2: no flush), one context, one launch per kernel."""
+    (63 M cells, beyond L2: no flush), one context, one launch per kernel.
+    Under torchrun each rank steps its share of the lattices (split by
+    cells, no exchange between ranks); the value is all ranks' cell
+    updates over the slowest rank's time."""
     import torch
 
     from paper_1606_01805_gb300 import build
     from paper_1606_01805_gb300 import workloads as W
+    from paper_1606_01805_gb300.shard import rank_instances
 
     prec = {"fp64": 0, "fp32": 1, "fp16s": 2}[args.precision]
     wls = W.batched_screening(steps=0)[:args.instances]
+    ws, rank, local = dist_env()
     if args.impl == "reference":
+        if rank != 0:
+            return
         # the oracle on the 8 sampled lattices 0, 64, ..., 448 (the whole batch
         # would take hours): cell updates over the time of the sample
         from oracle import oracle as o
@@ -703,24 +746,41 @@ def main_screening(args):
                                        f"OpenMP over the lattice rows on {cores} host threads"},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
-    torch.cuda.set_device(0)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
     build.build()
-    with ClockSampler(0) as clk:
-        cells, ms, msf, tile, _ = time_batched(prec, args.steps, args.warmup, args.instances)
+    # the lattices are independent: each rank steps its share of the batch
+    # as one context, with no exchange between ranks
+    mine = rank_instances([w.cells for w in wls], rank, ws) if ws > 1 else None
+    with ClockSampler(local) as clk:
+        cells_local, ms_local, msf_local, tile, _, launches = time_batched(
+            prec, args.steps, args.warmup, args.instances, indices=mine)
+    if ws > 1:
+        dist.barrier()
+    value, cells, (ms, _) = sharded_throughput(cells_local, [ms_local, msf_local], ws)
+    if rank != 0:
+        return
     peak, peak_kind = hbm_peak()
     bpc = BYTES_PER_CELL[prec]
-    achieved = bpc * cells / (msf * 1e-3) / 1e9
+    achieved = bpc * cells_local / (msf_local * 1e-3) / 1e9
     print(json.dumps({
-        "metric": METRIC, "value": cells / (ms * 1e-3) / 1e6, "unit": "MLUPS", "n_gpus": 1,
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAMES[prec], "data": "synthetic",
+        "scaling": "strong" if ws > 1 else "weak", "vs_baseline": None, "dtype": PREC_NAMES[prec],
+        "data": "synthetic",
         "config": {"workload": f"screening batch: {len(wls)} Couette lattices 256-1024 x 128-256, "
                                "one random particle each (seed 3)", "cells": cells,
-                   "l2": "inputs larger than L2", "tile": tile},
+                   "l2": "inputs larger than L2", "tile": tile,
+                   "parallelism": f"instances split over {ws} ranks (cells balanced), no exchange"
+                   if ws > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_fluid (task list)",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_fluid (task list)" + (", rank 0's share" if ws > 1 else ""),
                      "peak_source": f"{peak_kind} (burst copy)"},
-        "gpu_launches": 4 * args.steps, "clocks": clk.summary()}))
+        "gpu_launches": launches, "clocks": clk.summary()}))
 
 
 def main_adjoint(args):
