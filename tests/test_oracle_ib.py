@@ -8,6 +8,8 @@ import pytest
 
 from oracle import oracle as o
 
+from .test_oracle_golden import golden
+
 RNG = np.random.default_rng(777)
 
 
@@ -345,9 +347,11 @@ def test_marker_force_sign_pushes_fluid_with_the_body():
 
 def test_circle_in_couette_rotates_near_half_shear():
     """Section 4.2: a neutrally buoyant circle in Couette flow at Re = 20
-    rotates at omega L / u_max = 0.117, close to half the shear rate (0.125),
-    and is carried at the local undisturbed velocity.  400 x 100 channel,
-    walls at +-U, D = 20, released at y = 0.3 H (the plain FP64 workload)."""
+    rotates at omega L / u_max = 0.117, close to half the shear rate (0.125;
+    both from tests/golden/shear_transport.txt), and is carried at the local
+    undisturbed velocity.  400 x 100 channel, walls at +-U, D = 20, released
+    at y = 0.3 H (the plain FP64 workload)."""
+    g = golden()
     nx, ny, tau = 400, 100, 0.8
     H = ny - 1
     U = 20 * (tau - 0.5) / 3 / H / 2
@@ -356,7 +360,7 @@ def test_circle_in_couette_rotates_near_half_shear():
     s.step(2000)
     p = s.particles()[0]
     half_shear = 0.5 * 2 * U / H
-    assert -p["omega"] / half_shear == pytest.approx(0.117 / 0.125, abs=0.05)
+    assert -p["omega"] / half_shear == pytest.approx(g["omega_eq"] / g["half_shear_rate"], abs=0.05)
     u_local = -U + 2 * U * p["yc"] / H
     assert p["u"][0] == pytest.approx(u_local, rel=0.03)
     assert abs(p["u"][1]) < 0.02 * abs(p["u"][0])  # lateral drift is much slower
