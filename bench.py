@@ -281,14 +281,15 @@ def screening_batch(prec, wls):
     return b
 
 
-def time_batched(prec, steps, warmup, instances=512, mode=None, indices=None):
+def time_batched(prec, steps, warmup, instances=512, mode=None, indices=None, tile=None):
     """The screening batch (512 uneven lattices, 63 M cells, beyond L2) as
     one context, in step mode `mode` (None: the library's default for
     batches): device time per step over a run of graph-replayed steps (CUDA
     events on the context's stream around lbm_step, as a long run steps),
     and the fluid kernel's own time from timed single steps.  `indices`
     (this rank's share of a split batch) selects lattices of the first
-    `instances`."""
+    `instances`; `tile` forces a fluid tile variant instead of the
+    library's timing of all of them at the first step."""
     import torch
 
     from paper_1606_01805_gb300 import workloads as W
@@ -299,6 +300,8 @@ def time_batched(prec, steps, warmup, instances=512, mode=None, indices=None):
     b = screening_batch(prec, wls)
     if mode is not None:
         b.set_step_mode(mode)
+    if tile is not None:
+        b.set_tile(tile)
     b.step(max(warmup, 1))  # the first step picks the fluid tile
     b.sync()
     run = max(32, steps // 32 * 32)
@@ -757,7 +760,7 @@ def main_screening(args):
     mine = rank_instances([w.cells for w in wls], rank, ws) if ws > 1 else None
     with ClockSampler(local) as clk:
         cells_local, ms_local, msf_local, tile, _, launches = time_batched(
-            prec, args.steps, args.warmup, args.instances, indices=mine)
+            prec, args.steps, args.warmup, args.instances, indices=mine, tile=args.tile)
     if ws > 1:
         dist.barrier()
     value, cells, (ms, _) = sharded_throughput(cells_local, [ms_local, msf_local], ws)

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cuda/std/limits>
+#include <type_traits>
 
 #include "lbib_device.cuh"
 
@@ -157,6 +158,7 @@ template <> __device__ __forceinline__ float lds<__half, float>(const __half* p)
 // GlobalSrc: the population buffer itself (read-only path).
 template <class S, class C, int N>
 struct GlobalSrc {
+    static constexpr bool GLOBAL = true;
     const S* f;
     long long plane;
     int pitch, ny;
@@ -176,6 +178,7 @@ __device__ __forceinline__ GlobalSrc<S, C, N> global_src(const S* f, const Geo& 
 // (pitch, ny: the lattice's row pitch and rows).
 template <class S, class C, int N>
 struct StageSrc {
+    static constexpr bool GLOBAL = false;
     const S* st;
     int sw, rows, y0, xs, pitch, ny;
     __device__ __forceinline__ const S* row(int i, int y) const {
@@ -271,6 +274,77 @@ __device__ __forceinline__ void pulled_plane(int i, const C q[N], C bnd, C wl, i
     }
 }
 
+// FP16 storage read straight from global memory, two or four cells per
+// thread, stays packed (two halves per 32-bit word) from the loads through
+// the pull to the stores; a cell's values are widened to FP32 only around
+// its collision.  That takes half the registers of the widened
+// vectors (which spilled at the register budget of 1024 threads per SM).
+// The bits are those of the widened path: the pull only moves halves, the
+// collisions see the same FP32 values, and the results round to FP16 the
+// same way (round to nearest even).
+template <int N> struct Packed {
+    static_assert(N == 2 || N == 4, "packed FP16 vectors hold two or four cells");
+    static constexpr int W = N / 2;
+    unsigned w[W];  // w[j]: cell 2j in the low half, cell 2j + 1 in the high half
+    __device__ __forceinline__ void load(const __half* p) {
+        if constexpr (N == 4) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+            w[0] = q.x;
+            w[1] = q.y;
+        } else {
+            w[0] = __ldg(reinterpret_cast<const unsigned*>(p));
+        }
+    }
+    __device__ __forceinline__ void store(__half* p) const {
+        if constexpr (N == 4) *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+        else *reinterpret_cast<unsigned*>(p) = w[0];
+    }
+    __device__ __forceinline__ unsigned half(int k) const { return k & 1 ? w[k >> 1] >> 16 : w[k >> 1] & 0xffffu; }
+    __device__ __forceinline__ void set(int k, unsigned h) {
+        w[k >> 1] = k & 1 ? (w[k >> 1] & 0xffffu) | (h << 16) : (w[k >> 1] & 0xffff0000u) | h;
+    }
+};
+__device__ __forceinline__ unsigned ld_bits(const __half* p) {
+    return __ldg(reinterpret_cast<const unsigned short*>(p));
+}
+__device__ __forceinline__ void st_bits(__half* p, unsigned h) {
+    *reinterpret_cast<unsigned short*>(p) = static_cast<unsigned short>(h);
+}
+__device__ __forceinline__ float widen1(unsigned bits) {
+    return __half2float(__ushort_as_half(static_cast<unsigned short>(bits)));
+}
+__device__ __forceinline__ unsigned narrow1(float v) { return __half_as_ushort(__float2half_rn(v)); }
+
+// pulled_plane on packed halves: a pull along +-x moves every half one
+// place (a byte permutation of neighbouring words), the half that enters
+// at the warp's row end coming from the neighbouring lane's word (bnd at
+// lanes 0 / 31); on the periodic x edge x = 0 (wrap_l) or x = nx - 1 (at ke,
+// wrap_r) takes wl.
+template <int N>
+__device__ __forceinline__ void pulled_packed(int i, Packed<N>& q, unsigned bnd, unsigned wl, int lane, bool wrap_l,
+                                              bool wrap_r, int ke) {
+    constexpr int W = N / 2;
+    if (cx(i) > 0) {  // source x - 1: the left neighbour's last half enters at cell 0
+        unsigned left = __shfl_up_sync(0xffffffffu, q.w[W - 1], 1);
+        if (lane == 0) left = bnd << 16;
+#pragma unroll
+        for (int j = W - 1; j >= 1; --j) q.w[j] = __byte_perm(q.w[j - 1], q.w[j], 0x5432);
+        q.w[0] = __byte_perm(left, q.w[0], 0x5432);
+        if (wrap_l) q.set(0, wl);
+    } else if (cx(i) < 0) {  // source x + 1: the right neighbour's first half enters at cell N - 1
+        unsigned right = __shfl_down_sync(0xffffffffu, q.w[0], 1);
+        if (lane == 31) right = bnd;
+#pragma unroll
+        for (int j = 0; j < W - 1; ++j) q.w[j] = __byte_perm(q.w[j], q.w[j + 1], 0x5432);
+        q.w[W - 1] = __byte_perm(q.w[W - 1], right, 0x5432);
+        if (wrap_r) {
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+                if (k == ke) q.set(k, wl);
+        }
+    }
+}
+
 // Fused step of one tile: N consecutive cells (x0 .. x0+N-1, x0 = N * lane
 // index) of one row per thread, a warp covering 32 N cells of a row, the
 // block BY rows.  Populations move as vectors of N elements: a pull along
@@ -315,147 +389,230 @@ __device__ __forceinline__ void fluid_tile(const Src& src, const Geo& G, const S
     if (!PDL) forced = any && flags[seg] != 0;
     bool bad = false;  // watchdog
 
-    C v[9][N], fxh[N], fyh[N];  // (fxh, fyh: the forces read early, HOIST)
     const bool wrap = G.px && rows_in && any;
     const int ke = G.nx - 1 - x0;  // position of x = nx - 1 in this thread's cells
     const bool wrap_l = wrap && x0 == 0, wrap_r = wrap && ke >= 0 && ke < N;
-    // Two load orders, chosen per storage type and width by measurement on
-    // GB300: FP32 and FP16 vectors of two or four cells issue every
-    // population load and the force loads of a flagged segment before
-    // consuming any (the flag -> force chain then overlaps the population
-    // loads; the 512-lattice batch in FP16 storage 0.946 -> 0.902 ms per
-    // step); FP64 and one-cell tiles load and shuffle plane by plane and
-    // read the forces after the populations (fewer live registers).
-    if constexpr (HOIST) {
-        C q[9][N], bnd[9], wl[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const S* rp = src.row(i, y);
-            const int xa = min(x0, src.pitch - N);
-            src.vec(rp + xa, q[i]);
-            bnd[i] = wl[i] = C(0);
-            if (cx(i) > 0 && lane == 0) bnd[i] = src.one(rp + max(xa - 1, 0));
-            if (cx(i) < 0 && lane == 31) bnd[i] = src.one(rp + min(xa + N, src.pitch - 1));
-            const S* wp = fin + (long long)i * G.plane + (long long)(y - cy(i)) * G.pitch;
-            if (cx(i) > 0 && wrap_l) wl[i] = ld<S, C>(wp + (G.nx - 1));
-            if (cx(i) < 0 && wrap_r) wl[i] = ld<S, C>(wp);
-        }
-        if (PDL) {
-            // the populations are on their way; the forces of this step
-            // come from the spreading items before this one
-            wait();
-            forced = any && flags[seg] != 0;
-        }
-#pragma unroll
-        for (int k = 0; k < N; ++k) fxh[k] = fyh[k] = C(0);
-        load_forces<C, N>(forced, flb, row, G.plane, x0, G.nx, fxh, fyh);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) pulled_plane<C, N>(i, q[i], bnd[i], wl[i], lane, wrap_l, wrap_r, ke, v[i]);
-    } else {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const S* rp = src.row(i, y);
-            const int xa = min(x0, G.pitch - N);
-            C q[N], bnd = C(0), wl = C(0);
-            src.vec(rp + xa, q);
-            if (cx(i) > 0 && lane == 0) bnd = src.one(rp + max(xa - 1, 0));
-            if (cx(i) < 0 && lane == 31) bnd = src.one(rp + min(xa + N, G.pitch - 1));
-            pulled_plane<C, N>(i, q, bnd, wl, lane, false, false, ke, v[i]);
-        }
-        // periodic x: the three populations that cross the edge
-        if (wrap_l || wrap_r) {
+    constexpr bool PACKED = std::is_same<S, __half>::value && N >= 2 && Src::GLOBAL;
+    if constexpr (PACKED) {
+        // the HOIST load order on packed halves, then the cells one by one
+        Packed<N> pv[9];
+        C fxh[N], fyh[N];
+        {
+            unsigned bnd[9], wl[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
+                const S* rp = src.row(i, y);
+                const int xa = min(x0, src.pitch - N);
+                pv[i].load(rp + xa);
+                bnd[i] = wl[i] = 0u;
+                if (cx(i) > 0 && lane == 0) bnd[i] = ld_bits(rp + max(xa - 1, 0));
+                if (cx(i) < 0 && lane == 31) bnd[i] = ld_bits(rp + min(xa + N, src.pitch - 1));
                 const S* wp = fin + (long long)i * G.plane + (long long)(y - cy(i)) * G.pitch;
-                if (cx(i) > 0 && wrap_l) v[i][0] = ld<S, C>(wp + (G.nx - 1));
-                if (cx(i) < 0 && wrap_r) {
-                    const C w0 = ld<S, C>(wp);
-#pragma unroll
-                    for (int k = 0; k < N; ++k)
-                        if (k == ke) v[i][k] = w0;
-                }
+                if (cx(i) > 0 && wrap_l) wl[i] = ld_bits(wp + (G.nx - 1));
+                if (cx(i) < 0 && wrap_r) wl[i] = ld_bits(wp);
             }
-        }
-        if (PDL) {
-            wait();
-            forced = any && flags[seg] != 0;
-        }
-    }
-    if (any) {
-        C fxi[N], fyi[N];
+            if (PDL) {
+                wait();
+                forced = any && flags[seg] != 0;
+            }
 #pragma unroll
-        for (int k = 0; k < N; ++k) fxi[k] = fyi[k] = C(0);
-        if constexpr (HOIST) {
+            for (int k = 0; k < N; ++k) fxh[k] = fyh[k] = C(0);
+            load_forces<C, N>(forced, flb, row, G.plane, x0, G.nx, fxh, fyh);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) pulled_packed<N>(i, pv[i], bnd[i], wl[i], lane, wrap_l, wrap_r, ke);
+        }
+        if (any) {
+            unsigned edge = 0;  // bit k: cell x0 + k lies on an edge (and inside the lattice)
+            bool ok = true;
 #pragma unroll
             for (int k = 0; k < N; ++k) {
-                fxi[k] = fxh[k];
-                fyi[k] = fyh[k];
-            }
-        } else {
-            load_forces<C, N>(forced, flb, row, G.plane, x0, G.nx, fxi, fyi);
-        }
-        // interior cells from the vector values.  With one cell per thread
-        // so are the cells of an x wall between the two y edges: their six
-        // known populations come from inside the row range, and the Zou-He
-        // completion replaces the three that point into the fluid (with
-        // four cells per thread the completion inlined per cell costs the
-        // vector path registers, so those cells take the general path)
-        constexpr bool XW = N == 1;
-        unsigned edge = 0;  // bit k: cell x0 + k lies on an edge (and inside the lattice)
-        bool ok = true;     // the watchdog's verdict on this thread's cells
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const int xk = x0 + k;
-            if (rows_in && xk < G.nx && (wrap || XW || (xk >= 1 && xk <= G.nx - 2))) {
-                C c[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) c[i] = v[i][k];
-                if (XW && !G.px && (xk == 0 || xk == G.nx - 1)) {
-                    const C gx = geo_g<C>(G, 0), gy = geo_g<C>(G, 1);
-                    if (xk == 0) zou_he_edge<1, 0, C>(c, geo_uw<C>(G, 0, 0), geo_uw<C>(G, 0, 1), gx, gy);
-                    else zou_he_edge<-1, 0, C>(c, geo_uw<C>(G, 1, 0), geo_uw<C>(G, 1, 1), gx, gy);
-                }
-                ok &= cell_update<C>(c, G, fxi[k], fyi[k]);
-#pragma unroll
-                for (int i = 0; i < 9; ++i) v[i][k] = c[i];
-            } else if (xk < G.nx) {
-                edge |= 1u << k;
-            }
-        }
-        if (edge == 0 && x0 + N - 1 < G.nx) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) Vec<S, C, N>::store(fout + (long long)i * G.plane + row + x0, v[i]);
-        } else {
-#pragma unroll
-            for (int k = 0; k < N; ++k)
-                if (x0 + k < G.nx && !(edge >> k & 1u)) {
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) st<S, C>(fout + (long long)i * G.plane + row + x0 + k, v[i][k]);
-                }
-            // cells on a wall or periodic edge: general pull, wall completion,
-            // collision, one at a time (emitted once, nothing else live)
-#pragma unroll 1
-            for (int k = 0; k < N; ++k) {
-                if (!(edge >> k & 1u)) continue;
                 const int xk = x0 + k;
-                C c[9];
-                pull_general<S, C>(fin, G, xk, y, c);
-                complete_walls<S, C>(fin, G, xk, y, c);
-                C gx = C(0), gy = C(0);
-                if (forced) {  // forces of this cell were read above
+                if (rows_in && xk < G.nx && (wrap || (xk >= 1 && xk <= G.nx - 2))) {
+                    C c[9];
 #pragma unroll
-                    for (int j = 0; j < N; ++j)
-                        if (j == k) {
-                            gx = fxi[j];
-                            gy = fyi[j];
-                        }
+                    for (int i = 0; i < 9; ++i) c[i] = widen1(pv[i].half(k));
+                    ok &= cell_update<C>(c, G, fxh[k], fyh[k]);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) pv[i].set(k, narrow1(c[i]));
+                } else if (xk < G.nx) {
+                    edge |= 1u << k;
                 }
-                ok &= cell_update<C>(c, G, gx, gy);
+            }
+            if (edge == 0 && x0 + N - 1 < G.nx) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) st<S, C>(fout + (long long)i * G.plane + row + xk, c[i]);
+                for (int i = 0; i < 9; ++i) pv[i].store(fout + (long long)i * G.plane + row + x0);
+            } else {
+#pragma unroll
+                for (int k = 0; k < N; ++k)
+                    if (x0 + k < G.nx && !(edge >> k & 1u)) {
+#pragma unroll
+                        for (int i = 0; i < 9; ++i)
+                            st_bits(fout + (long long)i * G.plane + row + x0 + k, pv[i].half(k));
+                    }
+                // cells on a wall or periodic edge: the general path
+#pragma unroll 1
+                for (int k = 0; k < N; ++k) {
+                    if (!(edge >> k & 1u)) continue;
+                    const int xk = x0 + k;
+                    C c[9];
+                    pull_general<S, C>(fin, G, xk, y, c);
+                    complete_walls<S, C>(fin, G, xk, y, c);
+                    C gx = C(0), gy = C(0);
+                    if (forced) {
+#pragma unroll
+                        for (int jj = 0; jj < N; ++jj)
+                            if (jj == k) {
+                                gx = fxh[jj];
+                                gy = fyh[jj];
+                            }
+                    }
+                    ok &= cell_update<C>(c, G, gx, gy);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) st<S, C>(fout + (long long)i * G.plane + row + xk, c[i]);
+                }
+            }
+            bad = !ok;
+        }
+    } else {
+        C v[9][N], fxh[N], fyh[N];  // (fxh, fyh: the forces read early, HOIST)
+        // Two load orders, chosen per storage type and width by measurement on
+        // GB300: FP32 and FP16 vectors of two or four cells issue every
+        // population load and the force loads of a flagged segment before
+        // consuming any (the flag -> force chain then overlaps the population
+        // loads; the 512-lattice batch in FP16 storage 0.946 -> 0.902 ms per
+        // step); FP64 and one-cell tiles load and shuffle plane by plane and
+        // read the forces after the populations (fewer live registers).
+        if constexpr (HOIST) {
+            C q[9][N], bnd[9], wl[9];
+    #pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const S* rp = src.row(i, y);
+                const int xa = min(x0, src.pitch - N);
+                src.vec(rp + xa, q[i]);
+                bnd[i] = wl[i] = C(0);
+                if (cx(i) > 0 && lane == 0) bnd[i] = src.one(rp + max(xa - 1, 0));
+                if (cx(i) < 0 && lane == 31) bnd[i] = src.one(rp + min(xa + N, src.pitch - 1));
+                const S* wp = fin + (long long)i * G.plane + (long long)(y - cy(i)) * G.pitch;
+                if (cx(i) > 0 && wrap_l) wl[i] = ld<S, C>(wp + (G.nx - 1));
+                if (cx(i) < 0 && wrap_r) wl[i] = ld<S, C>(wp);
+            }
+            if (PDL) {
+                // the populations are on their way; the forces of this step
+                // come from the spreading items before this one
+                wait();
+                forced = any && flags[seg] != 0;
+            }
+    #pragma unroll
+            for (int k = 0; k < N; ++k) fxh[k] = fyh[k] = C(0);
+            load_forces<C, N>(forced, flb, row, G.plane, x0, G.nx, fxh, fyh);
+    #pragma unroll
+            for (int i = 0; i < 9; ++i) pulled_plane<C, N>(i, q[i], bnd[i], wl[i], lane, wrap_l, wrap_r, ke, v[i]);
+        } else {
+    #pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const S* rp = src.row(i, y);
+                const int xa = min(x0, G.pitch - N);
+                C q[N], bnd = C(0), wl = C(0);
+                src.vec(rp + xa, q);
+                if (cx(i) > 0 && lane == 0) bnd = src.one(rp + max(xa - 1, 0));
+                if (cx(i) < 0 && lane == 31) bnd = src.one(rp + min(xa + N, G.pitch - 1));
+                pulled_plane<C, N>(i, q, bnd, wl, lane, false, false, ke, v[i]);
+            }
+            // periodic x: the three populations that cross the edge
+            if (wrap_l || wrap_r) {
+    #pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const S* wp = fin + (long long)i * G.plane + (long long)(y - cy(i)) * G.pitch;
+                    if (cx(i) > 0 && wrap_l) v[i][0] = ld<S, C>(wp + (G.nx - 1));
+                    if (cx(i) < 0 && wrap_r) {
+                        const C w0 = ld<S, C>(wp);
+    #pragma unroll
+                        for (int k = 0; k < N; ++k)
+                            if (k == ke) v[i][k] = w0;
+                    }
+                }
+            }
+            if (PDL) {
+                wait();
+                forced = any && flags[seg] != 0;
             }
         }
-        bad = !ok;
+        if (any) {
+            C fxi[N], fyi[N];
+    #pragma unroll
+            for (int k = 0; k < N; ++k) fxi[k] = fyi[k] = C(0);
+            if constexpr (HOIST) {
+    #pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    fxi[k] = fxh[k];
+                    fyi[k] = fyh[k];
+                }
+            } else {
+                load_forces<C, N>(forced, flb, row, G.plane, x0, G.nx, fxi, fyi);
+            }
+            // interior cells from the vector values.  With one cell per thread
+            // so are the cells of an x wall between the two y edges: their six
+            // known populations come from inside the row range, and the Zou-He
+            // completion replaces the three that point into the fluid (with
+            // four cells per thread the completion inlined per cell costs the
+            // vector path registers, so those cells take the general path)
+            constexpr bool XW = N == 1;
+            unsigned edge = 0;  // bit k: cell x0 + k lies on an edge (and inside the lattice)
+            bool ok = true;     // the watchdog's verdict on this thread's cells
+    #pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const int xk = x0 + k;
+                if (rows_in && xk < G.nx && (wrap || XW || (xk >= 1 && xk <= G.nx - 2))) {
+                    C c[9];
+    #pragma unroll
+                    for (int i = 0; i < 9; ++i) c[i] = v[i][k];
+                    if (XW && !G.px && (xk == 0 || xk == G.nx - 1)) {
+                        const C gx = geo_g<C>(G, 0), gy = geo_g<C>(G, 1);
+                        if (xk == 0) zou_he_edge<1, 0, C>(c, geo_uw<C>(G, 0, 0), geo_uw<C>(G, 0, 1), gx, gy);
+                        else zou_he_edge<-1, 0, C>(c, geo_uw<C>(G, 1, 0), geo_uw<C>(G, 1, 1), gx, gy);
+                    }
+                    ok &= cell_update<C>(c, G, fxi[k], fyi[k]);
+    #pragma unroll
+                    for (int i = 0; i < 9; ++i) v[i][k] = c[i];
+                } else if (xk < G.nx) {
+                    edge |= 1u << k;
+                }
+            }
+            if (edge == 0 && x0 + N - 1 < G.nx) {
+    #pragma unroll
+                for (int i = 0; i < 9; ++i) Vec<S, C, N>::store(fout + (long long)i * G.plane + row + x0, v[i]);
+            } else {
+    #pragma unroll
+                for (int k = 0; k < N; ++k)
+                    if (x0 + k < G.nx && !(edge >> k & 1u)) {
+    #pragma unroll
+                        for (int i = 0; i < 9; ++i) st<S, C>(fout + (long long)i * G.plane + row + x0 + k, v[i][k]);
+                    }
+                // cells on a wall or periodic edge: general pull, wall completion,
+                // collision, one at a time (emitted once, nothing else live)
+    #pragma unroll 1
+                for (int k = 0; k < N; ++k) {
+                    if (!(edge >> k & 1u)) continue;
+                    const int xk = x0 + k;
+                    C c[9];
+                    pull_general<S, C>(fin, G, xk, y, c);
+                    complete_walls<S, C>(fin, G, xk, y, c);
+                    C gx = C(0), gy = C(0);
+                    if (forced) {  // forces of this cell were read above
+    #pragma unroll
+                        for (int j = 0; j < N; ++j)
+                            if (j == k) {
+                                gx = fxi[j];
+                                gy = fyi[j];
+                            }
+                    }
+                    ok &= cell_update<C>(c, G, gx, gy);
+    #pragma unroll
+                    for (int i = 0; i < 9; ++i) st<S, C>(fout + (long long)i * G.plane + row + xk, c[i]);
+                }
+            }
+            bad = !ok;
+        }
     }
     // the force field and the flag are cleared for the next step only now,
     // after their values were used (stores right behind the loads of the
