@@ -371,8 +371,9 @@ bool ctx_variant_ok(const lbm_ctx* ctx, int v) {
 bool watched(const lbm_ctx* ctx, int64_t step) { return (step + 1) % ctx->check_every == 0; }
 
 // pdl: launch the fluid kernel with programmatic stream serialization (only
-// right after the spreading kernel: its prologue loads the populations the
-// previous step's fluid kernel wrote); check: the kernel runs its watchdog;
+// right after the kernel that spreads the forces -- the marker kernel, or
+// the spreading kernel in FP64 and the tangent mode: its prologue loads the
+// populations the previous step's fluid kernel wrote); check: the kernel runs its watchdog;
 // stall: the test hook of lbm_inject_stall; keep: leave the forces and
 // their flags in place (the autotuner's repeated launches of one step)
 lbm_status launch_fluid_step(lbm_ctx* ctx, cudaStream_t st, int cur, int v, bool pdl = false,
@@ -1239,7 +1240,7 @@ lbm_status lbm_step_timed(lbm_ctx* ctx, int32_t nsteps, double* ms_step, double*
         if (!e) CK(cudaEventCreate(&e));
     double tot = 0, flu = 0;
     // the event before the fluid kernel only when its time is asked for: it
-    // keeps the fluid kernel from starting before the spreading kernel ends
+    // keeps the fluid kernel from starting before the forces are spread
     const bool mid = ms_fluid != nullptr;
     if (fused(ctx) && ctx->items_dirty && nsteps > 0) {
         lbm_status s = build_items(ctx);

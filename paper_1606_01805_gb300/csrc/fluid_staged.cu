@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(STHREADS, 2)
             if (t < ntiles)
                 issue_tile<S, N, ONE>(a, tmap, t, ntx, stages + s * Sh::STAGE, bar + s, slot + s, sinst + s);
         }
-    pdl_wait();  // forces and flags come from the spreading kernel before this one
+    pdl_wait();  // forces and flags come from the kernel before this one
     pdl_trigger();
     int k = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
