@@ -93,3 +93,22 @@ def test_null_arguments(lib):
     assert lib.lbm_steps_done(None) == 0
     assert lib.lbm_last_error(None) == b"null context"
     lib.lbm_destroy(None)
+
+
+def test_tile_variants_per_precision(lib):
+    """lbm_tile_info reports the ten tile shapes and which precisions have
+    them: FP32 and FP16 storage all ten, FP64 the six direct kernels, the
+    tangent mode the one-cell tile of 8 rows only."""
+    shapes = [(4, 8, 0), (4, 4, 0), (1, 8, 0), (2, 8, 0), (2, 4, 0), (1, 4, 0),
+              (4, 8, 2), (4, 8, 3), (2, 8, 3), (2, 8, 4)]
+    assert len(shapes) == lbib.LBM_TILE_VARIANTS
+    valid = {lbib.LBM_FP32: set(range(10)), lbib.LBM_FP16_SHIFTED: set(range(10)),
+             lbib.LBM_FP64: set(range(6)), lbib.LBM_FP32_TANGENT: {2}}
+    for prec, ok in valid.items():
+        for v in range(-1, lbib.LBM_TILE_VARIANTS + 1):
+            cpt, rows, st = C.c_int32(), C.c_int32(), C.c_int32()
+            rc = lib.lbm_tile_info(v, prec, C.byref(cpt), C.byref(rows), C.byref(st))
+            assert rc == (lbib.LBM_OK if v in ok else lbib.LBM_EINVAL), (prec, v)
+            if 0 <= v < lbib.LBM_TILE_VARIANTS:
+                assert (cpt.value, rows.value, st.value) == shapes[v]
+    assert lbib.tile_info(4, lbib.LBM_FP32)[:3] == (2, 4, 0)
