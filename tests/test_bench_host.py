@@ -1,8 +1,15 @@
 """Host logic of bench.py that needs no GPU: the kernel launches it claims
 per step, and the traffic record lookup keyed by the kernel sources."""
 import json
+import subprocess
+import sys
+from pathlib import Path
+
+import pytest
 
 import bench
+
+ROOT = Path(__file__).resolve().parent.parent
 
 
 def test_kernels_per_step():
@@ -47,3 +54,22 @@ def test_a_record_of_other_kernel_sources_is_ignored(tmp_path, monkeypatch):
     f.write_text(json.dumps([dict(rec, kernel_hash=bench.kernel_hash())]))
     assert bench.ncu_traffic("large_couette_16384x4096", 1, 4)[:2] == (1.0, 2.0)
     assert bench.ncu_traffic("large_couette_16384x4096", 1, 3) is None
+
+
+@pytest.mark.parametrize("args", [["--workload", "sedimentation"],
+                                  ["--workload", "screening", "--instances", "64"]])
+def test_reference_arm_prints_one_contract_line(args):
+    """`bench.py --impl reference` times the oracle on the host and prints
+    one JSON line with the bench's metric and the reference keys."""
+    out = subprocess.run([sys.executable, str(ROOT / "bench.py"), "--impl", "reference", *args,
+                          "--steps", "1", "--warmup", "0", "--threads", "2"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "MLUPS"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["dtype"] == "f64"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 2
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
