@@ -1,6 +1,7 @@
 """Host logic of bench.py that needs no GPU: the kernel launches it claims
 per step, and the traffic record lookup keyed by the kernel sources."""
 import json
+import socket
 import subprocess
 import sys
 from pathlib import Path
@@ -73,3 +74,19 @@ def test_reference_arm_prints_one_contract_line(args):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 2
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """Launched like the N-GPU bench (one process per rank), the reference
+    arm runs on rank 0 only and every rank exits 0."""
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    out = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                          "--master-addr", "127.0.0.1", "--master-port", str(port),
+                          str(ROOT / "bench.py"), "--impl", "reference", "--gpus", "2",
+                          "--workload", "sedimentation", "--steps", "1", "--warmup", "0", "--threads", "1"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1 and json.loads(lines[0])["impl"] == "reference"
